@@ -1,0 +1,158 @@
+"""The Fock exchange apply and exchange energy, one pair at a time (oracle).
+
+Conventions (Hartree units; Omega = cell volume; the grid has Ntot = N1 N2 N3
+points r_k; ``fft`` is the unnormalised forward transform with exp(-i G.r) and
+``ifft`` carries the 1/Ntot):
+
+  psi_n(r)     = Omega^-1/2 sum_{G in S} c_n(G) exp(i G.r)
+               = (Ntot / sqrt(Omega)) ifft(scatter(c_n))
+  rho_ij(r)    = psi_i*(r) psi_j(r)                      (overlap density, §4)
+  rhot_ij(G)   = fft(rho_ij)(G) / Ntot                   (M_ij of §4)
+  phi_ij(r)    = ifft(v * fft(rho_ij))(r)
+  (V_x psi_j)(r) = - sum_i f_i psi_i(r) phi_ij(r)        (V_x equation of §4)
+  (V_x psi_j)(G) = (sqrt(Omega) / Ntot) fft(V_x psi_j)(G),  G in S
+  E_x          = -(Omega/2) sum_{i,j} f_i f_j sum_G v(G) |rhot_ij(G)|^2
+                                                         (reciprocal E_x, §4)
+  dE_x/domega  = -(Omega/2) sum_{i,j} f_i f_j sum_G dv/domega |rhot_ij(G)|^2
+
+Readings of the paper used here: the printed M*(G) M(G') is diagonal in G; no
+spin or occupation factor is printed, so the occupations f_i enter exactly as
+above (f = 2 gives twice the spin-restricted physical value); V_x psi is
+projected back onto the sphere S.  All sums over i run over every band, and the
+pair loop visits every ordered pair (i, j) with its own transforms.
+"""
+
+import numpy as np
+
+from .lattice import cell_volume, grid_g2
+from .kernels import coulomb_kernel, coulomb_kernel_domega
+
+try:  # both are library FFTs; scipy's can use several host threads
+    import scipy.fft as _sfft
+
+    def _fftn(x):
+        return _sfft.fftn(x, workers=-1)
+
+    def _ifftn(x):
+        return _sfft.ifftn(x, workers=-1)
+
+except ImportError:  # pragma: no cover
+    def _fftn(x):
+        return np.fft.fftn(x)
+
+    def _ifftn(x):
+        return np.fft.ifftn(x)
+
+
+def _grid_index(miller, grid):
+    return tuple(np.asarray(miller)[:, a] % int(grid[a]) for a in range(3))
+
+
+def orbitals_to_real(c, miller, grid, cell, real=False):
+    """psi_n(r) on the grid for each row c_n(G) of ``c`` (shape nb x npw).
+
+    ``real=True`` keeps only the real part, which is the whole orbital when the
+    coefficients satisfy c(-G) = c(G)* (Gamma-point real orbitals).
+    """
+    grid = tuple(int(n) for n in grid)
+    c = np.atleast_2d(np.asarray(c, dtype=np.complex128))
+    ntot = grid[0] * grid[1] * grid[2]
+    scale = ntot / np.sqrt(cell_volume(cell))
+    idx = _grid_index(miller, grid)
+    out = np.empty((c.shape[0],) + grid, dtype=np.float64 if real else np.complex128)
+    for n in range(c.shape[0]):
+        box = np.zeros(grid, dtype=np.complex128)
+        box[idx] = c[n]
+        p = _ifftn(box) * scale
+        out[n] = p.real if real else p
+    return out
+
+
+def real_to_sphere(f, miller, grid, cell):
+    """(sqrt(Omega)/Ntot) fft(f) sampled on the sphere: the G-coefficients of f."""
+    grid = tuple(int(n) for n in grid)
+    ntot = grid[0] * grid[1] * grid[2]
+    scale = np.sqrt(cell_volume(cell)) / ntot
+    idx = _grid_index(miller, grid)
+    f = np.asarray(f)
+    if f.ndim == 3:
+        return _fftn(f)[idx] * scale
+    return np.stack([_fftn(fn)[idx] * scale for fn in f])
+
+
+def kernel_grid(kind, grid, cell, omega=None):
+    """v(G) and dv/domega on every point of the full grid."""
+    g2 = grid_g2(grid, cell)
+    vol = cell_volume(cell)
+    return coulomb_kernel(kind, g2, vol, omega), coulomb_kernel_domega(kind, g2, vol, omega)
+
+
+def pair_potential(psi_i, psi_j, vgrid):
+    """phi_ij = ifft(v * fft(psi_i* psi_j))."""
+    return _ifftn(vgrid * _fftn(np.conj(psi_i) * psi_j))
+
+
+def pair_energy(psi_i, psi_j, vgrid, dvgrid=None):
+    """e_ij = sum_G v(G) |rhot_ij(G)|^2 (and the same sum with dv/domega)."""
+    rho = np.conj(psi_i) * psi_j
+    rt = _fftn(rho) / rho.size
+    w = (rt * np.conj(rt)).real
+    e = float(np.sum(vgrid * w))
+    if dvgrid is None:
+        return e
+    return e, float(np.sum(dvgrid * w))
+
+
+def fock_apply(c, occ, miller, grid, cell, kind, omega=None, out_bands=None, real=True,
+               psi=None, src_bands=None):
+    """V_x psi_j on the sphere for j in ``out_bands`` (default: all bands).
+
+    Returns ``(vpsi[len(out_bands), npw], ex, dex)``.  ``ex`` and ``dex`` are the
+    exchange energy and its omega-derivative over the pairs visited; they are
+    returned only when ``out_bands`` covers all bands (else None).
+    ``src_bands`` restricts the sum over i (default: every band); summing the
+    results over a partition of the bands gives the full result, which is the
+    band-group distribution of the paper (§5, the EXX loop of Fig. 3).
+    ``psi`` may pass precomputed real-space orbitals (from ``orbitals_to_real``).
+    """
+    grid = tuple(int(n) for n in grid)
+    c = np.atleast_2d(np.asarray(c, dtype=np.complex128))
+    occ = np.asarray(occ, dtype=np.float64)
+    nb = c.shape[0]
+    if psi is None:
+        psi = orbitals_to_real(c, miller, grid, cell, real=real)
+    vgrid, dvgrid = kernel_grid(kind, grid, cell, omega)
+    ntot = grid[0] * grid[1] * grid[2]
+    vol = cell_volume(cell)
+    all_bands = out_bands is None
+    out_bands = list(range(nb)) if all_bands else list(out_bands)
+    src_bands = range(nb) if src_bands is None else list(src_bands)
+    vpsi = np.empty((len(out_bands), len(miller)), dtype=np.complex128)
+    esum = 0.0
+    dsum = 0.0
+    for a, j in enumerate(out_bands):
+        acc = np.zeros(grid, dtype=psi.dtype)
+        for i in src_bands:
+            rho = np.conj(psi[i]) * psi[j]
+            rho_g = _fftn(rho)
+            phi = _ifftn(vgrid * rho_g)
+            acc -= occ[i] * psi[i] * (phi.real if real else phi)
+            if all_bands:
+                w = (rho_g * np.conj(rho_g)).real / (ntot * ntot)
+                esum += occ[i] * occ[j] * float(np.sum(vgrid * w))
+                dsum += occ[i] * occ[j] * float(np.sum(dvgrid * w))
+        vpsi[a] = real_to_sphere(acc, miller, grid, cell)
+    if not all_bands:
+        return vpsi, None, None
+    return vpsi, -0.5 * vol * esum, -0.5 * vol * dsum
+
+
+def overlap_matrix_vx(c, vpsi):
+    """M_ab = <psi_a | V_x psi_b> = sum_G c_a(G)* (V_x psi_b)(G)."""
+    return np.conj(np.asarray(c)) @ np.asarray(vpsi).T
+
+
+def exchange_energy_from_vpsi(c, occ, vpsi):
+    """E_x = 1/2 sum_j f_j <psi_j | V_x psi_j>."""
+    d = np.einsum("jg,jg->j", np.conj(np.asarray(c)), np.asarray(vpsi)).real
+    return 0.5 * float(np.dot(np.asarray(occ, dtype=np.float64), d))
