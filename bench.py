@@ -1,0 +1,352 @@
+"""Throughput of the Fock exchange apply on one GB300 (and N GPUs under torchrun).
+
+Default workload: Gamma-point FP64 apply, cubic cell L = 27 bohr, 96^3 grid,
+Ecut = 12 Ha (39,127 plane waves), 512 bands, f = 2, Spencer-Alavi kernel: all
+131,328 unique band pairs per step.  The same 96^3 / 512-band apply in the
+mixed form (complex64 transforms, erfc kernel, omega = 0.106) is measured too
+and reported under "mixed32".  Inputs are seeded synthetic orbitals.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "band pairs/s for Vx·ψ at 96³/512 bands, FP32 vs FP64 form; HBM % of peak"
+UNIT = "band pairs/s"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP64 rate of GB300 from its unit counts: 1.25 TFLOP/s nominal at the 2070 MHz
+# maximum SM clock, i.e. 604 FP64 flops per clock over the 152 SMs (2 FMA per SM
+# per clock).
+FP64_FLOPS_PER_CLK = 1.25e12 / 2.070e9
+
+
+def workload(name):
+    from paper_1305_7313_gb300.workloads import WORKLOADS
+    return dict(WORKLOADS[name], name=name)
+
+
+def make_inputs(w, miller):
+    from paper_1305_7313_gb300 import synth
+    from paper_1305_7313_gb300.workloads import cubic_cell
+    cell = cubic_cell(w["L"])
+    c = synth.orbitals(miller, cell, w["nb"], w["seed"])
+    occ = np.full(w["nb"], 2.0)
+    return cell, c, occ
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle samples while the timed region runs."""
+
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.proc = None
+        self.device_id = device_id
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device_id), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[4 + k].lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_id():
+    import torch
+    try:
+        return str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        return "0"
+
+
+def time_form(plan, psi, occ, steps, warmup, want_dex=False, rank=0, world=1):
+    """Warm up, then time `steps` applies between synchronised CUDA events."""
+    import torch
+    vpsi = torch.empty_like(psi)
+
+    def step():
+        if world == 1:
+            plan.apply(psi, occ, vpsi, True, want_dex)
+        else:
+            import torch.distributed as dist
+            plan.apply_shard(psi, occ, rank, world, vpsi, True, want_dex)
+            dist.all_reduce(vpsi)
+
+    for _ in range(warmup):
+        step()
+    plan.set_timing(True)
+    phase_ms = {}
+    launches = 0
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_id()) as clk:
+        start.record()
+        for _ in range(steps):
+            step()
+            st = plan.stats()
+            launches += st["launches"]
+            for k, v in st["phase_ms"].items():
+                phase_ms[k] = phase_ms.get(k, 0.0) + v
+        end.record()
+        torch.cuda.synchronize()
+    plan.set_timing(False)
+    ms = start.elapsed_time(end)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=psi.device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return dict(ms=ms, phase_ms=phase_ms, launches=launches, stats=plan.stats(), clocks=clk.summary())
+
+
+def roofline(form, plan, res, steps, peaks, peak_src):
+    """Roofline of the dominant pair kernel (the phase with the largest device time)."""
+    n = plan.grid[0]
+    ntot = float(n) ** 3
+    nc = 2 * (n // 2 + 1)
+    st = res["stats"]
+    pair_phases = ["pair_fwd", "pair_col", "pair_inv"]
+    dom = max(pair_phases, key=lambda k: res["phase_ms"].get(k, 0.0))
+    launches = st["phase_launches"][dom] * steps
+    ms_per_launch = res["phase_ms"][dom] / max(1, launches)
+    chains_per_launch = st["chains"] / max(1, st["phase_launches"][dom])
+    log2n = np.log2(n)
+    if form == "fp64":
+        # 5 n log2 n flops per complex line transform of length n; the plane passes
+        # do 2 N^2 lines, the column pass N (N+2) lines forward and as many inverse
+        per_chain = {"pair_fwd": 5 * ntot * 2 * log2n, "pair_inv": 5 * ntot * 2 * log2n,
+                     "pair_col": 2 * 5 * ntot * log2n * nc / n}[dom]
+        achieved = per_chain * chains_per_launch / (ms_per_launch * 1e-3) / 1e12
+        mhz = res["clocks"].get("sm_mhz") or 2070.0
+        peak = FP64_FLOPS_PER_CLK * 2070.0e6 / 1e12
+        return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_src": "nominal FP64 at 2070 MHz",
+                "frac_at_sampled_clock": achieved / (FP64_FLOPS_PER_CLK * mhz * 1e6 / 1e12),
+                "ms_per_launch": ms_per_launch, "chains_per_launch": chains_per_launch}
+    # complex64 half-spectrum buffer traffic: written once by pair_fwd, read and
+    # written by pair_col, read once by pair_inv
+    hbytes = n * n * nc * 8.0
+    per_chain = {"pair_fwd": hbytes, "pair_col": 2 * hbytes, "pair_inv": hbytes}[dom]
+    achieved = per_chain * chains_per_launch / (ms_per_launch * 1e-3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_src": peak_src + " (hbm copy)",
+            "ms_per_launch": ms_per_launch, "chains_per_launch": chains_per_launch}
+
+
+def cpu_baseline(w, nbands_sample=32):
+    """The FP64 oracle on the first `nbands_sample` bands of the workload."""
+    import oracle
+    from paper_1305_7313_gb300 import synth
+    from paper_1305_7313_gb300.workloads import cubic_cell
+    n = w["N"]
+    cell = cubic_cell(w["L"])
+    mill, _ = oracle.gsphere((n, n, n), cell, w["ecut"])
+    c = synth.orbitals(mill, cell, w["nb"], w["seed"])[:nbands_sample]
+    occ = np.full(nbands_sample, 2.0)
+    kind = "spencer_alavi" if w["kernel"] == 0 else "erfc"
+    t0 = time.perf_counter()
+    oracle.fock_apply(c, occ, mill, (n, n, n), cell, kind, w["omega"])
+    dt = time.perf_counter() - t0
+    pairs = nbands_sample * (nbands_sample + 1) // 2
+    return {"value": pairs / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "oracle fock_apply (V_x psi and E_x) of the first %d bands of the %s workload "
+                      "(%d unique pairs, %.1f s)" % (nbands_sample, w["name"], pairs, dt),
+            "seconds": dt}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    w = workload("gamma_fp64_L27_N96_nb512")
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        vals.append(cpu_baseline(w, args.ref_bands))
+    timed = vals[args.warmup:]
+    v = statistics.median(x["value"] for x in timed)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.median(x["seconds"] for x in timed),
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w["name"], "grid": 96, "L_bohr": 27.0, "ecut_ha": 12.0,
+                       "nbands": 512, "pairs": 131328},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": timed[0]["cores"], "kind": "oracle",
+                             "sample": timed[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fock", choices=["fock", "reference"])
+    ap.add_argument("--workload", default="gamma_fp64_L27_N96_nb512")
+    ap.add_argument("--mixed-workload", default="gamma_mixed32_erfc_L27_N96_nb512")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-bands", type=int, default=32)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1305_7313_gb300 import FockPlan, PREC_FP64, PREC_MIXED32
+    peaks, peak_src = load_peaks()
+
+    # ---- FP64 form (the headline workload)
+    w = workload(args.workload)
+    n = w["N"]
+    from paper_1305_7313_gb300.workloads import cubic_cell
+    plan = FockPlan(n, cubic_cell(w["L"]), w["ecut"], w["kernel"], w["omega"], w["prec"])
+    cell, c, occ = make_inputs(w, plan.miller)
+    psi = torch.from_numpy(c).cuda()
+    pairs = w["nb"] * (w["nb"] + 1) // 2
+    res = time_form(plan, psi, occ, args.steps, args.warmup, rank=rank, world=world)
+    ms_step = res["ms"] / args.steps
+    value = pairs * args.steps / (res["ms"] * 1e-3)
+    form = "fp64" if w["prec"] == PREC_FP64 else "mixed32"
+    roof = roofline(form, plan, res, args.steps, peaks, peak_src)
+
+    # ---- end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e and world == 1:
+        host = torch.from_numpy(c).pin_memory()
+        out = torch.empty(host.shape, dtype=host.dtype, pin_memory=True)
+        plan.apply_host(host, occ, out)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.apply_host(host, occ, out)
+        dt = time.perf_counter() - t0
+        nbytes = host.numel() * host.element_size()
+        e2e = {"value": pairs * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": nbytes + 8 * w["nb"],
+               "d2h_bytes_per_step": nbytes + 16, "ms_per_step": 1e3 * dt / args.steps}
+        del host, out
+    del psi
+    plan.close()
+    torch.cuda.empty_cache()
+
+    # ---- mixed form, same 96^3 / 512-band shape
+    mixed = None
+    if not args.no_mixed:
+        wm = workload(args.mixed_workload)
+        planm = FockPlan(wm["N"], cubic_cell(wm["L"]), wm["ecut"], wm["kernel"], wm["omega"], wm["prec"])
+        _, cm, occm = make_inputs(wm, planm.miller)
+        psim = torch.from_numpy(cm).cuda()
+        resm = time_form(planm, psim, occm, args.steps, args.warmup, rank=rank, world=world)
+        pm = wm["nb"] * (wm["nb"] + 1) // 2
+        mixed = {"workload": wm["name"], "value": pm * args.steps / (resm["ms"] * 1e-3), "unit": UNIT,
+                 "ms_per_step": resm["ms"] / args.steps, "dtype": "f32",
+                 "roofline": roofline("mixed32", planm, resm, args.steps, peaks, peak_src),
+                 "phase_ms_per_step": {k: v / args.steps for k, v in resm["phase_ms"].items()},
+                 "gpu_launches": resm["launches"], "clocks": resm["clocks"]}
+        planm.close()
+        del psim
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(w, args.ref_bands)
+        cpu.pop("seconds", None)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f64" if form == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "grid": n, "L_bohr": w["L"], "ecut_ha": w["ecut"],
+                   "nbands": w["nb"], "pairs": pairs, "npw": plan.npw,
+                   "kernel": "spencer_alavi" if w["kernel"] == 0 else "erfc",
+                   "l2": "inputs larger than L2 (psi_G %.0f MB, real-space orbitals and accumulators "
+                         "%.1f GB each)" % (c.nbytes / 1e6, w["nb"] * n**3 * (8 if form == "fp64" else 4) / 1e9),
+                   "parallelism": "pair-triangle shards + all-reduce" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
+        "phase_ms_per_step": {k: v / args.steps for k, v in res["phase_ms"].items()},
+        "mixed32": mixed,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

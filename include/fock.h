@@ -1,0 +1,220 @@
+/*
+ * fock.h — C ABI of the GB300 Fock exact-exchange library (libfockx.so).
+ *
+ * The library applies the Fock exact-exchange operator of hybrid-functional
+ * plane-wave DFT to a set of Gamma-point orbitals and returns the exchange
+ * energy (arXiv:1305.7313, §4 "The Exact Exchange (EXX) within the planewave
+ * method": the reciprocal-space E_x equation, the V_x|u_i> equation and the
+ * paragraph on overlap charge densities computed by FFT):
+ *
+ *   psi_i(r)        = Omega^-1/2 sum_{G in S} c_i(G) exp(i G.r)
+ *   phi_ij(r)       = IFFT[ v(G) FFT(psi_i* psi_j) ](r)
+ *   (V_x psi_j)(r)  = - sum_i f_i psi_i(r) phi_ij(r)
+ *   (V_x psi_j)(G)  = (sqrt(Omega)/Ntot) FFT(V_x psi_j)(G),   G in S
+ *   E_x             = -(Omega/2) sum_{i,j} f_i f_j sum_G v(G) |FFT(psi_i* psi_j)(G)/Ntot|^2
+ *                   = 1/2 sum_j f_j <psi_j | V_x psi_j>
+ *
+ * Units are Hartree atomic units (bohr, Ha).  FFT is the unnormalised forward
+ * transform with exp(-i G.r); IFFT carries 1/Ntot; Ntot = N1 N2 N3.
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a fock_status; nothing is thrown and nothing exits.
+ *    fock_last_error(plan) gives a one-line description of the last failure.
+ *  - "device" pointers are CUDA global-memory pointers of the current device;
+ *    "host" pointers are ordinary CPU memory.  The caller owns every buffer it
+ *    passes; the library never frees or keeps them past the call.
+ *  - The plan owns its tables and a workspace that grows on demand (or via
+ *    fock_plan_reserve).  One plan must not be used by two calls at the same
+ *    time (host threads or overlapping streams): they share the workspace.
+ *  - Work is ordered on the given stream (a cudaStream_t passed as void*;
+ *    NULL = the legacy default stream).  A call returns after queueing its
+ *    kernels unless it must hand a value back in host memory (ex, dex or the
+ *    pair energies), in which case it synchronises that stream first.
+ *  - Inputs are never modified.
+ */
+#ifndef FOCK_H
+#define FOCK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fock_plan* fock_plan_t;
+typedef void* fock_stream_t; /* a cudaStream_t */
+
+typedef enum {
+  FOCK_OK = 0,
+  FOCK_ERR_INVALID_ARG = 1,      /* a NULL pointer, a non-positive size, a bad enum, ... */
+  FOCK_ERR_UNSUPPORTED_SIZE = 2, /* grid not cubic, N not 2^a 3^b, or too large for the kernels */
+  FOCK_ERR_GRID_TOO_SMALL = 3,   /* the G-sphere does not fit on the FFT grid (2|m_a| >= N_a) */
+  FOCK_ERR_OOM = 4,              /* device allocation failed */
+  FOCK_ERR_CUDA = 5,             /* a CUDA runtime call or a kernel launch failed */
+  FOCK_ERR_TIMEOUT = 6           /* a bounded device-side wait gave up */
+} fock_status;
+
+typedef enum {
+  /* Spencer-Alavi spherical truncation: v(G) = 4 pi (1 - cos(|G| Rc)) / |G|^2,
+   * v(0) = 2 pi Rc^2, Rc = (3 Omega / 4 pi)^(1/3).  No parameters. */
+  FOCK_KERNEL_SPENCER_ALAVI = 0,
+  /* erfc screening: v(G) = 4 pi (1 - exp(-|G|^2 / 4 w^2)) / |G|^2, v(0) = pi / w^2.
+   * kparams = {w} (bohr^-1, > 0). */
+  FOCK_KERNEL_ERFC = 1
+} fock_kernel;
+
+typedef enum {
+  /* Everything in FP64: transforms, products, accumulators, energies. */
+  FOCK_PREC_FP64 = 0,
+  /* complex64 transforms and FP32 pair products / V_x psi accumulation; the
+   * kernel terms of the smallest |G| (|m|^2 <= 3) and every energy sum in FP64. */
+  FOCK_PREC_MIXED32 = 1
+} fock_precision;
+
+/* Orbitals are Gamma-point real functions: c(-G) = c(G)*.  Required. */
+#define FOCK_GAMMA_REAL 1u
+
+/*
+ * fock_plan_create — build the plane-wave sphere, the Coulomb-kernel table and
+ * the FFT plan for one cell.
+ *   out      host; receives the new plan (set to NULL on failure).
+ *   grid     host int[3]; FFT grid N1, N2, N3.  Must be cubic (N1 = N2 = N3)
+ *            with N one of the compiled sizes 8, 12, 16, 24, 32, 36, 48, 64,
+ *            72, 96 (other N: UNSUPPORTED_SIZE).
+ *   cell     host double[9]; rows a1, a2, a3 of the cell in bohr (any
+ *            non-degenerate lattice).
+ *   ecut_ha  plane-wave cutoff in Ha: S = {G : |G|^2 / 2 <= ecut_ha}.
+ *   kind, kparams, nkparams   Coulomb kernel and its parameters (see fock_kernel).
+ *   prec     arithmetic of the apply (see fock_precision).
+ *   flags    must contain FOCK_GAMMA_REAL.
+ * The sphere's canonical order: ascending FP64 |G|^2, ties broken
+ * lexicographically on the Miller indices (m1, m2, m3); |G|^2 is evaluated as
+ * G_x = (m1 b1x + m2 b2x) + m3 b3x (same for y, z), |G|^2 = (Gx^2 + Gy^2) + Gz^2,
+ * with b_i = (2 pi / Omega) (a_j x a_k), Omega = a1 . (a2 x a3), no fused
+ * multiply-add anywhere.
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, GRID_TOO_SMALL, OOM, CUDA.
+ */
+fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double cell[9],
+                             double ecut_ha, fock_kernel kind, const double* kparams,
+                             int nkparams, fock_precision prec, unsigned flags);
+
+/*
+ * fock_gsphere — the plane-wave sphere of a cell without creating a plan (host
+ * only, no GPU needed): the same list, in the same canonical order, that
+ * fock_plan_create builds.
+ *   grid, cell, ecut_ha   as in fock_plan_create (the grid is used only for the
+ *                         GRID_TOO_SMALL check).
+ *   npw      host int64; receives the number of plane waves.
+ *   miller   host int32 [capacity][3] or NULL; receives the Miller indices
+ *            when capacity >= npw (call once with NULL to size the buffer).
+ * Errors: INVALID_ARG, GRID_TOO_SMALL, and INVALID_ARG when miller is not NULL
+ * but capacity < npw.
+ */
+fock_status fock_gsphere(const int grid[3], const double cell[9], double ecut_ha, int64_t* npw,
+                         int32_t* miller, int64_t capacity);
+
+/* Number of plane waves npw in the sphere.  npw: host int64. */
+fock_status fock_plan_npw(fock_plan_t plan, int64_t* npw);
+
+/* Miller indices of the sphere in canonical order.  miller: host int32[npw][3]. */
+fock_status fock_plan_gvectors(fock_plan_t plan, int32_t* miller);
+
+/* Grow the workspace now for up to nb_max bands (otherwise the first apply
+ * grows it).  Errors: INVALID_ARG, OOM. */
+fock_status fock_plan_reserve(fock_plan_t plan, int nb_max);
+
+/* Number of band-pair chains (two pairs per complex transform) each launch of
+ * the pair passes processes; sets the size of the plan's transform buffer
+ * (chain_batch x N^2 (N+2) complex elements).  The default targets 120 MiB.
+ * Takes effect at the next call.  Errors: INVALID_ARG. */
+fock_status fock_plan_set_batch(fock_plan_t plan, int chain_batch);
+
+/* Phases of a call, for fock_plan_stats. */
+enum {
+  FOCK_PHASE_TO_REAL = 0,   /* G-sphere scatter + inverse 3D FFT of the orbitals */
+  FOCK_PHASE_PAIR_FWD = 1,  /* pair products + forward plane FFTs */
+  FOCK_PHASE_PAIR_COL = 2,  /* column FFTs, kernel multiply, energy partials, inverse */
+  FOCK_PHASE_PAIR_INV = 3,  /* inverse plane FFTs + V_x psi accumulation */
+  FOCK_PHASE_TO_SPHERE = 4, /* forward 3D FFT of V_x psi + gather to the sphere */
+  FOCK_PHASE_ENERGY = 5,    /* E_x reduction */
+  FOCK_NPHASES = 6
+};
+
+typedef struct {
+  int64_t launches;                   /* kernels the last call launched */
+  int64_t phase_launches[FOCK_NPHASES];
+  double phase_ms[FOCK_NPHASES];      /* device time per phase of the last call (timing on), else 0 */
+  int64_t chains;                     /* pair chains the last call processed */
+  int64_t pairs;                      /* unique pairs the last call processed */
+  int chain_batch;                    /* chains per launch of the pair passes */
+  int band_batch;                     /* bands per launch of the O(nb) transforms */
+} fock_stats;
+
+/* Time every launch with CUDA events on the call's stream (enable != 0).  A
+ * timed call synchronises its stream before returning.  Errors: INVALID_ARG, CUDA. */
+fock_status fock_plan_set_timing(fock_plan_t plan, int enable);
+
+/* Counters and (with timing on) per-phase device times of the last call.
+ * stats: host.  Errors: INVALID_ARG. */
+fock_status fock_plan_stats(fock_plan_t plan, fock_stats* stats);
+
+/* Bytes of device memory the plan holds (tables + workspace).  bytes: host. */
+fock_status fock_plan_device_bytes(fock_plan_t plan, int64_t* bytes);
+
+/*
+ * fock_apply — V_x psi and E_x for nb orbitals (§4, V_x equation and E_x).
+ *   psi_G   device complex128 [nb][npw] (interleaved re, im), canonical order.
+ *   nb      number of orbitals, >= 1.
+ *   occ     host double [nb]; occupations f_i (any real values).
+ *   vpsi_G  device complex128 [nb][npw]; receives (V_x psi_j)(G).  Must not
+ *           overlap psi_G.
+ *   ex      host double or NULL; receives E_x.
+ *   dex     host double or NULL; receives dE_x/domega (erfc kernel; 0 for
+ *           Spencer-Alavi).
+ *   stream  cudaStream_t or NULL.
+ * Every unique pair i <= j is evaluated once (phi_ji = phi_ij for real
+ * orbitals); two pairs share one complex transform.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+fock_status fock_apply(fock_plan_t plan, const void* psi_G, int nb, const double* occ,
+                       void* vpsi_G, double* ex, double* dex, fock_stream_t stream);
+
+/*
+ * fock_apply_shard — one part of fock_apply's pair loop: the band-group
+ * distribution of §5 (Fig. 3: the band loop is split over groups and the
+ * results are summed at the end).  The unique pairs are cut, in the library's
+ * fixed schedule, into nshards contiguous parts of near-equal size; this call
+ * evaluates part `shard` (0 <= shard < nshards) and returns the partial
+ * V_x psi and partial E_x, dE_x/domega.  Summing the results of all shards
+ * reproduces fock_apply up to rounding.  Arguments as in fock_apply.
+ */
+fock_status fock_apply_shard(fock_plan_t plan, const void* psi_G, int nb, const double* occ,
+                             int shard, int nshards, void* vpsi_G, double* ex, double* dex,
+                             fock_stream_t stream);
+
+/*
+ * fock_pair_energies — the pair terms of the §4 E_x sum,
+ *   e_ij = sum_G v(G) |FFT(psi_i psi_j)(G)/Ntot|^2,   d_ij = the same with dv/domega,
+ * for an explicit list of pairs.
+ *   pairs   host int32 [npairs][2]; band indices (i, j), 0 <= i, j < nb.
+ *   e, d    host double [npairs]; d may be NULL.
+ * Synchronises the stream.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+fock_status fock_pair_energies(fock_plan_t plan, const void* psi_G, int nb, const int32_t* pairs,
+                               int npairs, double* e, double* d, fock_stream_t stream);
+
+/* Release the plan and everything it holds.  NULL is accepted. */
+fock_status fock_destroy(fock_plan_t plan);
+
+/* Static, never-NULL description of a status code. */
+const char* fock_status_string(fock_status s);
+
+/* Description of the last failure on this plan ("" if none); plan may be NULL
+ * for failures of fock_plan_create.  Valid until the next call on the plan. */
+const char* fock_last_error(fock_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FOCK_H */

@@ -1,0 +1,251 @@
+"""ctypes binding of libfockx.so: the C-ABI entry points of include/fock.h under
+the same names, with argument marshalling only.
+
+Device buffers are passed as torch CUDA tensors (complex128, contiguous); the
+binding hands their addresses and torch's current CUDA stream to the library.
+All computation happens in the library's CUDA kernels; when the library is not
+built this module raises instead of computing anything another way.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+SPENCER_ALAVI = 0
+ERFC = 1
+PREC_FP64 = 0
+PREC_MIXED32 = 1
+GAMMA_REAL = 1
+
+STATUS = {
+    0: "FOCK_OK",
+    1: "FOCK_ERR_INVALID_ARG",
+    2: "FOCK_ERR_UNSUPPORTED_SIZE",
+    3: "FOCK_ERR_GRID_TOO_SMALL",
+    4: "FOCK_ERR_OOM",
+    5: "FOCK_ERR_CUDA",
+    6: "FOCK_ERR_TIMEOUT",
+}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfockx.so")
+
+_lib = None
+
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_dbl_p = ctypes.POINTER(ctypes.c_double)
+_c_i32_p = ctypes.POINTER(ctypes.c_int32)
+_c_i64_p = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+
+NPHASES = 6
+PHASES = ("to_real", "pair_fwd", "pair_col", "pair_inv", "to_sphere", "energy")
+
+
+class FockStats(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_int64),
+        ("phase_launches", ctypes.c_int64 * NPHASES),
+        ("phase_ms", ctypes.c_double * NPHASES),
+        ("chains", ctypes.c_int64),
+        ("pairs", ctypes.c_int64),
+        ("chain_batch", ctypes.c_int),
+        ("band_batch", ctypes.c_int),
+    ]
+
+
+_SIGNATURES = {
+    "fock_plan_create": [ctypes.POINTER(_vp), _c_int_p, _c_dbl_p, ctypes.c_double, ctypes.c_int,
+                         _c_dbl_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint],
+    "fock_gsphere": [_c_int_p, _c_dbl_p, ctypes.c_double, _c_i64_p, _c_i32_p, ctypes.c_int64],
+    "fock_plan_npw": [_vp, _c_i64_p],
+    "fock_plan_gvectors": [_vp, _c_i32_p],
+    "fock_plan_reserve": [_vp, ctypes.c_int],
+    "fock_plan_set_batch": [_vp, ctypes.c_int],
+    "fock_plan_device_bytes": [_vp, _c_i64_p],
+    "fock_plan_set_timing": [_vp, ctypes.c_int],
+    "fock_plan_stats": [_vp, ctypes.POINTER(FockStats)],
+    "fock_apply": [_vp, _vp, ctypes.c_int, _c_dbl_p, _vp, _c_dbl_p, _c_dbl_p, _vp],
+    "fock_apply_shard": [_vp, _vp, ctypes.c_int, _c_dbl_p, ctypes.c_int, ctypes.c_int, _vp,
+                         _c_dbl_p, _c_dbl_p, _vp],
+    "fock_pair_energies": [_vp, _vp, ctypes.c_int, _c_i32_p, ctypes.c_int, _c_dbl_p, _c_dbl_p, _vp],
+    "fock_destroy": [_vp],
+    "fock_status_string": [ctypes.c_int],
+    "fock_last_error": [_vp],
+}
+
+
+class FockError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = int(status)
+        super().__init__("%s: %s" % (STATUS.get(self.status, str(status)), message))
+
+
+def load():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libfockx.so is not built; run `python -m paper_1305_7313_gb300.build` "
+                           "or __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, args in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name in ("fock_status_string", "fock_last_error") else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status, plan=None):
+    if status != 0:
+        msg = load().fock_last_error(plan).decode()
+        raise FockError(status, msg)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, name, shape=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.complex128 or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous complex128 tensor" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dbl_array(x):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    return a, a.ctypes.data_as(_c_dbl_p)
+
+
+def fock_status_string(status):
+    return load().fock_status_string(int(status)).decode()
+
+
+def fock_last_error(plan=None):
+    return load().fock_last_error(plan).decode()
+
+
+def fock_gsphere(grid, cell, ecut):
+    """Miller indices [npw, 3] (int32) of the sphere in canonical order (host only)."""
+    lib = load()
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    c, cp = _dbl_array(np.asarray(cell, dtype=np.float64).ravel())
+    n = ctypes.c_int64()
+    _check(lib.fock_gsphere(g, cp, float(ecut), ctypes.byref(n), None, 0))
+    out = np.empty((n.value, 3), dtype=np.int32)
+    _check(lib.fock_gsphere(g, cp, float(ecut), ctypes.byref(n), out.ctypes.data_as(_c_i32_p), n.value))
+    return out
+
+
+def fock_plan_create(grid, cell, ecut, kind=SPENCER_ALAVI, kparams=(), prec=PREC_FP64, flags=GAMMA_REAL):
+    """Create a plan; returns its handle (an int)."""
+    lib = load()
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    c, cp = _dbl_array(np.asarray(cell, dtype=np.float64).ravel())
+    kp, kpp = _dbl_array(list(kparams) if len(kparams) else [0.0])
+    h = ctypes.c_void_p()
+    _check(lib.fock_plan_create(ctypes.byref(h), g, cp, float(ecut), int(kind), kpp, len(kparams),
+                                int(prec), int(flags)))
+    return h.value
+
+
+def fock_plan_npw(plan):
+    n = ctypes.c_int64()
+    _check(load().fock_plan_npw(plan, ctypes.byref(n)), plan)
+    return n.value
+
+
+def fock_plan_gvectors(plan):
+    out = np.empty((fock_plan_npw(plan), 3), dtype=np.int32)
+    _check(load().fock_plan_gvectors(plan, out.ctypes.data_as(_c_i32_p)), plan)
+    return out
+
+
+def fock_plan_reserve(plan, nb_max):
+    _check(load().fock_plan_reserve(plan, int(nb_max)), plan)
+
+
+def fock_plan_set_batch(plan, chain_batch):
+    _check(load().fock_plan_set_batch(plan, int(chain_batch)), plan)
+
+
+def fock_plan_set_timing(plan, enable):
+    _check(load().fock_plan_set_timing(plan, 1 if enable else 0), plan)
+
+
+def fock_plan_stats(plan):
+    """Counters of the last call as a dict (per-phase device times need timing on)."""
+    s = FockStats()
+    _check(load().fock_plan_stats(plan, ctypes.byref(s)), plan)
+    return {
+        "launches": s.launches,
+        "phase_launches": dict(zip(PHASES, list(s.phase_launches))),
+        "phase_ms": dict(zip(PHASES, list(s.phase_ms))),
+        "chains": s.chains,
+        "pairs": s.pairs,
+        "chain_batch": s.chain_batch,
+        "band_batch": s.band_batch,
+    }
+
+
+def fock_plan_device_bytes(plan):
+    n = ctypes.c_int64()
+    _check(load().fock_plan_device_bytes(plan, ctypes.byref(n)), plan)
+    return n.value
+
+
+def fock_apply(plan, psi_G, occ, vpsi_G, want_ex=True, want_dex=False, stream=None):
+    """V_x psi into ``vpsi_G``; returns (E_x or None, dE_x/domega or None)."""
+    nb, npw = psi_G.shape
+    a = _dev_ptr(psi_G, "psi_G")
+    b = _dev_ptr(vpsi_G, "vpsi_G", (nb, npw))
+    o, op = _dbl_array(occ)
+    if o.shape != (nb,):
+        raise ValueError("occ must have one entry per band")
+    ex, dex = ctypes.c_double(), ctypes.c_double()
+    _check(load().fock_apply(plan, a, nb, op, b, ctypes.byref(ex) if want_ex else None,
+                             ctypes.byref(dex) if want_dex else None, _stream(stream)), plan)
+    return (ex.value if want_ex else None), (dex.value if want_dex else None)
+
+
+def fock_apply_shard(plan, psi_G, occ, shard, nshards, vpsi_G, want_ex=True, want_dex=False, stream=None):
+    """Part ``shard`` of ``nshards`` of the pair loop; returns the partial (E_x, dE_x/domega)."""
+    nb, npw = psi_G.shape
+    a = _dev_ptr(psi_G, "psi_G")
+    b = _dev_ptr(vpsi_G, "vpsi_G", (nb, npw))
+    o, op = _dbl_array(occ)
+    ex, dex = ctypes.c_double(), ctypes.c_double()
+    _check(load().fock_apply_shard(plan, a, nb, op, int(shard), int(nshards), b,
+                                   ctypes.byref(ex) if want_ex else None,
+                                   ctypes.byref(dex) if want_dex else None, _stream(stream)), plan)
+    return (ex.value if want_ex else None), (dex.value if want_dex else None)
+
+
+def fock_pair_energies(plan, psi_G, pairs, want_d=False, stream=None):
+    """e_ij (and d_ij) for the listed (i, j) pairs; numpy float64 arrays."""
+    nb = psi_G.shape[0]
+    a = _dev_ptr(psi_G, "psi_G")
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    e = np.empty(len(pr))
+    d = np.empty(len(pr))
+    _check(load().fock_pair_energies(plan, a, nb, pr.ctypes.data_as(_c_i32_p), len(pr),
+                                     e.ctypes.data_as(_c_dbl_p),
+                                     d.ctypes.data_as(_c_dbl_p) if want_d else None,
+                                     _stream(stream)), plan)
+    return (e, d) if want_d else e
+
+
+def fock_destroy(plan):
+    _check(load().fock_destroy(plan))

@@ -1,0 +1,237 @@
+// fft_core.cuh — batched mixed-radix (2, 3, 4, 8) Stockham FFT on lines held in
+// shared memory, specialised at compile time for one line length N.
+//
+// The 3D FFTs of the Fock apply (orbitals to real space, pair densities to G
+// space and back, V_x psi back to G space; §4 of the paper computes all of
+// them "via Fast Fourier Transform") are done as one pass over planes and one
+// pass over columns.  Inside a pass, every CTA owns whole lines in shared
+// memory and runs the Stockham autosort recursion on them:
+//
+//   stage (radix R, P = product of the radices of the earlier stages):
+//     for every butterfly b in [0, N/R):  k = b mod P
+//       x_r = in[b + r N/R] * w_N^(SIGN r k N/(PR)),   r = 0..R-1
+//       y   = DFT_R(x)                                  (exp(SIGN 2 pi i r q / R))
+//       out[(b - k) R + k + q P] = y_q,                 q = 0..R-1
+//
+// which leaves the result in natural order after the last stage.  A stage is
+// done in place: each thread loads all its butterfly inputs into registers,
+// the CTA synchronises, then the outputs are written back.
+//
+// Thread mapping: thread `tid` works on line (tid mod NLINES) as sub-thread
+// (tid / NLINES) of TL sub-threads per line; consecutive threads therefore
+// touch consecutive lines, which keeps shared-memory accesses conflict-free
+// when lines are contiguous (column FFTs) or when the line stride is odd
+// (row FFTs with a padded stride).  Sub-thread t owns butterflies t, t + TL, ...
+// of every stage, so it holds N / TL elements between the two barriers.
+//
+// Twiddles come from a table w[t] = exp(-2 pi i t / N), t < N, computed on the
+// host in FP64 and staged in shared memory; SIGN = +1 uses its conjugate.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace fockx {
+
+constexpr int kMaxStages = 8;
+constexpr int kMaxThreads = 1024;
+constexpr int kEmax = 24;  // elements a thread may hold across a stage
+
+struct RadixPlan {
+  int nst;                 // number of stages
+  int r[kMaxStages];       // radices, in stage order
+  int tl_plane;            // sub-threads per line, plane passes (N lines)
+  int tl_colh;             // sub-threads per line, half-spectrum column pass (2(N/2+1) lines)
+};
+
+__host__ __device__ constexpr int cgcd(int a, int b) {
+  while (b != 0) {
+    const int t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+__host__ __device__ constexpr int best_tl(int n, const int* r, int nst, int nlines) {
+  int g = 0;
+  for (int s = 0; s < nst; ++s) g = cgcd(g, n / r[s]);
+  for (int t = g; t >= 1; --t)
+    if (g % t == 0 && n / t <= kEmax && nlines * t <= kMaxThreads) return t;
+  return 0;
+}
+
+// Fewest stages first, then the most threads per line.
+__host__ __device__ constexpr RadixPlan make_radix_plan(int n) {
+  int a = 0, b = 0, m = n;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  while (m % 3 == 0) { m /= 3; ++b; }
+  RadixPlan best{};
+  best.nst = 0;
+  if (m != 1) return best;
+  int best_score = 1 << 30;
+  for (int n8 = 0; 3 * n8 <= a; ++n8) {
+    for (int n4 = 0; 3 * n8 + 2 * n4 <= a; ++n4) {
+      const int n2 = a - 3 * n8 - 2 * n4;
+      if (n8 + n4 + n2 + b > kMaxStages) continue;
+      RadixPlan p{};
+      p.nst = 0;
+      for (int i = 0; i < n8; ++i) p.r[p.nst++] = 8;
+      for (int i = 0; i < n4; ++i) p.r[p.nst++] = 4;
+      for (int i = 0; i < n2; ++i) p.r[p.nst++] = 2;
+      for (int i = 0; i < b; ++i) p.r[p.nst++] = 3;
+      p.tl_plane = best_tl(n, p.r, p.nst, n);
+      p.tl_colh = best_tl(n, p.r, p.nst, 2 * (n / 2 + 1));
+      if (p.tl_plane == 0 || p.tl_colh == 0) continue;
+      const int score = p.nst * 4096 - p.tl_plane;
+      if (score < best_score) {
+        best_score = score;
+        best = p;
+      }
+    }
+  }
+  return best;
+}
+
+template <class T> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+template <class T> using cplx = typename CplxOf<T>::type;
+
+template <class T>
+__device__ __forceinline__ cplx<T> cmake(T x, T y) {
+  cplx<T> r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+template <class C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <class C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <class C> __device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+// S * i * a for S = +1 or -1
+template <int S, class C> __device__ __forceinline__ C cmul_si(C a) {
+  C r;
+  r.x = S > 0 ? -a.y : a.y;
+  r.y = S > 0 ? a.x : -a.x;
+  return r;
+}
+
+// In-register DFTs, y_q = sum_r x_r exp(SIGN 2 pi i r q / R).
+template <int SIGN, class T> struct Dft {
+  using C = cplx<T>;
+  static __device__ __forceinline__ void r2(C* x) {
+    C a = x[0];
+    x[0] = cadd(a, x[1]);
+    x[1] = csub(a, x[1]);
+  }
+  static __device__ __forceinline__ void r3(C* x) {
+    const T h = T(SIGN) * T(0.86602540378443864676372317075293618);  // sin(2 pi / 3)
+    C s = cadd(x[1], x[2]);
+    C d = csub(x[1], x[2]);
+    C m = cmake<T>(x[0].x - T(0.5) * s.x, x[0].y - T(0.5) * s.y);
+    C u = cmake<T>(-h * d.y, h * d.x);
+    x[0] = cadd(x[0], s);
+    x[1] = cadd(m, u);
+    x[2] = csub(m, u);
+  }
+  static __device__ __forceinline__ void r4v(C& x0, C& x1, C& x2, C& x3) {
+    C a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = cmul_si<SIGN>(csub(x1, x3));
+    x0 = cadd(a, c);
+    x2 = csub(a, c);
+    x1 = cadd(b, d);
+    x3 = csub(b, d);
+  }
+  static __device__ __forceinline__ void r4(C* x) { r4v(x[0], x[1], x[2], x[3]); }
+  static __device__ __forceinline__ void r8(C* x) {
+    const T c = T(0.70710678118654752440084436210484904);  // cos(pi / 4)
+    C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+    C o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+    r4v(e0, e1, e2, e3);
+    r4v(o0, o1, o2, o3);
+    // o_q *= exp(SIGN 2 pi i q / 8)
+    C t1 = cmake<T>(c * (o1.x - T(SIGN) * o1.y), c * (o1.y + T(SIGN) * o1.x));
+    C t2 = cmul_si<SIGN>(o2);
+    C t3 = cmake<T>(-c * (o3.x + T(SIGN) * o3.y), c * (T(SIGN) * o3.x - o3.y));
+    x[0] = cadd(e0, o0);
+    x[4] = csub(e0, o0);
+    x[1] = cadd(e1, t1);
+    x[5] = csub(e1, t1);
+    x[2] = cadd(e2, t2);
+    x[6] = csub(e2, t2);
+    x[3] = cadd(e3, t3);
+    x[7] = csub(e3, t3);
+  }
+  template <int R> static __device__ __forceinline__ void run(C* x) {
+    if constexpr (R == 2) r2(x);
+    else if constexpr (R == 3) r3(x);
+    else if constexpr (R == 4) r4(x);
+    else r8(x);
+  }
+};
+
+// One Stockham stage on one line (base, element stride ES) for sub-thread t of TL.
+template <class T, int N, int R, int P, int TL, int ES, int SIGN>
+__device__ __forceinline__ void fft_stage(cplx<T>* base, int t, bool active, const cplx<T>* tw) {
+  using C = cplx<T>;
+  constexpr int NB = N / R;
+  constexpr int PER = NB / TL;
+  constexpr int TWS = N / (P * R);
+  C x[PER][R];
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int b = t + TL * k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[k][r] = base[(b + r * NB) * ES];
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int b = t + TL * k;
+      const int kk = b % P;
+      if (P > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          C w = tw[r * kk * TWS];
+          if (SIGN > 0) w.y = -w.y;
+          x[k][r] = cmul(x[k][r], w);
+        }
+      }
+      Dft<SIGN, T>::template run<R>(x[k]);
+      const int j = (b - kk) * R + kk;
+#pragma unroll
+      for (int q = 0; q < R; ++q) base[(j + q * P) * ES] = x[k][q];
+    }
+  }
+  __syncthreads();
+}
+
+template <class T, int N, int SIGN, int TL, int ES, int S, int P>
+__device__ __forceinline__ void fft_stages(cplx<T>* base, int t, bool active, const cplx<T>* tw) {
+  constexpr RadixPlan pl = make_radix_plan(N);
+  if constexpr (S < pl.nst) {
+    constexpr int R = pl.r[S];
+    fft_stage<T, N, R, P, TL, ES, SIGN>(base, t, active, tw);
+    fft_stages<T, N, SIGN, TL, ES, S + 1, P * R>(base, t, active, tw);
+  }
+}
+
+// FFT of NLINES lines of length N in shared memory: line l starts at buf + l*LS,
+// its elements are ES apart.  Every thread of the CTA must call this (it
+// synchronises); threads with tid >= NLINES*TL idle.
+template <class T, int N, int SIGN, int NLINES, int TL, int LS, int ES>
+__device__ __forceinline__ void fft_lines(cplx<T>* buf, const cplx<T>* tw) {
+  const int tid = threadIdx.x;
+  const int line = tid % NLINES;
+  const int t = tid / NLINES;
+  const bool active = t < TL;
+  fft_stages<T, N, SIGN, TL, ES, 0, 1>(buf + line * LS, t, active, tw);
+}
+
+}  // namespace fockx

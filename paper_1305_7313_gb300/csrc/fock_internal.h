@@ -1,0 +1,69 @@
+// fock_internal.h — what the host plan (fock_plan.cpp) and the kernel
+// translation units (fock_kernels_f64.cu, fock_kernels_f32.cu) share.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+
+namespace fockx {
+
+// Two band pairs that share one complex transform: pair a = (ai, aj) in the
+// real part, pair b = (bi, bj) in the imaginary part (bi < 0: no pair b).
+// pa / pb index the per-pair energy slots.
+struct Chain {
+  int ai, aj, bi, bj;
+  int pa, pb;
+  int pad0, pad1;
+};
+
+// Everything a kernel needs to know about a plan (device pointers included).
+struct DevPlan {
+  int n;            // cubic grid N
+  int k3h;          // N/2 + 1: stored half of the last axis
+  int64_t ntot;     // N^3
+  int64_t hsize;    // elements of one half-spectrum pair buffer: N * N * 2 * k3h
+  int npw;
+  const int* gidx;     // [npw] grid offset of G
+  const int* gidxneg;  // [npw] grid offset of -G
+  const void* tw;      // [N] exp(-2 pi i t / N) in the working precision
+  const void* vtab;    // [N][N][k3h] v(G) / Ntot in the working precision
+  const double* vtab64;   // [N][N][k3h] v(G) in FP64
+  const double* dvtab64;  // [N][N][k3h] dv/domega in FP64 (NULL: not needed)
+  double inv_ntot;     // 1 / Ntot
+  double psi_scale;    // 1 / sqrt(Omega)
+  double out_scale;    // sqrt(Omega) / Ntot
+  int msmall2;         // |m|^2 at or below which kernel terms are done in FP64 (mixed form)
+};
+
+struct KernelOps {
+  int real_bytes;  // sizeof of the working real type
+  int n;           // grid size these kernels are compiled for
+  size_t smem;     // largest dynamic shared memory of its kernels
+  cudaError_t (*configure)(const DevPlan&);
+  // c(G) of bands [band0, band0 + nbat) to psi(r); X is scratch of >= ceil(nbat/2) grids.
+  cudaError_t (*to_real)(const DevPlan&, const double2* psiG, int nb, int band0, int nbat, void* X,
+                         void* psi, cudaStream_t);
+  // Forward plane pass of the pair densities of `nch` chains into H.
+  cudaError_t (*pair_fwd)(const DevPlan&, const void* psi, const Chain* ch, int nch, void* H,
+                          cudaStream_t);
+  // Column pass: forward, times v, energy partials, inverse.
+  cudaError_t (*pair_col)(const DevPlan&, void* H, const Chain* ch, int nch, double* epair,
+                          double* dpair, cudaStream_t);
+  // Inverse plane pass and W -= f psi phi accumulation.
+  cudaError_t (*pair_inv)(const DevPlan&, const void* psi, void* W, const void* occ,
+                          const Chain* ch, int nch, const void* H, cudaStream_t);
+  // W(r) of bands [band0, band0 + nbat) to (V_x psi)(G) on the sphere.
+  cudaError_t (*to_sphere)(const DevPlan&, const void* W, int nb, int band0, int nbat, void* X,
+                           double2* vpsiG, cudaStream_t);
+};
+
+// Kernels for grid size n and precision (0: FP64, 1: mixed); NULL if not built.
+const KernelOps* find_kernel_ops(int prec, int n);
+
+// E = scale * sum_p f_i f_j (1 or 2) e_p over the pairs; out[0] = E, out[1] = dE.
+cudaError_t launch_energy_reduce(const int2* pairs, int npairs, const double* occ,
+                                 const double* epair, const double* dpair, double scale,
+                                 double* out, cudaStream_t s);
+
+}  // namespace fockx

@@ -1,0 +1,439 @@
+// fock_kernels.cuh — the CUDA kernels of the Gamma-point Fock apply, templated
+// on the working real type T (double: FP64 form; float: mixed form).
+//
+// Data layout in HBM (all row-major, last index fastest):
+//   psi  [nb][N][N][N]  real T      orbitals in real space, psi(r) of §4
+//   W    [nb][N][N][N]  real T      accumulators of V_x psi_j(r)
+//   H    [chain][N][N][2][N/2+1]    complex T: per plane i1 and row k2, the
+//        stored half (k3 <= N/2) of the 2D transforms of the two pair densities
+//        of a chain (index 0: pair a, 1: pair b)
+//   X    [q][N][N][N]   complex T   full grids for the O(nb) transforms
+//
+// Hot path per chain of two pairs (a = (ai, aj), b = (bi, bj)):
+//   pair_fwd  (plane i1):  z = psi_ai psi_aj + i psi_bi psi_bj, 2D FFT over
+//             (i2, i3), split z = A + iB by Hermitian symmetry (A, B are the
+//             transforms of real planes), store the k3 <= N/2 half of A and B.
+//   pair_col  (row k2):    FFT along i1 of every stored column, energy partials
+//             sum w(k3) v |A|^2 and sum w(k3) v |B|^2 (w = 1 on the k3 = 0, N/2
+//             planes, 2 elsewhere: the k3 > N/2 half is the mirror image), times
+//             v/Ntot, inverse FFT along k1.
+//   pair_inv  (plane i1):  rebuild z = A + iB over the whole plane from the
+//             stored half, inverse 2D FFT -> phi_a + i phi_b, then
+//             W_aj -= f_ai psi_ai phi_a, W_ai -= f_aj psi_aj phi_a (i != j), same for b.
+#pragma once
+
+#include "fft_core.cuh"
+#include "fock_internal.h"
+
+namespace fockx {
+
+__device__ __forceinline__ int freq_of(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
+
+template <class T> __device__ __forceinline__ void atomic_add_real(T* p, T v) { atomicAdd(p, v); }
+
+// Sum of four doubles over the CTA; the result is valid in thread 0.
+__device__ inline void block_sum4(double v[4], double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[warp * 4 + k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += red[w * 4 + k];
+      v[k] = s;
+    }
+  }
+}
+
+// Compile-time geometry of the passes for grid size N.
+template <class T, int N>
+struct Geo {
+  using C = cplx<T>;
+  static constexpr RadixPlan pl = make_radix_plan(N);
+  static_assert(pl.nst > 0, "grid size must be 2^a 3^b and fit the FFT kernels");
+  static constexpr int KH = N / 2 + 1;                    // stored half of the last axis
+  static constexpr int NC = 2 * KH;                       // stored columns per row (A and B)
+  static constexpr int RP = (N % 2 == 0) ? N + 1 : N;     // odd padded row stride of a plane
+  static constexpr int TLP = pl.tl_plane;
+  static constexpr int TLC = pl.tl_colh;
+  // CTA sizes rounded up to whole warps (the extra threads idle in the FFT
+  // stages), so warp shuffles always see 32 live lanes
+  static constexpr int THR_PLANE = (N * TLP + 31) / 32 * 32;
+  static constexpr int THR_COLH = (NC * TLC + 31) / 32 * 32;
+  static constexpr int THR_COLF = (N * TLP + 31) / 32 * 32;
+  static_assert(THR_PLANE <= 1024 && THR_COLH <= 1024, "CTA too large");
+  static constexpr size_t SMEM_PLANE = sizeof(C) * (size_t)(N * RP + N);
+  static constexpr size_t SMEM_COLH = sizeof(C) * (size_t)(N * NC + N) + 32 * 4 * sizeof(double);
+  static constexpr size_t SMEM_COLF = sizeof(C) * (size_t)(N * N + N);
+};
+
+template <class T>
+__device__ __forceinline__ void load_twiddles(cplx<T>* tw, const DevPlan& g) {
+  const cplx<T>* src = static_cast<const cplx<T>*>(g.tw);
+  for (int t = threadIdx.x; t < g.n; t += blockDim.x) tw[t] = src[t];
+}
+
+// ---------------------------------------------------------------- O(nb) passes
+
+// X[q] = scatter(c_{b0} + i c_{b0+1}) for band pairs q of the batch (X zeroed before).
+template <class T>
+__global__ void k_scatter(DevPlan g, const double2* __restrict__ psiG, int nb, int band0, int nbat,
+                          cplx<T>* __restrict__ X) {
+  const int q = blockIdx.y;
+  const int b0 = band0 + 2 * q;
+  const bool has1 = (2 * q + 1 < nbat) && (b0 + 1 < nb);
+  cplx<T>* Xq = X + (int64_t)q * g.ntot;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.npw; k += gridDim.x * blockDim.x) {
+    const double2 c0 = psiG[(int64_t)b0 * g.npw + k];
+    const double2 c1 = has1 ? psiG[(int64_t)(b0 + 1) * g.npw + k] : make_double2(0.0, 0.0);
+    Xq[g.gidx[k]] = cmake<T>(T(c0.x - c1.y), T(c0.y + c1.x));
+  }
+}
+
+// FFT along i1 of the slab X[q][:, i2, :] (all N columns).
+template <class T, int N, int SIGN>
+__global__ void __launch_bounds__(Geo<T, N>::THR_COLF) k_col_full(DevPlan g, cplx<T>* __restrict__ X) {
+  using C = cplx<T>;
+  using G = Geo<T, N>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* S = reinterpret_cast<C*>(smem_raw);
+  C* tw = S + N * N;
+  const int i2 = blockIdx.x;
+  C* Xq = X + (int64_t)blockIdx.y * g.ntot;
+  load_twiddles<T>(tw, g);
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i1 = e / N, i3 = e - i1 * N;
+    S[e] = Xq[((int64_t)i1 * N + i2) * N + i3];
+  }
+  __syncthreads();
+  fft_lines<T, N, SIGN, N, G::TLP, 1, N>(S, tw);
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i1 = e / N, i3 = e - i1 * N;
+    Xq[((int64_t)i1 * N + i2) * N + i3] = S[e];
+  }
+}
+
+// 2D FFT over (i2, i3) of plane i1 of X[q].  PRO 0: load from X; PRO 1: z = W_b0 + i W_b0+1.
+// EPI 0: store to X; EPI 1: psi_b0 = Re z * psi_scale, psi_b0+1 = Im z * psi_scale.
+template <class T, int N, int SIGN, int PRO, int EPI>
+__global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
+    k_plane_full(DevPlan g, cplx<T>* __restrict__ X, const T* __restrict__ W, T* __restrict__ psi,
+                 int band0, int nb, int nbat) {
+  using C = cplx<T>;
+  using G = Geo<T, N>;
+  constexpr int RP = G::RP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* P = reinterpret_cast<C*>(smem_raw);
+  C* tw = P + N * RP;
+  const int i1 = blockIdx.x, q = blockIdx.y;
+  const int b0 = band0 + 2 * q;
+  const bool has1 = (2 * q + 1 < nbat) && (b0 + 1 < nb);
+  C* Xq = X + (int64_t)q * g.ntot + (int64_t)i1 * N * N;
+  const int64_t plane0 = (int64_t)i1 * N * N;
+  load_twiddles<T>(tw, g);
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i2 = e / N, i3 = e - i2 * N;
+    C z;
+    if (PRO == 0) {
+      z = Xq[e];
+    } else {
+      z.x = W[(int64_t)b0 * g.ntot + plane0 + e];
+      z.y = has1 ? W[(int64_t)(b0 + 1) * g.ntot + plane0 + e] : T(0);
+    }
+    P[i2 * RP + i3] = z;
+  }
+  __syncthreads();
+  fft_lines<T, N, SIGN, N, G::TLP, RP, 1>(P, tw);  // along i3
+  fft_lines<T, N, SIGN, N, G::TLP, 1, RP>(P, tw);  // along i2
+  const T s = T(g.psi_scale);
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i2 = e / N, i3 = e - i2 * N;
+    const C z = P[i2 * RP + i3];
+    if (EPI == 0) {
+      Xq[e] = z;
+    } else {
+      psi[(int64_t)b0 * g.ntot + plane0 + e] = z.x * s;
+      if (has1) psi[(int64_t)(b0 + 1) * g.ntot + plane0 + e] = z.y * s;
+    }
+  }
+}
+
+// (V_x psi)(G) of the band pair q: Y = fft(W_b0 + i W_b0+1); X_b0(G) = (Y(G) + Y(-G)*)/2,
+// X_b0+1(G) = (Y(G) - Y(-G)*)/(2i); both scaled by sqrt(Omega)/Ntot.
+template <class T>
+__global__ void k_gather(DevPlan g, const cplx<T>* __restrict__ X, int nb, int band0, int nbat,
+                         double2* __restrict__ vpsiG) {
+  const int q = blockIdx.y;
+  const int b0 = band0 + 2 * q;
+  const bool has1 = (2 * q + 1 < nbat) && (b0 + 1 < nb);
+  const cplx<T>* Xq = X + (int64_t)q * g.ntot;
+  const double s = 0.5 * g.out_scale;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.npw; k += gridDim.x * blockDim.x) {
+    const cplx<T> y = Xq[g.gidx[k]], ym = Xq[g.gidxneg[k]];
+    const double yx = y.x, yy = y.y, mx = ym.x, my = ym.y;
+    vpsiG[(int64_t)b0 * g.npw + k] = make_double2(s * (yx + mx), s * (yy - my));
+    if (has1) vpsiG[(int64_t)(b0 + 1) * g.npw + k] = make_double2(s * (yy + my), s * (mx - yx));
+  }
+}
+
+// ------------------------------------------------------------------ pair passes
+
+template <class T, int N>
+__global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
+    k_pair_fwd(DevPlan g, const T* __restrict__ psi, const Chain* __restrict__ chains,
+               cplx<T>* __restrict__ H) {
+  using C = cplx<T>;
+  using G = Geo<T, N>;
+  constexpr int RP = G::RP, KH = G::KH, NC = G::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* P = reinterpret_cast<C*>(smem_raw);
+  C* tw = P + N * RP;
+  const int i1 = blockIdx.x;
+  const Chain ch = chains[blockIdx.y];
+  load_twiddles<T>(tw, g);
+  const int64_t plane0 = (int64_t)i1 * N * N;
+  const bool hb = ch.bi >= 0;
+  const T* pai = psi + (int64_t)ch.ai * g.ntot + plane0;
+  const T* paj = psi + (int64_t)ch.aj * g.ntot + plane0;
+  const T* pbi = psi + (int64_t)(hb ? ch.bi : 0) * g.ntot + plane0;
+  const T* pbj = psi + (int64_t)(hb ? ch.bj : 0) * g.ntot + plane0;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i2 = e / N, i3 = e - i2 * N;
+    const T a = pai[e] * paj[e];
+    const T b = hb ? pbi[e] * pbj[e] : T(0);
+    P[i2 * RP + i3] = cmake<T>(a, b);
+  }
+  __syncthreads();
+  fft_lines<T, N, -1, N, G::TLP, RP, 1>(P, tw);  // along i3
+  fft_lines<T, N, -1, N, G::TLP, 1, RP>(P, tw);  // along i2
+  C* Hp = H + (int64_t)blockIdx.y * g.hsize + (int64_t)i1 * N * NC;
+  for (int e = threadIdx.x; e < N * KH; e += blockDim.x) {
+    const int k2 = e / KH, k3 = e - k2 * KH;
+    const int m2 = k2 == 0 ? 0 : N - k2, m3 = k3 == 0 ? 0 : N - k3;
+    const C z = P[k2 * RP + k3], zm = P[m2 * RP + m3];
+    const T h = T(0.5);
+    Hp[k2 * NC + k3] = cmake<T>(h * (z.x + zm.x), h * (z.y - zm.y));
+    Hp[k2 * NC + KH + k3] = cmake<T>(h * (z.y + zm.y), h * (zm.x - z.x));
+  }
+}
+
+template <class T, int N>
+__global__ void __launch_bounds__(Geo<T, N>::THR_COLH)
+    k_pair_col(DevPlan g, cplx<T>* __restrict__ H, const Chain* __restrict__ chains,
+               double* __restrict__ epair, double* __restrict__ dpair) {
+  using C = cplx<T>;
+  using G = Geo<T, N>;
+  constexpr int KH = G::KH, NC = G::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int k2 = blockIdx.x;
+  C* S = reinterpret_cast<C*>(smem_raw);
+  C* tw = S + N * NC;
+  double* red = reinterpret_cast<double*>(tw + N);
+  const Chain ch = chains[blockIdx.y];
+  C* Hc = H + (int64_t)blockIdx.y * g.hsize;
+  load_twiddles<T>(tw, g);
+  for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
+    const int i1 = e / NC, c = e - i1 * NC;
+    S[e] = Hc[((int64_t)i1 * N + k2) * NC + c];
+  }
+  __syncthreads();
+  fft_lines<T, N, -1, NC, G::TLC, 1, NC>(S, tw);  // along i1
+
+  // kernel multiply and energy partials
+  const T* vt = static_cast<const T*>(g.vtab);
+  const bool want_d = g.dvtab64 != nullptr;
+  const int m2 = freq_of(k2, N);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // e_a, e_b, d_a, d_b
+  T accf[4] = {T(0), T(0), T(0), T(0)};
+  for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
+    const int k1 = e / NC, c = e - k1 * NC;
+    const int s = c >= KH ? 1 : 0;
+    const int k3 = c - s * KH;
+    const int64_t vi = ((int64_t)k1 * N + k2) * KH + k3;
+    const T wgt = (k3 == 0 || 2 * k3 == N) ? T(1) : T(2);
+    C z = S[e];
+    const int m1 = freq_of(k1, N), m3 = freq_of(k3, N);
+    const int mm = m1 * m1 + m2 * m2 + m3 * m3;
+    if (sizeof(T) == 8 || mm <= g.msmall2) {
+      // kernel term in FP64
+      const double zx = z.x, zy = z.y, a2 = zx * zx + zy * zy;
+      const double v = g.vtab64[vi];
+      acc[s] += double(wgt) * v * a2;
+      if (want_d) acc[2 + s] += double(wgt) * g.dvtab64[vi] * a2;
+      const double vs = v * g.inv_ntot;
+      z.x = T(zx * vs);
+      z.y = T(zy * vs);
+    } else {
+      const T a2 = z.x * z.x + z.y * z.y;
+      const T v = vt[vi];  // v / Ntot
+      accf[s] += wgt * v * a2;
+      if (want_d) accf[2 + s] += wgt * T(g.dvtab64[vi]) * a2;
+      z.x *= v;
+      z.y *= v;
+    }
+    S[e] = z;
+  }
+  if (sizeof(T) != 8) {
+    const double ntot = double(g.ntot);
+    acc[0] += double(accf[0]) * ntot;  // the working-precision table holds v / Ntot
+    acc[1] += double(accf[1]) * ntot;
+    acc[2] += double(accf[2]);
+    acc[3] += double(accf[3]);
+  }
+  __syncthreads();
+  fft_lines<T, N, +1, NC, G::TLC, 1, NC>(S, tw);  // inverse along k1
+  for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
+    const int i1 = e / NC, c = e - i1 * NC;
+    Hc[((int64_t)i1 * N + k2) * NC + c] = S[e];
+  }
+  block_sum4(acc, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&epair[ch.pa], acc[0]);
+    if (ch.pb >= 0) atomicAdd(&epair[ch.pb], acc[1]);
+    if (want_d) {
+      atomicAdd(&dpair[ch.pa], acc[2]);
+      if (ch.pb >= 0) atomicAdd(&dpair[ch.pb], acc[3]);
+    }
+  }
+}
+
+template <class T, int N>
+__global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
+    k_pair_inv(DevPlan g, const T* __restrict__ psi, T* __restrict__ W, const T* __restrict__ occ,
+               const Chain* __restrict__ chains, const cplx<T>* __restrict__ H) {
+  using C = cplx<T>;
+  using G = Geo<T, N>;
+  constexpr int RP = G::RP, KH = G::KH, NC = G::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* P = reinterpret_cast<C*>(smem_raw);
+  C* tw = P + N * RP;
+  const int i1 = blockIdx.x;
+  const Chain ch = chains[blockIdx.y];
+  load_twiddles<T>(tw, g);
+  const C* Hp = H + (int64_t)blockIdx.y * g.hsize + (int64_t)i1 * N * NC;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int k2 = e / N, k3 = e - k2 * N;
+    C a, b;
+    if (k3 < KH) {
+      a = Hp[k2 * NC + k3];
+      b = Hp[k2 * NC + KH + k3];
+    } else {
+      const int m2 = k2 == 0 ? 0 : N - k2, m3 = N - k3;
+      a = Hp[m2 * NC + m3];
+      b = Hp[m2 * NC + KH + m3];
+      a.y = -a.y;
+      b.y = -b.y;
+    }
+    P[k2 * RP + k3] = cmake<T>(a.x - b.y, a.y + b.x);
+  }
+  __syncthreads();
+  fft_lines<T, N, +1, N, G::TLP, 1, RP>(P, tw);  // along k2
+  fft_lines<T, N, +1, N, G::TLP, RP, 1>(P, tw);  // along k3
+  const int64_t plane0 = (int64_t)i1 * N * N;
+  const bool hb = ch.bi >= 0;
+  const T fai = occ[ch.ai], faj = occ[ch.aj];
+  const T fbi = hb ? occ[ch.bi] : T(0), fbj = hb ? occ[ch.bj] : T(0);
+  const T* pai = psi + (int64_t)ch.ai * g.ntot + plane0;
+  const T* paj = psi + (int64_t)ch.aj * g.ntot + plane0;
+  const T* pbi = psi + (int64_t)(hb ? ch.bi : 0) * g.ntot + plane0;
+  const T* pbj = psi + (int64_t)(hb ? ch.bj : 0) * g.ntot + plane0;
+  T* wai = W + (int64_t)ch.ai * g.ntot + plane0;
+  T* waj = W + (int64_t)ch.aj * g.ntot + plane0;
+  T* wbi = W + (int64_t)(hb ? ch.bi : 0) * g.ntot + plane0;
+  T* wbj = W + (int64_t)(hb ? ch.bj : 0) * g.ntot + plane0;
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i2 = e / N, i3 = e - i2 * N;
+    const C z = P[i2 * RP + i3];
+    const T ai = pai[e], aj = paj[e];
+    atomic_add_real(waj + e, -fai * ai * z.x);
+    if (ch.ai != ch.aj) atomic_add_real(wai + e, -faj * aj * z.x);
+    if (hb) {
+      const T bi = pbi[e], bj = pbj[e];
+      atomic_add_real(wbj + e, -fbi * bi * z.y);
+      if (ch.bi != ch.bj) atomic_add_real(wbi + e, -fbj * bj * z.y);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+
+template <class T, int N>
+struct Launch {
+  using C = cplx<T>;
+  using G = Geo<T, N>;
+
+  static cudaError_t configure(const DevPlan&) {
+    const void* fns[] = {(const void*)k_col_full<T, N, +1>, (const void*)k_col_full<T, N, -1>,
+                         (const void*)k_plane_full<T, N, +1, 0, 1>,
+                         (const void*)k_plane_full<T, N, -1, 1, 0>, (const void*)k_pair_fwd<T, N>,
+                         (const void*)k_pair_inv<T, N>};
+    for (const void* f : fns) {
+      cudaError_t err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)G::SMEM_PLANE);
+      if (err != cudaSuccess) return err;
+    }
+    return cudaFuncSetAttribute((const void*)k_pair_col<T, N>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_COLH);
+  }
+
+  static cudaError_t to_real(const DevPlan& g, const double2* psiG, int nb, int band0, int nbat,
+                             void* Xv, void* psiv, cudaStream_t s) {
+    C* X = static_cast<C*>(Xv);
+    const int nq = (nbat + 1) / 2;
+    cudaError_t err = cudaMemsetAsync(X, 0, sizeof(C) * (size_t)g.ntot * nq, s);
+    if (err != cudaSuccess) return err;
+    k_scatter<T><<<dim3((g.npw + 255) / 256, nq), 256, 0, s>>>(g, psiG, nb, band0, nbat, X);
+    k_col_full<T, N, +1><<<dim3(N, nq), G::THR_COLF, G::SMEM_COLF, s>>>(g, X);
+    k_plane_full<T, N, +1, 0, 1><<<dim3(N, nq), G::THR_PLANE, G::SMEM_PLANE, s>>>(
+        g, X, nullptr, static_cast<T*>(psiv), band0, nb, nbat);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t pair_fwd(const DevPlan& g, const void* psi, const Chain* ch, int nch, void* H,
+                              cudaStream_t s) {
+    k_pair_fwd<T, N><<<dim3(N, nch), G::THR_PLANE, G::SMEM_PLANE, s>>>(
+        g, static_cast<const T*>(psi), ch, static_cast<C*>(H));
+    return cudaGetLastError();
+  }
+
+  static cudaError_t pair_col(const DevPlan& g, void* H, const Chain* ch, int nch, double* ep,
+                              double* dp, cudaStream_t s) {
+    k_pair_col<T, N><<<dim3(N, nch), G::THR_COLH, G::SMEM_COLH, s>>>(g, static_cast<C*>(H), ch,
+                                                                       ep, dp);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t pair_inv(const DevPlan& g, const void* psi, void* W, const void* occ,
+                              const Chain* ch, int nch, const void* H, cudaStream_t s) {
+    k_pair_inv<T, N><<<dim3(N, nch), G::THR_PLANE, G::SMEM_PLANE, s>>>(
+        g, static_cast<const T*>(psi), static_cast<T*>(W), static_cast<const T*>(occ), ch,
+        static_cast<const C*>(H));
+    return cudaGetLastError();
+  }
+
+  static cudaError_t to_sphere(const DevPlan& g, const void* W, int nb, int band0, int nbat,
+                               void* Xv, double2* vpsiG, cudaStream_t s) {
+    C* X = static_cast<C*>(Xv);
+    const int nq = (nbat + 1) / 2;
+    k_plane_full<T, N, -1, 1, 0><<<dim3(N, nq), G::THR_PLANE, G::SMEM_PLANE, s>>>(
+        g, X, static_cast<const T*>(W), nullptr, band0, nb, nbat);
+    k_col_full<T, N, -1><<<dim3(N, nq), G::THR_COLF, G::SMEM_COLF, s>>>(g, X);
+    k_gather<T><<<dim3((g.npw + 255) / 256, nq), 256, 0, s>>>(g, X, nb, band0, nbat, vpsiG);
+    return cudaGetLastError();
+  }
+
+  static constexpr KernelOps ops() {
+    return KernelOps{(int)sizeof(T), N, G::SMEM_COLH > G::SMEM_PLANE ? G::SMEM_COLH : G::SMEM_PLANE,
+                     configure, to_real, pair_fwd, pair_col, pair_inv, to_sphere};
+  }
+};
+
+}  // namespace fockx

@@ -1,0 +1,855 @@
+// fock_plan.cpp — host side of the C ABI declared in include/fock.h: cell and
+// plane-wave sphere, Coulomb-kernel tables, twiddles, pair schedule, workspace
+// and the orchestration of the kernel passes.
+//
+// Built with -ffp-contract=off: the sphere's order is defined by a fixed
+// sequence of IEEE operations (no fused multiply-add), so every machine builds
+// the same list.
+#include "fock.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fock_internal.h"
+
+using fockx::Chain;
+using fockx::DevPlan;
+using fockx::KernelOps;
+
+namespace {
+
+constexpr double kTwoPi = 2.0 * 3.14159265358979323846;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kBandBlock = 16;                  // bands per block of the pair schedule
+constexpr size_t kChainBufferBytes = 120u << 20;  // default size of the pair-transform buffer
+constexpr int kMsmall2 = 3;                     // |m|^2 of the kernel terms kept in FP64 (mixed)
+
+thread_local std::string g_create_error;
+
+void cross3(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+int freq_of(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
+
+struct Workspace {
+  int nb_cap = 0;
+  size_t psi_bytes = 0;
+  void* psi = nullptr;
+  void* w = nullptr;
+  void* h = nullptr;
+  size_t h_bytes = 0;
+  int npair_cap = 0;
+  double* epair = nullptr;
+  double* dpair = nullptr;
+  int2* pairs = nullptr;
+  Chain* chains = nullptr;
+  double* occ = nullptr;
+  void* occT = nullptr;
+};
+
+}  // namespace
+
+struct fock_plan {
+  int device = 0;
+  int n = 0;
+  double cell[9];
+  double recip[9];
+  double vol = 0.0;
+  double ecut = 0.0;
+  fock_kernel kind = FOCK_KERNEL_SPENCER_ALAVI;
+  double omega = 0.0;
+  fock_precision prec = FOCK_PREC_FP64;
+  std::vector<int32_t> miller;
+  int npw = 0;
+  const KernelOps* ops = nullptr;
+  DevPlan dp{};
+  int chain_batch = 1;
+  // device tables
+  int* d_gidx = nullptr;
+  int* d_gidxneg = nullptr;
+  void* d_tw = nullptr;
+  void* d_vtab = nullptr;
+  double* d_vtab64 = nullptr;
+  double* d_dvtab64 = nullptr;
+  double* d_result = nullptr;
+  double* h_result = nullptr;  // pinned
+  int64_t table_bytes = 0;
+  Workspace ws;
+  // pair schedule of the last band count uploaded
+  int sched_nb = -1;
+  std::vector<int2> pairs;
+  std::vector<Chain> chains;
+  std::vector<double> occ_host;
+  // launch accounting and optional per-launch event timing
+  fock_stats stats{};
+  bool timing = false;
+  std::vector<cudaEvent_t> events;  // pool, two per timed launch
+  std::vector<int> event_phase;     // phase of each timed launch
+  size_t nev = 0;                   // timed launches recorded in the current call
+  std::string err;
+};
+
+namespace {
+
+fock_status fail(fock_plan* p, fock_status s, const std::string& msg) {
+  if (p) p->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+fock_status cuda_fail(fock_plan* p, cudaError_t e, const char* what) {
+  const fock_status s = (e == cudaErrorMemoryAllocation) ? FOCK_ERR_OOM : FOCK_ERR_CUDA;
+  std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();  // clear a sticky launch error of this thread's last call
+  return fail(p, s, msg);
+}
+
+#define FOCK_CUDA(p, call)                              \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(p, e_, #call); \
+  } while (0)
+
+template <class Ptr>
+cudaError_t dev_alloc(Ptr** ptr, size_t bytes) {
+  return cudaMalloc(reinterpret_cast<void**>(ptr), bytes == 0 ? 16 : bytes);
+}
+
+void free_ws(Workspace& w) {
+  cudaFree(w.psi);
+  cudaFree(w.w);
+  cudaFree(w.h);
+  cudaFree(w.epair);
+  cudaFree(w.dpair);
+  cudaFree(w.pairs);
+  cudaFree(w.chains);
+  cudaFree(w.occ);
+  cudaFree(w.occT);
+  w = Workspace{};
+}
+
+// G = m1 b1 + m2 b2 + m3 b3 componentwise as ((m1 b1x + m2 b2x) + m3 b3x);
+// |G|^2 = (Gx^2 + Gy^2) + Gz^2.
+double g2_of(const double* b, int m1, int m2, int m3) {
+  double c[3];
+  for (int x = 0; x < 3; ++x) c[x] = (double(m1) * b[0 + x] + double(m2) * b[3 + x]) + double(m3) * b[6 + x];
+  return (c[0] * c[0] + c[1] * c[1]) + c[2] * c[2];
+}
+
+struct GEntry {
+  double g2;
+  int m[3];
+};
+
+void reciprocal(const double* cell, double* recip, double* vol_signed) {
+  double c23[3], c31[3], c12[3];
+  cross3(cell + 3, cell + 6, c23);
+  cross3(cell + 6, cell + 0, c31);
+  cross3(cell + 0, cell + 3, c12);
+  const double vol = (cell[0] * c23[0] + cell[1] * c23[1]) + cell[2] * c23[2];
+  const double fac = kTwoPi / vol;
+  for (int x = 0; x < 3; ++x) {
+    recip[0 + x] = c23[x] * fac;
+    recip[3 + x] = c31[x] * fac;
+    recip[6 + x] = c12[x] * fac;
+  }
+  *vol_signed = vol;
+}
+
+// The sphere |G|^2 <= 2 Ecut sorted by (|G|^2, m1, m2, m3); false if it does not
+// fit on an N^3 grid (2 |m_a| >= N).
+bool build_sphere(const double* cell, const double* recip, double ecut, int n,
+                  std::vector<GEntry>& sph) {
+  const double gmax = std::sqrt(2.0 * ecut);
+  int mmax[3];
+  for (int i = 0; i < 3; ++i) {
+    const double* a = cell + 3 * i;
+    const double len = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    mmax[i] = (int)std::floor(gmax * len / kTwoPi) + 1;
+  }
+  sph.clear();
+  for (int m1 = -mmax[0]; m1 <= mmax[0]; ++m1)
+    for (int m2 = -mmax[1]; m2 <= mmax[1]; ++m2)
+      for (int m3 = -mmax[2]; m3 <= mmax[2]; ++m3) {
+        const double g2 = g2_of(recip, m1, m2, m3);
+        if (g2 <= 2.0 * ecut) sph.push_back(GEntry{g2, {m1, m2, m3}});
+      }
+  std::sort(sph.begin(), sph.end(), [](const GEntry& x, const GEntry& y) {
+    if (x.g2 != y.g2) return x.g2 < y.g2;
+    if (x.m[0] != y.m[0]) return x.m[0] < y.m[0];
+    if (x.m[1] != y.m[1]) return x.m[1] < y.m[1];
+    return x.m[2] < y.m[2];
+  });
+  for (const GEntry& e : sph)
+    for (int a = 0; a < 3; ++a)
+      if (2 * std::abs(e.m[a]) >= n) return false;
+  return true;
+}
+
+void kernel_value(const fock_plan* p, double g2, double* v, double* dv) {
+  if (p->kind == FOCK_KERNEL_SPENCER_ALAVI) {
+    const double rc = std::cbrt(3.0 * p->vol / (4.0 * kPi));
+    if (g2 == 0.0) {
+      *v = 2.0 * kPi * rc * rc;
+    } else {
+      const double s = std::sin(0.5 * std::sqrt(g2) * rc);
+      *v = 8.0 * kPi * s * s / g2;
+    }
+    *dv = 0.0;
+  } else {
+    const double w = p->omega;
+    *v = (g2 == 0.0) ? kPi / (w * w) : -4.0 * kPi * std::expm1(-g2 / (4.0 * w * w)) / g2;
+    *dv = -(2.0 * kPi / (w * w * w)) * std::exp(-g2 / (4.0 * w * w));
+  }
+}
+
+// Unique pairs i <= j in band blocks of kBandBlock (block rows outer), i outer and j
+// inner inside a block, so consecutive pairs share psi_i and a batch of chains
+// touches a few blocks of orbitals.  Chain k holds pairs 2k and 2k+1.
+void build_schedule(fock_plan* p, int nb) {
+  p->pairs.clear();
+  p->pairs.reserve((size_t)nb * (nb + 1) / 2);
+  const int nblk = (nb + kBandBlock - 1) / kBandBlock;
+  for (int bi = 0; bi < nblk; ++bi) {
+    for (int bj = bi; bj < nblk; ++bj) {
+      const int i0 = bi * kBandBlock, i1 = std::min(nb, i0 + kBandBlock);
+      const int j0 = bj * kBandBlock, j1 = std::min(nb, j0 + kBandBlock);
+      for (int i = i0; i < i1; ++i)
+        for (int j = std::max(i, j0); j < j1; ++j) p->pairs.push_back(make_int2(i, j));
+    }
+  }
+}
+
+void chains_from_pairs(const std::vector<int2>& pairs, std::vector<Chain>& chains) {
+  chains.clear();
+  const int np = (int)pairs.size();
+  chains.reserve((np + 1) / 2);
+  for (int k = 0; 2 * k < np; ++k) {
+    Chain c{};
+    c.ai = pairs[2 * k].x;
+    c.aj = pairs[2 * k].y;
+    c.pa = 2 * k;
+    if (2 * k + 1 < np) {
+      c.bi = pairs[2 * k + 1].x;
+      c.bj = pairs[2 * k + 1].y;
+      c.pb = 2 * k + 1;
+    } else {
+      c.bi = c.bj = -1;
+      c.pb = -1;
+    }
+    chains.push_back(c);
+  }
+}
+
+void stats_reset(fock_plan* p) {
+  const int cb = p->stats.chain_batch, bb = p->stats.band_batch;
+  p->stats = fock_stats{};
+  p->stats.chain_batch = cb;
+  p->stats.band_batch = bb;
+  p->nev = 0;
+  p->event_phase.clear();
+}
+
+// Brackets one pass (`launches` kernels) of phase `ph`: events are recorded on
+// the stream around it when timing is on.
+struct PhaseScope {
+  fock_plan* p;
+  int ph;
+  cudaStream_t s;
+  size_t idx;
+  PhaseScope(fock_plan* p_, int ph_, int launches, cudaStream_t s_) : p(p_), ph(ph_), s(s_), idx(0) {
+    p->stats.launches += launches;
+    p->stats.phase_launches[ph] += launches;
+    if (p->timing) {
+      idx = p->nev++;
+      while (p->events.size() < 2 * p->nev) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) break;
+        p->events.push_back(e);
+      }
+      if (p->events.size() >= 2 * p->nev) {
+        cudaEventRecord(p->events[2 * idx], s);
+        p->event_phase.push_back(ph);
+      } else {
+        p->nev--;
+        p->timing = false;
+      }
+    }
+  }
+  ~PhaseScope() {
+    if (p->timing && idx < p->nev) cudaEventRecord(p->events[2 * idx + 1], s);
+  }
+};
+
+fock_status collect_timing(fock_plan* p, cudaStream_t s) {
+  if (!p->timing || p->nev == 0) return FOCK_OK;
+  FOCK_CUDA(p, cudaStreamSynchronize(s));
+  for (size_t k = 0; k < p->nev; ++k) {
+    float ms = 0.f;
+    FOCK_CUDA(p, cudaEventElapsedTime(&ms, p->events[2 * k], p->events[2 * k + 1]));
+    p->stats.phase_ms[p->event_phase[k]] += ms;
+  }
+  return FOCK_OK;
+}
+
+fock_status check_device(fock_plan* p) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(p, e, "cudaGetDevice");
+  if (dev != p->device) return fail(p, FOCK_ERR_INVALID_ARG, "the plan belongs to another device");
+  return FOCK_OK;
+}
+
+fock_status ensure_workspace(fock_plan* p, int nb, int npairs) {
+  Workspace& w = p->ws;
+  const size_t rb = (size_t)p->ops->real_bytes;
+  if (nb > w.nb_cap) {
+    cudaFree(w.psi);
+    cudaFree(w.w);
+    cudaFree(w.occ);
+    cudaFree(w.occT);
+    w.psi = w.w = w.occT = nullptr;
+    w.occ = nullptr;
+    w.nb_cap = 0;
+    w.psi_bytes = (size_t)nb * (size_t)p->dp.ntot * rb;
+    FOCK_CUDA(p, dev_alloc(&w.psi, w.psi_bytes));
+    FOCK_CUDA(p, dev_alloc(&w.w, w.psi_bytes));
+    FOCK_CUDA(p, dev_alloc(&w.occ, sizeof(double) * nb));
+    FOCK_CUDA(p, dev_alloc(&w.occT, rb * nb));
+    w.nb_cap = nb;
+  }
+  if (w.h == nullptr) {
+    const size_t chain_bytes = (size_t)p->dp.hsize * 2 * rb;
+    w.h_bytes = chain_bytes * (size_t)p->chain_batch;
+    FOCK_CUDA(p, dev_alloc(&w.h, w.h_bytes));
+  }
+  if (npairs > w.npair_cap) {
+    cudaFree(w.epair);
+    cudaFree(w.dpair);
+    cudaFree(w.pairs);
+    cudaFree(w.chains);
+    w.epair = w.dpair = nullptr;
+    w.pairs = nullptr;
+    w.chains = nullptr;
+    w.npair_cap = 0;
+    p->sched_nb = -1;
+    FOCK_CUDA(p, dev_alloc(&w.epair, sizeof(double) * npairs));
+    FOCK_CUDA(p, dev_alloc(&w.dpair, sizeof(double) * npairs));
+    FOCK_CUDA(p, dev_alloc(&w.pairs, sizeof(int2) * npairs));
+    FOCK_CUDA(p, dev_alloc(&w.chains, sizeof(Chain) * ((npairs + 1) / 2)));
+    w.npair_cap = npairs;
+  }
+  return FOCK_OK;
+}
+
+fock_status upload_occ(fock_plan* p, const double* occ, int nb, cudaStream_t s) {
+  p->occ_host.assign(occ, occ + nb);
+  FOCK_CUDA(p, cudaMemcpyAsync(p->ws.occ, occ, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+  if (p->ops->real_bytes == 8) {
+    FOCK_CUDA(p, cudaMemcpyAsync(p->ws.occT, occ, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+  } else {
+    std::vector<float> f(occ, occ + nb);
+    FOCK_CUDA(p, cudaMemcpyAsync(p->ws.occT, f.data(), sizeof(float) * nb, cudaMemcpyHostToDevice, s));
+    FOCK_CUDA(p, cudaStreamSynchronize(s));  // f is a local buffer
+  }
+  return FOCK_OK;
+}
+
+int bands_per_grid_batch(const fock_plan* p) {
+  const size_t grid_bytes = (size_t)p->dp.ntot * 2 * (size_t)p->ops->real_bytes;
+  const int q = (int)std::max<size_t>(1, p->ws.h_bytes / grid_bytes);
+  return 2 * q;
+}
+
+fock_status orbitals_to_real(fock_plan* p, const void* psiG, int nb, cudaStream_t s) {
+  const int nbat = bands_per_grid_batch(p);
+  p->stats.band_batch = nbat;
+  for (int b0 = 0; b0 < nb; b0 += nbat) {
+    const int cnt = std::min(nbat, nb - b0);
+    PhaseScope ps(p, FOCK_PHASE_TO_REAL, 3, s);
+    FOCK_CUDA(p, p->ops->to_real(p->dp, static_cast<const double2*>(psiG), nb, b0, cnt, p->ws.h,
+                                 p->ws.psi, s));
+  }
+  return FOCK_OK;
+}
+
+fock_status validate_apply(fock_plan* p, const void* psiG, int nb, const void* out) {
+  if (!p) return fail(nullptr, FOCK_ERR_INVALID_ARG, "plan is NULL");
+  if (!psiG || !out) return fail(p, FOCK_ERR_INVALID_ARG, "psi_G or the output is NULL");
+  if (nb < 1) return fail(p, FOCK_ERR_INVALID_ARG, "nb must be >= 1");
+  if (nb > (1 << 15)) return fail(p, FOCK_ERR_INVALID_ARG, "nb is larger than 32768");
+  return check_device(p);
+}
+
+fock_status apply_impl(fock_plan* p, const void* psiG, int nb, const double* occ, int shard,
+                       int nshards, void* vpsiG, double* ex, double* dex, fock_stream_t stream) {
+  fock_status st = validate_apply(p, psiG, nb, vpsiG);
+  if (st != FOCK_OK) return st;
+  if (!occ) return fail(p, FOCK_ERR_INVALID_ARG, "occ is NULL");
+  if (nshards < 1 || shard < 0 || shard >= nshards)
+    return fail(p, FOCK_ERR_INVALID_ARG, "shard must satisfy 0 <= shard < nshards");
+  for (int i = 0; i < nb; ++i)
+    if (!std::isfinite(occ[i])) return fail(p, FOCK_ERR_INVALID_ARG, "occupations must be finite");
+  const size_t bytes = (size_t)nb * (size_t)p->npw * 16;
+  const char* a = static_cast<const char*>(psiG);
+  const char* b = static_cast<const char*>(vpsiG);
+  if (a < b + bytes && b < a + bytes) return fail(p, FOCK_ERR_INVALID_ARG, "psi_G and vpsi_G overlap");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  stats_reset(p);
+  const int npairs = nb * (nb + 1) / 2;
+  st = ensure_workspace(p, nb, npairs);
+  if (st != FOCK_OK) return st;
+  if (p->sched_nb != nb) {
+    build_schedule(p, nb);
+    chains_from_pairs(p->pairs, p->chains);
+    FOCK_CUDA(p, cudaMemcpyAsync(p->ws.pairs, p->pairs.data(), sizeof(int2) * npairs,
+                                 cudaMemcpyHostToDevice, s));
+    FOCK_CUDA(p, cudaMemcpyAsync(p->ws.chains, p->chains.data(), sizeof(Chain) * p->chains.size(),
+                                 cudaMemcpyHostToDevice, s));
+    FOCK_CUDA(p, cudaStreamSynchronize(s));  // the host vectors may change on the next call
+    p->sched_nb = nb;
+  }
+  st = upload_occ(p, occ, nb, s);
+  if (st != FOCK_OK) return st;
+  const size_t rb = (size_t)p->ops->real_bytes;
+  FOCK_CUDA(p, cudaMemsetAsync(p->ws.w, 0, (size_t)nb * (size_t)p->dp.ntot * rb, s));
+  FOCK_CUDA(p, cudaMemsetAsync(p->ws.epair, 0, sizeof(double) * npairs, s));
+  FOCK_CUDA(p, cudaMemsetAsync(p->ws.dpair, 0, sizeof(double) * npairs, s));
+  st = orbitals_to_real(p, psiG, nb, s);
+  if (st != FOCK_OK) return st;
+
+  DevPlan dp = p->dp;
+  if (!dex) dp.dvtab64 = nullptr;  // skip the dE/domega partials nobody asked for
+  const int nch = (int)p->chains.size();
+  const int c0 = (int)((int64_t)nch * shard / nshards);
+  const int c1 = (int)((int64_t)nch * (shard + 1) / nshards);
+  p->stats.chain_batch = p->chain_batch;
+  p->stats.chains = c1 - c0;
+  p->stats.pairs = std::min(npairs, 2 * c1) - std::min(npairs, 2 * c0);
+  for (int c = c0; c < c1; c += p->chain_batch) {
+    const int cnt = std::min(p->chain_batch, c1 - c);
+    const Chain* ch = p->ws.chains + c;
+    {
+      PhaseScope ps(p, FOCK_PHASE_PAIR_FWD, 1, s);
+      FOCK_CUDA(p, p->ops->pair_fwd(dp, p->ws.psi, ch, cnt, p->ws.h, s));
+    }
+    {
+      PhaseScope ps(p, FOCK_PHASE_PAIR_COL, 1, s);
+      FOCK_CUDA(p, p->ops->pair_col(dp, p->ws.h, ch, cnt, p->ws.epair, p->ws.dpair, s));
+    }
+    {
+      PhaseScope ps(p, FOCK_PHASE_PAIR_INV, 1, s);
+      FOCK_CUDA(p, p->ops->pair_inv(dp, p->ws.psi, p->ws.w, p->ws.occT, ch, cnt, p->ws.h, s));
+    }
+  }
+
+  const int nbat = bands_per_grid_batch(p);
+  for (int b0 = 0; b0 < nb; b0 += nbat) {
+    const int cnt = std::min(nbat, nb - b0);
+    PhaseScope ps(p, FOCK_PHASE_TO_SPHERE, 3, s);
+    FOCK_CUDA(p, p->ops->to_sphere(p->dp, p->ws.w, nb, b0, cnt, p->ws.h,
+                                   static_cast<double2*>(vpsiG), s));
+  }
+
+  const int p0 = std::min(npairs, 2 * c0), p1 = std::min(npairs, 2 * c1);
+  const double scale = -0.5 * p->vol / ((double)p->dp.ntot * (double)p->dp.ntot);
+  {
+    PhaseScope ps(p, FOCK_PHASE_ENERGY, 1, s);
+    FOCK_CUDA(p, fockx::launch_energy_reduce(p->ws.pairs + p0, p1 - p0, p->ws.occ,
+                                             p->ws.epair + p0,
+                                             dp.dvtab64 ? p->ws.dpair + p0 : nullptr, scale,
+                                             p->d_result, s));
+  }
+  st = collect_timing(p, s);
+  if (st != FOCK_OK) return st;
+  if (ex || dex) {
+    FOCK_CUDA(p, cudaMemcpyAsync(p->h_result, p->d_result, 2 * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s));
+    FOCK_CUDA(p, cudaStreamSynchronize(s));
+    if (ex) *ex = p->h_result[0];
+    if (dex) *dex = p->h_result[1];
+  }
+  return FOCK_OK;
+}
+
+bool supported_n(int n) {
+  int m = n;
+  while (m % 2 == 0) m /= 2;
+  while (m % 3 == 0) m /= 3;
+  return m == 1 && n >= 2;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fock_status_string(fock_status s) {
+  switch (s) {
+    case FOCK_OK: return "ok";
+    case FOCK_ERR_INVALID_ARG: return "invalid argument";
+    case FOCK_ERR_UNSUPPORTED_SIZE: return "unsupported grid size";
+    case FOCK_ERR_GRID_TOO_SMALL: return "the plane-wave sphere does not fit on the grid";
+    case FOCK_ERR_OOM: return "out of device memory";
+    case FOCK_ERR_CUDA: return "CUDA error";
+    case FOCK_ERR_TIMEOUT: return "a bounded device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* fock_last_error(fock_plan_t plan) {
+  return plan ? plan->err.c_str() : g_create_error.c_str();
+}
+
+fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double cell[9],
+                             double ecut_ha, fock_kernel kind, const double* kparams,
+                             int nkparams, fock_precision prec, unsigned flags) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, FOCK_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grid || !cell) return fail(nullptr, FOCK_ERR_INVALID_ARG, "grid or cell is NULL");
+  if (!(flags & FOCK_GAMMA_REAL))
+    return fail(nullptr, FOCK_ERR_INVALID_ARG, "FOCK_GAMMA_REAL is required");
+  if (flags & ~FOCK_GAMMA_REAL) return fail(nullptr, FOCK_ERR_INVALID_ARG, "unknown flag bits");
+  if (prec != FOCK_PREC_FP64 && prec != FOCK_PREC_MIXED32)
+    return fail(nullptr, FOCK_ERR_INVALID_ARG, "unknown precision");
+  if (kind != FOCK_KERNEL_SPENCER_ALAVI && kind != FOCK_KERNEL_ERFC)
+    return fail(nullptr, FOCK_ERR_INVALID_ARG, "unknown kernel kind");
+  if (!(ecut_ha > 0.0) || !std::isfinite(ecut_ha))
+    return fail(nullptr, FOCK_ERR_INVALID_ARG, "ecut must be positive and finite");
+  double omega = 0.0;
+  if (kind == FOCK_KERNEL_ERFC) {
+    if (!kparams || nkparams < 1 || !(kparams[0] > 0.0) || !std::isfinite(kparams[0]))
+      return fail(nullptr, FOCK_ERR_INVALID_ARG, "erfc kernel needs kparams = {omega > 0}");
+    omega = kparams[0];
+  }
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(cell[i])) return fail(nullptr, FOCK_ERR_INVALID_ARG, "cell is not finite");
+  if (grid[0] != grid[1] || grid[1] != grid[2])
+    return fail(nullptr, FOCK_ERR_UNSUPPORTED_SIZE, "the FFT grid must be cubic (N1 = N2 = N3)");
+  const int n = grid[0];
+  if (n < 2 || !supported_n(n)) return fail(nullptr, FOCK_ERR_UNSUPPORTED_SIZE, "N must be 2^a 3^b");
+  const KernelOps* ops = fockx::find_kernel_ops(prec == FOCK_PREC_FP64 ? 0 : 1, n);
+  if (!ops) {
+    return fail(nullptr, FOCK_ERR_UNSUPPORTED_SIZE,
+                "no kernels compiled for N = " + std::to_string(n));
+  }
+
+  fock_plan* p = new (std::nothrow) fock_plan();
+  if (!p) return fail(nullptr, FOCK_ERR_OOM, "host allocation failed");
+  std::memcpy(p->cell, cell, sizeof(p->cell));
+  p->n = n;
+  p->ecut = ecut_ha;
+  p->kind = kind;
+  p->omega = omega;
+  p->prec = prec;
+  p->ops = ops;
+
+  // cell volume and reciprocal lattice, b_i = (2 pi / Omega) (a_j x a_k)
+  reciprocal(cell, p->recip, &p->vol);
+  if (!(std::fabs(p->vol) > 0.0)) {
+    delete p;
+    return fail(nullptr, FOCK_ERR_INVALID_ARG, "the cell is degenerate");
+  }
+  p->vol = std::fabs(p->vol);
+
+  // the sphere |G|^2 <= 2 Ecut in canonical order
+  std::vector<GEntry> sph;
+  if (!build_sphere(cell, p->recip, ecut_ha, n, sph)) {
+    delete p;
+    return fail(nullptr, FOCK_ERR_GRID_TOO_SMALL, "the G-sphere does not fit on the grid");
+  }
+  p->npw = (int)sph.size();
+  p->miller.resize(3 * sph.size());
+  std::vector<int> gidx(sph.size()), gneg(sph.size());
+  auto off = [n](int m1, int m2, int m3) {
+    const int i1 = ((m1 % n) + n) % n, i2 = ((m2 % n) + n) % n, i3 = ((m3 % n) + n) % n;
+    return (i1 * n + i2) * n + i3;
+  };
+  for (size_t k = 0; k < sph.size(); ++k) {
+    for (int a = 0; a < 3; ++a) p->miller[3 * k + a] = sph[k].m[a];
+    gidx[k] = off(sph[k].m[0], sph[k].m[1], sph[k].m[2]);
+    gneg[k] = off(-sph[k].m[0], -sph[k].m[1], -sph[k].m[2]);
+  }
+
+  // kernel tables on the stored half of the grid: [k1][k2][k3 <= N/2]
+  const int kh = n / 2 + 1;
+  const int64_t nhalf = (int64_t)n * n * kh;
+  const int64_t ntot = (int64_t)n * n * n;
+  std::vector<double> v64(nhalf), dv64(nhalf);
+  for (int k1 = 0; k1 < n; ++k1)
+    for (int k2 = 0; k2 < n; ++k2)
+      for (int k3 = 0; k3 < kh; ++k3) {
+        const double g2 = g2_of(p->recip, freq_of(k1, n), freq_of(k2, n), freq_of(k3, n));
+        const int64_t i = ((int64_t)k1 * n + k2) * kh + k3;
+        kernel_value(p, g2, &v64[i], &dv64[i]);
+      }
+  const bool fp64 = ops->real_bytes == 8;
+  // twiddles w[t] = exp(-2 pi i t / N)
+  std::vector<double> tw64(2 * n);
+  for (int t = 0; t < n; ++t) {
+    const long double ang = 2.0L * 3.141592653589793238462643383279502884L * t / n;
+    tw64[2 * t] = (double)std::cos(ang);
+    tw64[2 * t + 1] = -(double)std::sin(ang);
+  }
+
+  fock_status st = FOCK_OK;
+  auto upload = [&](void** dst, const void* src, size_t bytes) -> bool {
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      st = cuda_fail(nullptr, e, "uploading plan tables");
+      return false;
+    }
+    p->table_bytes += (int64_t)bytes;
+    return true;
+  };
+  cudaError_t ge = cudaGetDevice(&p->device);
+  if (ge != cudaSuccess) {
+    delete p;
+    return cuda_fail(nullptr, ge, "cudaGetDevice");
+  }
+  bool ok = upload((void**)&p->d_gidx, gidx.data(), sizeof(int) * gidx.size()) &&
+            upload((void**)&p->d_gidxneg, gneg.data(), sizeof(int) * gneg.size()) &&
+            upload((void**)&p->d_vtab64, v64.data(), sizeof(double) * nhalf);
+  if (ok && kind == FOCK_KERNEL_ERFC) ok = upload((void**)&p->d_dvtab64, dv64.data(), sizeof(double) * nhalf);
+  if (ok) {
+    if (fp64) {
+      std::vector<double> vs(nhalf);
+      for (int64_t i = 0; i < nhalf; ++i) vs[i] = v64[i] / (double)ntot;
+      ok = upload(&p->d_vtab, vs.data(), sizeof(double) * nhalf) &&
+           upload(&p->d_tw, tw64.data(), sizeof(double) * tw64.size());
+    } else {
+      std::vector<float> vs(nhalf), tw32(2 * n);
+      for (int64_t i = 0; i < nhalf; ++i) vs[i] = (float)(v64[i] / (double)ntot);
+      for (int t = 0; t < 2 * n; ++t) tw32[t] = (float)tw64[t];
+      ok = upload(&p->d_vtab, vs.data(), sizeof(float) * nhalf) &&
+           upload(&p->d_tw, tw32.data(), sizeof(float) * tw32.size());
+    }
+  }
+  if (ok) ok = upload((void**)&p->d_result, std::vector<double>(4, 0.0).data(), 4 * sizeof(double));
+  if (ok) {
+    cudaError_t e = cudaMallocHost((void**)&p->h_result, 4 * sizeof(double));
+    if (e != cudaSuccess) {
+      st = cuda_fail(nullptr, e, "cudaMallocHost");
+      ok = false;
+    }
+  }
+  if (!ok) {
+    fock_destroy(p);
+    return st;
+  }
+
+  DevPlan& d = p->dp;
+  d.n = n;
+  d.k3h = kh;
+  d.ntot = ntot;
+  d.hsize = (int64_t)n * n * 2 * kh;
+  d.npw = p->npw;
+  d.gidx = p->d_gidx;
+  d.gidxneg = p->d_gidxneg;
+  d.tw = p->d_tw;
+  d.vtab = p->d_vtab;
+  d.vtab64 = p->d_vtab64;
+  d.dvtab64 = p->d_dvtab64;
+  d.inv_ntot = 1.0 / (double)ntot;
+  d.psi_scale = 1.0 / std::sqrt(p->vol);
+  d.out_scale = std::sqrt(p->vol) / (double)ntot;
+  d.msmall2 = fp64 ? -1 : kMsmall2;
+
+  const size_t chain_bytes = (size_t)d.hsize * 2 * (size_t)ops->real_bytes;
+  p->chain_batch = (int)std::max<size_t>(1, kChainBufferBytes / chain_bytes);
+
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+  if (e != cudaSuccess) {
+    fock_destroy(p);
+    return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
+  }
+  if (ops->smem > (size_t)optin) {
+    fock_destroy(p);
+    return fail(nullptr, FOCK_ERR_UNSUPPORTED_SIZE, "the grid needs more shared memory than a CTA has");
+  }
+  e = ops->configure(d);
+  if (e != cudaSuccess) {
+    fock_destroy(p);
+    return cuda_fail(nullptr, e, "configuring kernels");
+  }
+  *out = p;
+  return FOCK_OK;
+}
+
+fock_status fock_gsphere(const int grid[3], const double cell[9], double ecut_ha, int64_t* npw,
+                         int32_t* miller, int64_t capacity) {
+  g_create_error.clear();
+  if (!grid || !cell || !npw) return fail(nullptr, FOCK_ERR_INVALID_ARG, "NULL argument");
+  if (!(ecut_ha > 0.0) || !std::isfinite(ecut_ha))
+    return fail(nullptr, FOCK_ERR_INVALID_ARG, "ecut must be positive and finite");
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(cell[i])) return fail(nullptr, FOCK_ERR_INVALID_ARG, "cell is not finite");
+  double recip[9], vol;
+  reciprocal(cell, recip, &vol);
+  if (!(std::fabs(vol) > 0.0)) return fail(nullptr, FOCK_ERR_INVALID_ARG, "the cell is degenerate");
+  const int n = std::min(grid[0], std::min(grid[1], grid[2]));
+  std::vector<GEntry> sph;
+  if (!build_sphere(cell, recip, ecut_ha, n, sph))
+    return fail(nullptr, FOCK_ERR_GRID_TOO_SMALL, "the G-sphere does not fit on the grid");
+  *npw = (int64_t)sph.size();
+  if (miller) {
+    if (capacity < (int64_t)sph.size())
+      return fail(nullptr, FOCK_ERR_INVALID_ARG, "miller buffer too small");
+    for (size_t k = 0; k < sph.size(); ++k)
+      for (int a = 0; a < 3; ++a) miller[3 * k + a] = sph[k].m[a];
+  }
+  return FOCK_OK;
+}
+
+fock_status fock_plan_set_batch(fock_plan_t plan, int chain_batch) {
+  if (!plan) return fail(nullptr, FOCK_ERR_INVALID_ARG, "plan is NULL");
+  if (chain_batch < 1 || chain_batch > 4096)
+    return fail(plan, FOCK_ERR_INVALID_ARG, "chain_batch must be in [1, 4096]");
+  if (chain_batch != plan->chain_batch) {
+    cudaFree(plan->ws.h);  // stream-ordered work using it has been queued by earlier calls;
+    plan->ws.h = nullptr;  // cudaFree waits for the device to finish with it
+    plan->ws.h_bytes = 0;
+    plan->chain_batch = chain_batch;
+  }
+  return FOCK_OK;
+}
+
+fock_status fock_plan_set_timing(fock_plan_t plan, int enable) {
+  if (!plan) return fail(nullptr, FOCK_ERR_INVALID_ARG, "plan is NULL");
+  plan->timing = enable != 0;
+  return FOCK_OK;
+}
+
+fock_status fock_plan_stats(fock_plan_t plan, fock_stats* stats) {
+  if (!plan || !stats) return fail(plan, FOCK_ERR_INVALID_ARG, "NULL argument");
+  *stats = plan->stats;
+  return FOCK_OK;
+}
+
+fock_status fock_plan_npw(fock_plan_t plan, int64_t* npw) {
+  if (!plan || !npw) return fail(plan, FOCK_ERR_INVALID_ARG, "NULL argument");
+  *npw = plan->npw;
+  return FOCK_OK;
+}
+
+fock_status fock_plan_gvectors(fock_plan_t plan, int32_t* miller) {
+  if (!plan || !miller) return fail(plan, FOCK_ERR_INVALID_ARG, "NULL argument");
+  std::memcpy(miller, plan->miller.data(), sizeof(int32_t) * plan->miller.size());
+  return FOCK_OK;
+}
+
+fock_status fock_plan_reserve(fock_plan_t plan, int nb_max) {
+  if (!plan) return fail(nullptr, FOCK_ERR_INVALID_ARG, "plan is NULL");
+  if (nb_max < 1 || nb_max > (1 << 15)) return fail(plan, FOCK_ERR_INVALID_ARG, "nb_max out of range");
+  fock_status st = check_device(plan);
+  if (st != FOCK_OK) return st;
+  return ensure_workspace(plan, nb_max, nb_max * (nb_max + 1) / 2);
+}
+
+fock_status fock_plan_device_bytes(fock_plan_t plan, int64_t* bytes) {
+  if (!plan || !bytes) return fail(plan, FOCK_ERR_INVALID_ARG, "NULL argument");
+  const Workspace& w = plan->ws;
+  int64_t b = plan->table_bytes + 2 * (int64_t)w.psi_bytes + (int64_t)w.h_bytes;
+  b += (int64_t)w.npair_cap * (2 * sizeof(double) + sizeof(int2)) +
+       (int64_t)((w.npair_cap + 1) / 2) * sizeof(Chain);
+  b += (int64_t)w.nb_cap * (sizeof(double) + plan->ops->real_bytes);
+  *bytes = b;
+  return FOCK_OK;
+}
+
+fock_status fock_apply(fock_plan_t plan, const void* psi_G, int nb, const double* occ,
+                       void* vpsi_G, double* ex, double* dex, fock_stream_t stream) {
+  return apply_impl(plan, psi_G, nb, occ, 0, 1, vpsi_G, ex, dex, stream);
+}
+
+fock_status fock_apply_shard(fock_plan_t plan, const void* psi_G, int nb, const double* occ,
+                             int shard, int nshards, void* vpsi_G, double* ex, double* dex,
+                             fock_stream_t stream) {
+  return apply_impl(plan, psi_G, nb, occ, shard, nshards, vpsi_G, ex, dex, stream);
+}
+
+fock_status fock_pair_energies(fock_plan_t plan, const void* psi_G, int nb, const int32_t* pairs,
+                               int npairs, double* e, double* d, fock_stream_t stream) {
+  fock_status st = validate_apply(plan, psi_G, nb, e);
+  if (st != FOCK_OK) return st;
+  if (!pairs || npairs < 1) return fail(plan, FOCK_ERR_INVALID_ARG, "pairs is empty");
+  std::vector<int2> list(npairs);
+  for (int k = 0; k < npairs; ++k) {
+    const int i = pairs[2 * k], j = pairs[2 * k + 1];
+    if (i < 0 || j < 0 || i >= nb || j >= nb)
+      return fail(plan, FOCK_ERR_INVALID_ARG, "a band index is out of range");
+    list[k] = make_int2(i, j);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = ensure_workspace(plan, nb, npairs);
+  if (st != FOCK_OK) return st;
+  std::vector<Chain> chains;
+  chains_from_pairs(list, chains);
+  plan->sched_nb = -1;  // the device chain list is overwritten below
+  stats_reset(plan);
+  FOCK_CUDA(plan, cudaMemcpyAsync(plan->ws.chains, chains.data(), sizeof(Chain) * chains.size(),
+                                  cudaMemcpyHostToDevice, s));
+  FOCK_CUDA(plan, cudaMemsetAsync(plan->ws.epair, 0, sizeof(double) * npairs, s));
+  FOCK_CUDA(plan, cudaMemsetAsync(plan->ws.dpair, 0, sizeof(double) * npairs, s));
+  st = orbitals_to_real(plan, psi_G, nb, s);
+  if (st != FOCK_OK) return st;
+  const int nch = (int)chains.size();
+  for (int c = 0; c < nch; c += plan->chain_batch) {
+    const int cnt = std::min(plan->chain_batch, nch - c);
+    const Chain* ch = plan->ws.chains + c;
+    {
+      PhaseScope ps(plan, FOCK_PHASE_PAIR_FWD, 1, s);
+      FOCK_CUDA(plan, plan->ops->pair_fwd(plan->dp, plan->ws.psi, ch, cnt, plan->ws.h, s));
+    }
+    {
+      PhaseScope ps(plan, FOCK_PHASE_PAIR_COL, 1, s);
+      FOCK_CUDA(plan, plan->ops->pair_col(plan->dp, plan->ws.h, ch, cnt, plan->ws.epair,
+                                          plan->ws.dpair, s));
+    }
+  }
+  plan->stats.chains = nch;
+  plan->stats.pairs = npairs;
+  plan->stats.chain_batch = plan->chain_batch;
+  st = collect_timing(plan, s);
+  if (st != FOCK_OK) return st;
+  std::vector<double> he(npairs), hd(npairs);
+  FOCK_CUDA(plan, cudaMemcpyAsync(he.data(), plan->ws.epair, sizeof(double) * npairs,
+                                  cudaMemcpyDeviceToHost, s));
+  FOCK_CUDA(plan, cudaMemcpyAsync(hd.data(), plan->ws.dpair, sizeof(double) * npairs,
+                                  cudaMemcpyDeviceToHost, s));
+  FOCK_CUDA(plan, cudaStreamSynchronize(s));
+  const double inv2 = 1.0 / ((double)plan->dp.ntot * (double)plan->dp.ntot);
+  for (int k = 0; k < npairs; ++k) {
+    e[k] = he[k] * inv2;
+    if (d) d[k] = plan->dp.dvtab64 ? hd[k] * inv2 : 0.0;
+  }
+  return FOCK_OK;
+}
+
+fock_status fock_destroy(fock_plan_t plan) {
+  if (!plan) return FOCK_OK;
+  for (cudaEvent_t e : plan->events) cudaEventDestroy(e);
+  free_ws(plan->ws);
+  cudaFree(plan->d_gidx);
+  cudaFree(plan->d_gidxneg);
+  cudaFree(plan->d_tw);
+  cudaFree(plan->d_vtab);
+  cudaFree(plan->d_vtab64);
+  cudaFree(plan->d_dvtab64);
+  cudaFree(plan->d_result);
+  if (plan->h_result) cudaFreeHost(plan->h_result);
+  delete plan;
+  return FOCK_OK;
+}
+
+}  // extern "C"

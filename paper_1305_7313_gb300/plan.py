@@ -1,0 +1,110 @@
+"""Object wrapper around one fock_plan_t (the plan of include/fock.h)."""
+
+import numpy as np
+
+from . import _lib
+
+
+class FockPlan:
+    """A plane-wave cell on an N^3 grid with one Coulomb kernel and precision.
+
+    ``kernel``: ``SPENCER_ALAVI`` or ``ERFC`` (then ``omega`` in bohr^-1);
+    ``precision``: ``PREC_FP64`` or ``PREC_MIXED32``.
+    """
+
+    def __init__(self, grid, cell, ecut, kernel=_lib.SPENCER_ALAVI, omega=None,
+                 precision=_lib.PREC_FP64):
+        if isinstance(grid, int):
+            grid = (grid, grid, grid)
+        kp = () if kernel == _lib.SPENCER_ALAVI else (float(omega),)
+        self.grid = tuple(int(g) for g in grid)
+        self.cell = np.asarray(cell, dtype=np.float64).reshape(3, 3)
+        self.ecut = float(ecut)
+        self.kernel = kernel
+        self.omega = omega
+        self.precision = precision
+        self.handle = None
+        self.handle = _lib.fock_plan_create(self.grid, self.cell, self.ecut, kernel, kp, precision)
+        self.npw = _lib.fock_plan_npw(self.handle)
+        self._miller = None
+
+    @property
+    def miller(self):
+        if self._miller is None:
+            self._miller = _lib.fock_plan_gvectors(self.handle)
+        return self._miller
+
+    @property
+    def volume(self):
+        return float(abs(np.linalg.det(self.cell)))
+
+    def set_batch(self, chain_batch):
+        _lib.fock_plan_set_batch(self.handle, chain_batch)
+
+    def set_timing(self, enable):
+        _lib.fock_plan_set_timing(self.handle, enable)
+
+    def stats(self):
+        return _lib.fock_plan_stats(self.handle)
+
+    def reserve(self, nb_max):
+        _lib.fock_plan_reserve(self.handle, nb_max)
+
+    def device_bytes(self):
+        return _lib.fock_plan_device_bytes(self.handle)
+
+    def apply(self, psi_G, occ, vpsi_G=None, want_ex=True, want_dex=False, stream=None):
+        """(V_x psi, E_x, dE_x/domega) for device orbitals ``psi_G`` [nb, npw] complex128."""
+        import torch
+        if vpsi_G is None:
+            vpsi_G = torch.empty_like(psi_G)
+        ex, dex = _lib.fock_apply(self.handle, psi_G, occ, vpsi_G, want_ex, want_dex, stream)
+        return vpsi_G, ex, dex
+
+    def apply_shard(self, psi_G, occ, shard, nshards, vpsi_G=None, want_ex=True, want_dex=False,
+                    stream=None):
+        import torch
+        if vpsi_G is None:
+            vpsi_G = torch.empty_like(psi_G)
+        ex, dex = _lib.fock_apply_shard(self.handle, psi_G, occ, shard, nshards, vpsi_G, want_ex,
+                                        want_dex, stream)
+        return vpsi_G, ex, dex
+
+    def apply_host(self, psi_host, occ, out_host=None, want_dex=False):
+        """End-to-end call from host memory: copy in, apply, copy the result back.
+
+        ``psi_host`` is a (preferably pinned) CPU complex128 tensor or a numpy
+        array; returns (V_x psi on the host, E_x, dE_x/domega).
+        """
+        import torch
+        if isinstance(psi_host, np.ndarray):
+            psi_host = torch.from_numpy(np.ascontiguousarray(psi_host))
+        dev = torch.device("cuda", torch.cuda.current_device())
+        psi = psi_host.to(dev, non_blocking=True)
+        vpsi = torch.empty_like(psi)
+        ex, dex = _lib.fock_apply(self.handle, psi, occ, vpsi, True, want_dex)
+        if out_host is None:
+            out_host = torch.empty(vpsi.shape, dtype=vpsi.dtype, pin_memory=True)
+        out_host.copy_(vpsi, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return out_host, ex, dex
+
+    def pair_energies(self, psi_G, pairs, want_d=False, stream=None):
+        return _lib.fock_pair_energies(self.handle, psi_G, pairs, want_d, stream)
+
+    def close(self):
+        if self.handle is not None:
+            _lib.fock_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

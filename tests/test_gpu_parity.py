@@ -1,0 +1,143 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances:
+* FP64 form: 1e-10 relative (max |diff| / max |oracle|) on V_x psi and on E_x,
+  the target of the FP64 path.
+* mixed form (complex64 transforms): a transform of length Ntot in FP32 carries
+  a relative error of a few u * log2(Ntot) with u = 2^-24 = 6e-8 and
+  log2(Ntot) ~ 17-20, i.e. ~1e-6 RMS; the pair potential goes through two of
+  them and a product, V_x psi through one more and an FP32 sum over bands.
+  Bound used: 2e-5 on V_x psi (max norm), 5e-6 on E_x and dE_x/domega, whose
+  terms are all non-negative and summed in FP64.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.kernels import ERFC as O_ERFC, SPENCER_ALAVI as O_SA
+from paper_1305_7313_gb300 import FockPlan, synth
+from paper_1305_7313_gb300 import _lib
+from tests._common import cubic, rel_inf, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32_V = 2e-5
+TOL32_E = 5e-6
+
+
+def setup_case(N, L, ecut, nb, seed, kind=_lib.SPENCER_ALAVI, omega=None, prec=_lib.PREC_FP64,
+               occ=None, cell=None):
+    torch = require_gpu()
+    cell = cubic(L) if cell is None else np.asarray(cell, dtype=np.float64).ravel()
+    plan = FockPlan(N, cell, ecut, kind, omega, prec)
+    mill, _ = oracle.gsphere((N, N, N), cell, ecut)
+    assert np.array_equal(plan.miller, mill)
+    c = synth.orbitals(mill, cell, nb, seed)
+    occ = np.full(nb, 2.0) if occ is None else np.asarray(occ, dtype=np.float64)
+    psi = torch.from_numpy(c).cuda()
+    return dict(torch=torch, plan=plan, mill=mill, c=c, occ=occ, psi=psi, cell=cell, N=N,
+                kind=O_SA if kind == _lib.SPENCER_ALAVI else O_ERFC, omega=omega)
+
+
+def oracle_of(case):
+    return oracle.fock_apply(case["c"], case["occ"], case["mill"], (case["N"],) * 3, case["cell"],
+                             case["kind"], case["omega"])
+
+
+def test_small_fp64_matches_oracle():
+    # 24^3 grid, L = 10, Ecut = 10 Ha, 8 bands, f = 2, Spencer-Alavi
+    case = setup_case(24, 10.0, 10.0, 8, 1305)
+    vpsi, ex, _ = case["plan"].apply(case["psi"], case["occ"])
+    vref, eref, _ = oracle_of(case)
+    assert rel_inf(vpsi.cpu().numpy(), vref) <= TOL64
+    assert abs(ex - eref) <= TOL64 * abs(eref)
+
+
+def test_fp64_many_batches_ragged_tails_uneven_occupations():
+    # 48^3 grid, 37 bands (odd: a lone last pair and a lone last band), chains in
+    # batches of 5 so both the pair loop and the band transforms have ragged tails
+    occ = np.linspace(2.0, 0.0, 37)
+    occ[5] = -0.5
+    case = setup_case(48, 13.5, 12.0, 37, 77, occ=occ)
+    case["plan"].set_batch(5)
+    vpsi, ex, _ = case["plan"].apply(case["psi"], case["occ"])
+    vref, eref, _ = oracle_of(case)
+    assert rel_inf(vpsi.cpu().numpy(), vref) <= TOL64
+    assert abs(ex - eref) <= TOL64 * abs(eref)
+
+
+def test_fp64_erfc_energy_derivative_and_general_cell():
+    cell = np.array([[9.0, 0.4, 0.0], [0.3, 9.5, 0.2], [0.0, -0.3, 8.5]])
+    case = setup_case(32, None, 8.0, 6, 5, kind=_lib.ERFC, omega=0.3, cell=cell,
+                      occ=[2.0, 2.0, 1.5, 1.0, 0.5, 0.25])
+    vpsi, ex, dex = case["plan"].apply(case["psi"], case["occ"], want_dex=True)
+    vref, eref, dref = oracle_of(case)
+    assert rel_inf(vpsi.cpu().numpy(), vref) <= TOL64
+    assert abs(ex - eref) <= TOL64 * abs(eref)
+    assert abs(dex - dref) <= TOL64 * abs(dref)
+
+
+def test_single_band_and_two_bands():
+    for nb in (1, 2, 3):
+        case = setup_case(24, 10.0, 10.0, nb, 40 + nb)
+        vpsi, ex, _ = case["plan"].apply(case["psi"], case["occ"])
+        vref, eref, _ = oracle_of(case)
+        assert rel_inf(vpsi.cpu().numpy(), vref) <= TOL64
+        assert abs(ex - eref) <= TOL64 * abs(eref)
+
+
+def test_shards_sum_to_the_full_apply():
+    # the band-group split of the paper's EXX loop: partial results add up
+    case = setup_case(24, 10.0, 10.0, 11, 9)
+    vfull, efull, _ = case["plan"].apply(case["psi"], case["occ"])
+    vsum = 0.0
+    esum = 0.0
+    for s in range(3):
+        v, e, _ = case["plan"].apply_shard(case["psi"], case["occ"], s, 3)
+        vsum = vsum + v.cpu().numpy()
+        esum += e
+    assert rel_inf(vsum, vfull.cpu().numpy()) <= 1e-13
+    assert abs(esum - efull) <= 1e-13 * abs(efull)
+
+
+def test_pair_energies_match_the_oracle():
+    case = setup_case(24, 10.0, 10.0, 6, 21, kind=_lib.ERFC, omega=0.4)
+    pairs = [(0, 0), (0, 5), (3, 2), (4, 4), (1, 3)]
+    e, d = case["plan"].pair_energies(case["psi"], pairs, want_d=True)
+    psi = oracle.orbitals_to_real(case["c"], case["mill"], (24,) * 3, case["cell"], real=True)
+    from oracle.fock import kernel_grid
+    vg, dvg = kernel_grid(O_ERFC, (24,) * 3, case["cell"], 0.4)
+    for k, (i, j) in enumerate(pairs):
+        er, dr = oracle.pair_energy(psi[i], psi[j], vg, dvg)
+        assert abs(e[k] - er) <= TOL64 * abs(er)
+        assert abs(d[k] - dr) <= TOL64 * abs(dr)
+
+
+def test_mixed_precision_matches_oracle_within_stated_bound():
+    case = setup_case(48, 13.5, 12.0, 20, 31, kind=_lib.ERFC, omega=0.106, prec=_lib.PREC_MIXED32)
+    vpsi, ex, dex = case["plan"].apply(case["psi"], case["occ"], want_dex=True)
+    vref, eref, dref = oracle_of(case)
+    assert rel_inf(vpsi.cpu().numpy(), vref) <= TOL32_V
+    assert abs(ex - eref) <= TOL32_E * abs(eref)
+    assert abs(dex - dref) <= TOL32_E * abs(dref)
+
+
+def test_invalid_calls_fail_cleanly():
+    case = setup_case(24, 10.0, 10.0, 4, 3)
+    torch = case["torch"]
+    plan = case["plan"]
+    with pytest.raises(_lib.FockError) as e:
+        _lib.fock_apply(plan.handle, case["psi"], case["occ"], case["psi"])  # in place
+    assert e.value.status == 1
+    with pytest.raises(_lib.FockError):
+        _lib.fock_apply_shard(plan.handle, case["psi"], case["occ"], 3, 3, torch.empty_like(case["psi"]))
+    with pytest.raises(_lib.FockError):
+        _lib.fock_apply(plan.handle, case["psi"], [2.0, np.nan, 2.0, 2.0], torch.empty_like(case["psi"]))
+    with pytest.raises(_lib.FockError):
+        plan.pair_energies(case["psi"], [(0, 4)])
+    # the plan still works afterwards
+    vpsi, ex, _ = plan.apply(case["psi"], case["occ"])
+    vref, eref, _ = oracle_of(case)
+    assert abs(ex - eref) <= TOL64 * abs(eref)
