@@ -108,11 +108,13 @@ class ClockSampler:
 
 
 def gpu_id():
+    """nvidia-smi's name for the current device: its UUID ("GPU-..."), else its index."""
     import torch
     try:
-        return str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
     except Exception:
-        return "0"
+        return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
 
 
 def time_form(plan, psi, occ, steps, warmup, want_dex=False, rank=0, world=1):
