@@ -203,6 +203,29 @@ fock_status fock_apply_shard(fock_plan_t plan, const void* psi_G, int nb, const 
 fock_status fock_pair_energies(fock_plan_t plan, const void* psi_G, int nb, const int32_t* pairs,
                                int npairs, double* e, double* d, fock_stream_t stream);
 
+/*
+ * fock_pair_energies_static — fock_pair_energies without any device
+ * allocation.  The paper has no counterpart: this serves callers that cannot
+ * call cudaMalloc when they need the pair energies (code running during CUDA
+ * stream capture, frameworks that own every device allocation or impose a
+ * fixed memory budget, latency-bound loops that cannot afford an allocation or
+ * its implicit synchronisation).
+ *   Arguments, results and errors as in fock_pair_energies (pairs, e and d are
+ *   host arrays; the call synchronises the stream).
+ *   Working memory: one static device array of 32 MiB per device, held from
+ *   library load to process exit.  It must hold nb*N^3 reals of the plan's
+ *   precision (8 or 4 bytes), 8*npairs + 16*npairs + 16*npairs bytes, and one
+ *   transform buffer of N^2 (N+2) complex elements; larger requests fail with
+ *   FOCK_ERR_INVALID_ARG before any work is queued.
+ *   The first call on a device (with that device current) looks up the array's
+ *   device address; make that first call before any stream capture.
+ *   All calls share the array: calls whose work overlaps on the GPU race.
+ *   The plan's own workspace is not touched, but its tables are used.
+ */
+fock_status fock_pair_energies_static(fock_plan_t plan, const void* psi_G, int nb,
+                                      const int32_t* pairs, int npairs, double* e, double* d,
+                                      fock_stream_t stream);
+
 /* Release the plan and everything it holds.  NULL is accepted. */
 fock_status fock_destroy(fock_plan_t plan);
 

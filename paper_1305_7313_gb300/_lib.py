@@ -69,6 +69,8 @@ _SIGNATURES = {
     "fock_apply_shard": [_vp, _vp, ctypes.c_int, _c_dbl_p, ctypes.c_int, ctypes.c_int, _vp,
                          _c_dbl_p, _c_dbl_p, _vp],
     "fock_pair_energies": [_vp, _vp, ctypes.c_int, _c_i32_p, ctypes.c_int, _c_dbl_p, _c_dbl_p, _vp],
+    "fock_pair_energies_static": [_vp, _vp, ctypes.c_int, _c_i32_p, ctypes.c_int, _c_dbl_p, _c_dbl_p,
+                                  _vp],
     "fock_destroy": [_vp],
     "fock_status_string": [ctypes.c_int],
     "fock_last_error": [_vp],
@@ -244,6 +246,20 @@ def fock_pair_energies(plan, psi_G, pairs, want_d=False, stream=None):
                                      e.ctypes.data_as(_c_dbl_p),
                                      d.ctypes.data_as(_c_dbl_p) if want_d else None,
                                      _stream(stream)), plan)
+    return (e, d) if want_d else e
+
+
+def fock_pair_energies_static(plan, psi_G, pairs, want_d=False, stream=None):
+    """fock_pair_energies computed in the library's static device scratch (no allocation)."""
+    nb = psi_G.shape[0]
+    a = _dev_ptr(psi_G, "psi_G")
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    e = np.empty(len(pr))
+    d = np.empty(len(pr))
+    _check(load().fock_pair_energies_static(plan, a, nb, pr.ctypes.data_as(_c_i32_p), len(pr),
+                                            e.ctypes.data_as(_c_dbl_p),
+                                            d.ctypes.data_as(_c_dbl_p) if want_d else None,
+                                            _stream(stream)), plan)
     return (e, d) if want_d else e
 
 

@@ -58,6 +58,7 @@ def _jobs():
                                  "-I" + os.path.join(cuda, "include")] + inc +
                  ["-c", os.path.join(CSRC, "fock_plan.cpp")]))
     jobs.append(("fock_common.o", nv + ["-c", os.path.join(CSRC, "fock_common.cu")]))
+    jobs.append(("fock_static.o", nv + ["-c", os.path.join(CSRC, "fock_static.cu")]))
     for n in grid_sizes():
         for tag, t in (("f64", "double"), ("f32", "float")):
             jobs.append(("fock_%s_%d.o" % (tag, n),

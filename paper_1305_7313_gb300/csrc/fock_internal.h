@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 
+struct fock_plan;
+
 namespace fockx {
 
 // Two band pairs that share one complex transform: pair a = (ai, aj) in the
@@ -60,6 +62,15 @@ struct KernelOps {
 
 // Kernels for grid size n and precision (0: FP64, 1: mixed); NULL if not built.
 const KernelOps* find_kernel_ops(int prec, int n);
+
+// What code outside fock_plan.cpp may read of a plan.
+struct PlanView {
+  int device;
+  const KernelOps* ops;
+  DevPlan dp;
+};
+bool plan_view(struct ::fock_plan* plan, PlanView* out);
+void plan_set_error(struct ::fock_plan* plan, const char* msg);
 
 // E = scale * sum_p f_i f_j (1 or 2) e_p over the pairs; out[0] = E, out[1] = dE.
 cudaError_t launch_energy_reduce(const int2* pairs, int npairs, const double* occ,

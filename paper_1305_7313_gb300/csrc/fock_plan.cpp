@@ -489,6 +489,22 @@ bool supported_n(int n) {
 
 }  // namespace
 
+namespace fockx {
+
+bool plan_view(fock_plan* plan, PlanView* out) {
+  if (!plan || !out) return false;
+  out->device = plan->device;
+  out->ops = plan->ops;
+  out->dp = plan->dp;
+  return true;
+}
+
+void plan_set_error(fock_plan* plan, const char* msg) {
+  if (plan) plan->err = msg;
+}
+
+}  // namespace fockx
+
 extern "C" {
 
 const char* fock_status_string(fock_status s) {
