@@ -251,6 +251,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-bands", type=int, default=32)
+    ap.add_argument("--nb", type=int, default=None,
+                    help="override the band count of the workloads (small profiling cases)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -271,6 +273,8 @@ def main():
 
     # ---- FP64 form (the headline workload)
     w = workload(args.workload)
+    if args.nb:
+        w["nb"] = args.nb
     n = w["N"]
     from paper_1305_7313_gb300.workloads import cubic_cell
     plan = FockPlan(n, cubic_cell(w["L"]), w["ecut"], w["kernel"], w["omega"], w["prec"])
@@ -306,6 +310,8 @@ def main():
     mixed = None
     if not args.no_mixed:
         wm = workload(args.mixed_workload)
+        if args.nb:
+            wm["nb"] = args.nb
         planm = FockPlan(wm["N"], cubic_cell(wm["L"]), wm["ecut"], wm["kernel"], wm["omega"], wm["prec"])
         _, cm, occm = make_inputs(wm, planm.miller)
         psim = torch.from_numpy(cm).cuda()

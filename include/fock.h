@@ -113,6 +113,18 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
 fock_status fock_gsphere(const int grid[3], const double cell[9], double ecut_ha, int64_t* npw,
                          int32_t* miller, int64_t capacity);
 
+/*
+ * fock_schedule — the unique pairs (i <= j) that fock_apply_shard(..., shard,
+ * nshards, ...) evaluates for nb bands, in the library's fixed schedule (host
+ * only, no GPU).  This is the band-group split of §5 (Fig. 3) as the library
+ * draws it: the shards are disjoint and together hold every unique pair once.
+ *   pairs    host int32 [capacity][2] or NULL (call with NULL to size it).
+ *   npairs   host int64; receives the number of pairs of the shard.
+ * Errors: INVALID_ARG.
+ */
+fock_status fock_schedule(int nb, int shard, int nshards, int32_t* pairs, int64_t capacity,
+                          int64_t* npairs);
+
 /* Number of plane waves npw in the sphere.  npw: host int64. */
 fock_status fock_plan_npw(fock_plan_t plan, int64_t* npw);
 

@@ -21,6 +21,8 @@ from ._lib import (  # noqa: F401
     fock_gsphere,
     fock_last_error,
     fock_pair_energies,
+    fock_pair_energies_static,
+    fock_schedule,
     fock_plan_create,
     fock_plan_device_bytes,
     fock_plan_gvectors,

@@ -58,6 +58,7 @@ _SIGNATURES = {
     "fock_plan_create": [ctypes.POINTER(_vp), _c_int_p, _c_dbl_p, ctypes.c_double, ctypes.c_int,
                          _c_dbl_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint],
     "fock_gsphere": [_c_int_p, _c_dbl_p, ctypes.c_double, _c_i64_p, _c_i32_p, ctypes.c_int64],
+    "fock_schedule": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_i32_p, ctypes.c_int64, _c_i64_p],
     "fock_plan_npw": [_vp, _c_i64_p],
     "fock_plan_gvectors": [_vp, _c_i32_p],
     "fock_plan_reserve": [_vp, ctypes.c_int],
@@ -148,6 +149,17 @@ def fock_gsphere(grid, cell, ecut):
     _check(lib.fock_gsphere(g, cp, float(ecut), ctypes.byref(n), None, 0))
     out = np.empty((n.value, 3), dtype=np.int32)
     _check(lib.fock_gsphere(g, cp, float(ecut), ctypes.byref(n), out.ctypes.data_as(_c_i32_p), n.value))
+    return out
+
+
+def fock_schedule(nb, shard=0, nshards=1):
+    """Unique pairs [npairs, 2] (int32) that shard `shard` of `nshards` evaluates (host only)."""
+    lib = load()
+    n = ctypes.c_int64()
+    _check(lib.fock_schedule(int(nb), int(shard), int(nshards), None, 0, ctypes.byref(n)))
+    out = np.empty((n.value, 2), dtype=np.int32)
+    _check(lib.fock_schedule(int(nb), int(shard), int(nshards), out.ctypes.data_as(_c_i32_p), n.value,
+                             ctypes.byref(n)))
     return out
 
 

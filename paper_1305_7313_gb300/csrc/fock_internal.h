@@ -32,6 +32,7 @@ struct DevPlan {
   const void* vtab;    // [N][N][k3h] v(G) / Ntot in the working precision
   const double* vtab64;   // [N][N][k3h] v(G) in FP64
   const double* dvtab64;  // [N][N][k3h] dv/domega in FP64 (NULL: not needed)
+  const void* dvtab;      // [N][N][k3h] dv/domega in the working precision
   double inv_ntot;     // 1 / Ntot
   double psi_scale;    // 1 / sqrt(Omega)
   double out_scale;    // sqrt(Omega) / Ntot

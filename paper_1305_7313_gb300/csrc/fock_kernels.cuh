@@ -70,10 +70,60 @@ struct Geo {
   static constexpr int THR_COLH = (NC * TLC + 31) / 32 * 32;
   static constexpr int THR_COLF = (N * TLP + 31) / 32 * 32;
   static_assert(THR_PLANE <= 1024 && THR_COLH <= 1024, "CTA too large");
+  // CTAs per SM the column pass is register-budgeted for (shared memory allows
+  // two in FP32 up to N = 96, one in FP64)
+  static constexpr int MIN_CTAS = (sizeof(T) == 4) ? 2 : 1;
   static constexpr size_t SMEM_PLANE = sizeof(C) * (size_t)(N * RP + N);
-  static constexpr size_t SMEM_COLH = sizeof(C) * (size_t)(N * NC + N) + 32 * 4 * sizeof(double);
+  static constexpr size_t SMEM_COLH = sizeof(C) * (size_t)(N * NC + N) + (32 + 12) * 4 * sizeof(double);
   static constexpr size_t SMEM_COLF = sizeof(C) * (size_t)(N * N + N);
 };
+
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) += (h2, l2) in float-float arithmetic (about 48 significant bits).
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float h2, float l2) {
+  float s, e;
+  two_sum(hi, h2, s, e);
+  e += lo + l2;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+// CTA sum of four float partials, carried in float-float across threads and
+// warps and finished in FP64 by thread 0 (valid there).  Keeps the FP64 pipe
+// out of the FP32 kernels.
+__device__ inline void block_sum4_ff(const float v[4], double out[4], double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  float hi[4], lo[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    hi[k] = v[k];
+    lo[k] = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_down_sync(0xffffffffu, hi[k], o);
+      const float l2 = __shfl_down_sync(0xffffffffu, lo[k], o);
+      ff_add(hi[k], lo[k], h2, l2);
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[warp * 4 + k] = (double)hi[k] + (double)lo[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) {
+      double s = out[k];
+      for (int w = 0; w < nw; ++w) s += red[w * 4 + k];
+      out[k] = s;
+    }
+  }
+}
 
 template <class T>
 __device__ __forceinline__ void load_twiddles(cplx<T>* tw, const DevPlan& g) {
@@ -226,7 +276,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
 }
 
 template <class T, int N>
-__global__ void __launch_bounds__(Geo<T, N>::THR_COLH)
+__global__ void __launch_bounds__(Geo<T, N>::THR_COLH, Geo<T, N>::MIN_CTAS)
     k_pair_col(DevPlan g, cplx<T>* __restrict__ H, const Chain* __restrict__ chains,
                double* __restrict__ epair, double* __restrict__ dpair) {
   using C = cplx<T>;
@@ -248,45 +298,97 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_COLH)
   fft_lines<T, N, -1, NC, G::TLC, 1, NC>(S, tw);  // along i1
 
   // kernel multiply and energy partials
-  const T* vt = static_cast<const T*>(g.vtab);
   const bool want_d = g.dvtab64 != nullptr;
   const int m2 = freq_of(k2, N);
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // e_a, e_b, d_a, d_b
-  T accf[4] = {T(0), T(0), T(0), T(0)};
-  for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
-    const int k1 = e / NC, c = e - k1 * NC;
-    const int s = c >= KH ? 1 : 0;
-    const int k3 = c - s * KH;
-    const int64_t vi = ((int64_t)k1 * N + k2) * KH + k3;
-    const T wgt = (k3 == 0 || 2 * k3 == N) ? T(1) : T(2);
-    C z = S[e];
-    const int m1 = freq_of(k1, N), m3 = freq_of(k3, N);
-    const int mm = m1 * m1 + m2 * m2 + m3 * m3;
-    if (sizeof(T) == 8 || mm <= g.msmall2) {
-      // kernel term in FP64
-      const double zx = z.x, zy = z.y, a2 = zx * zx + zy * zy;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // e_a, e_b, d_a, d_b (FP64 terms)
+  float acc_f32[4] = {0.f, 0.f, 0.f, 0.f};  // the same from the FP32 terms (mixed form)
+  if constexpr (sizeof(T) == 8) {
+    for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
+      const int k1 = e / NC, c = e - k1 * NC;
+      const int s = c >= KH ? 1 : 0;
+      const int k3 = c - s * KH;
+      const int64_t vi = ((int64_t)k1 * N + k2) * KH + k3;
+      const double wgt = (k3 == 0 || 2 * k3 == N) ? 1.0 : 2.0;
+      C z = S[e];
+      const double a2 = z.x * z.x + z.y * z.y;
       const double v = g.vtab64[vi];
-      acc[s] += double(wgt) * v * a2;
-      if (want_d) acc[2 + s] += double(wgt) * g.dvtab64[vi] * a2;
+      const double te = wgt * v * a2;
+      const double td = want_d ? wgt * g.dvtab64[vi] * a2 : 0.0;
+      if (s) {
+        acc[1] += te;
+        acc[3] += td;
+      } else {
+        acc[0] += te;
+        acc[2] += td;
+      }
       const double vs = v * g.inv_ntot;
-      z.x = T(zx * vs);
-      z.y = T(zy * vs);
-    } else {
+      z.x *= vs;
+      z.y *= vs;
+      S[e] = z;
+    }
+  } else {
+    // The kernel terms of the smallest |m| (|m|^2 <= msmall2) in FP64: at most
+    // 3 (m1) x 2 (m3 = 0, 1 in the stored half) x 2 (A, B) points of this row,
+    // one thread each.  The FP32 loop below skips exactly these points.
+    if (m2 * m2 <= g.msmall2 && threadIdx.x < 12) {
+      const int t = threadIdx.x;
+      const int s = t & 1, m3 = (t >> 1) & 1, m1 = (t >> 2) - 1;
+      if (m1 * m1 + m2 * m2 + m3 * m3 <= g.msmall2) {
+        const int k1 = (m1 + N) % N, k3 = m3;
+        const int e = k1 * NC + s * KH + k3;
+        const int64_t vi = ((int64_t)k1 * N + k2) * KH + k3;
+        const double wgt = (k3 == 0 || 2 * k3 == N) ? 1.0 : 2.0;
+        C z = S[e];
+        const double zx = z.x, zy = z.y, a2 = zx * zx + zy * zy;
+        const double v = g.vtab64[vi];
+        const double te = wgt * v * a2;
+        const double td = want_d ? wgt * g.dvtab64[vi] * a2 : 0.0;
+        if (s) {
+          acc[1] += te;
+          acc[3] += td;
+        } else {
+          acc[0] += te;
+          acc[2] += td;
+        }
+        const double vs = v * g.inv_ntot;
+        z.x = T(zx * vs);
+        z.y = T(zy * vs);
+        S[e] = z;
+      }
+    }
+    const T* vt = static_cast<const T*>(g.vtab);    // v / Ntot
+    const T* dvt = static_cast<const T*>(g.dvtab);  // dv/domega
+    T accf[4] = {T(0), T(0), T(0), T(0)};
+    for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
+      const int k1 = e / NC, c = e - k1 * NC;
+      const int s = c >= KH ? 1 : 0;
+      const int k3 = c - s * KH;
+      const int m1 = freq_of(k1, N), m3 = freq_of(k3, N);
+      if (m1 * m1 + m2 * m2 + m3 * m3 <= g.msmall2) continue;
+      const int vi = (k1 * N + k2) * KH + k3;
+      const T wgt = (k3 == 0 || 2 * k3 == N) ? T(1) : T(2);
+      C z = S[e];
       const T a2 = z.x * z.x + z.y * z.y;
-      const T v = vt[vi];  // v / Ntot
-      accf[s] += wgt * v * a2;
-      if (want_d) accf[2 + s] += wgt * T(g.dvtab64[vi]) * a2;
+      const T v = vt[vi];
+      const T te = wgt * v * a2;
+      const T td = want_d ? wgt * dvt[vi] * a2 : T(0);
+      if (s) {
+        accf[1] += te;
+        accf[3] += td;
+      } else {
+        accf[0] += te;
+        accf[2] += td;
+      }
       z.x *= v;
       z.y *= v;
+      S[e] = z;
     }
-    S[e] = z;
-  }
-  if (sizeof(T) != 8) {
-    const double ntot = double(g.ntot);
-    acc[0] += double(accf[0]) * ntot;  // the working-precision table holds v / Ntot
-    acc[1] += double(accf[1]) * ntot;
-    acc[2] += double(accf[2]);
-    acc[3] += double(accf[3]);
+    // per-thread FP32 sums of at most N (N+2) / blockDim non-negative terms;
+    // the table holds v / Ntot, undone in FP64 after the CTA reduction
+    acc_f32[0] = accf[0];
+    acc_f32[1] = accf[1];
+    acc_f32[2] = accf[2];
+    acc_f32[3] = accf[3];
   }
   __syncthreads();
   fft_lines<T, N, +1, NC, G::TLC, 1, NC>(S, tw);  // inverse along k1
@@ -294,7 +396,26 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_COLH)
     const int i1 = e / NC, c = e - i1 * NC;
     Hc[((int64_t)i1 * N + k2) * NC + c] = S[e];
   }
-  block_sum4(acc, red);
+  if constexpr (sizeof(T) == 8) {
+    block_sum4(acc, red);
+  } else {
+    double tot[4] = {0.0, 0.0, 0.0, 0.0};
+    block_sum4_ff(acc_f32, tot, red);
+    __syncthreads();
+    if (threadIdx.x < 12) {
+      // the FP64 small-|m| terms live in threads 0..11 only
+      for (int k = 0; k < 4; ++k) red[32 * 4 + threadIdx.x * 4 + k] = acc[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double ntot = double(g.ntot);
+      for (int k = 0; k < 4; ++k) {
+        double s = (k < 2 ? ntot : 1.0) * tot[k];
+        for (int t = 0; t < 12; ++t) s += red[32 * 4 + t * 4 + k];
+        acc[k] = s;
+      }
+    }
+  }
   if (threadIdx.x == 0) {
     atomicAdd(&epair[ch.pa], acc[0]);
     if (ch.pb >= 0) atomicAdd(&epair[ch.pb], acc[1]);
@@ -339,26 +460,84 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
   fft_lines<T, N, +1, N, G::TLP, RP, 1>(P, tw);  // along k3
   const int64_t plane0 = (int64_t)i1 * N * N;
   const bool hb = ch.bi >= 0;
-  const T fai = occ[ch.ai], faj = occ[ch.aj];
-  const T fbi = hb ? occ[ch.bi] : T(0), fbj = hb ? occ[ch.bj] : T(0);
-  const T* pai = psi + (int64_t)ch.ai * g.ntot + plane0;
-  const T* paj = psi + (int64_t)ch.aj * g.ntot + plane0;
-  const T* pbi = psi + (int64_t)(hb ? ch.bi : 0) * g.ntot + plane0;
-  const T* pbj = psi + (int64_t)(hb ? ch.bj : 0) * g.ntot + plane0;
-  T* wai = W + (int64_t)ch.ai * g.ntot + plane0;
-  T* waj = W + (int64_t)ch.aj * g.ntot + plane0;
-  T* wbi = W + (int64_t)(hb ? ch.bi : 0) * g.ntot + plane0;
-  T* wbj = W + (int64_t)(hb ? ch.bj : 0) * g.ntot + plane0;
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int i2 = e / N, i3 = e - i2 * N;
-    const C z = P[i2 * RP + i3];
-    const T ai = pai[e], aj = paj[e];
-    atomic_add_real(waj + e, -fai * ai * z.x);
-    if (ch.ai != ch.aj) atomic_add_real(wai + e, -faj * aj * z.x);
-    if (hb) {
-      const T bi = pbi[e], bj = pbj[e];
-      atomic_add_real(wbj + e, -fbi * bi * z.y);
-      if (ch.bi != ch.bj) atomic_add_real(wbi + e, -fbj * bj * z.y);
+  // Up to four updates k, W[tgt_k] -= f[src_k] psi[src_k] phi:
+  //   k = 0: W_aj -= f_ai psi_ai phi_a      k = 1: W_ai -= f_aj psi_aj phi_a (i != j)
+  //   k = 2: W_bj -= f_bi psi_bi phi_b      k = 3: W_bi -= f_bj psi_bj phi_b (i != j)
+  // Updates of the same band are summed first (into[k] = first slot with that
+  // band), so each distinct band costs one atomic per point.
+  int tgt[4] = {ch.aj, ch.ai != ch.aj ? ch.ai : -1, hb ? ch.bj : -1, (hb && ch.bi != ch.bj) ? ch.bi : -1};
+  const int src[4] = {ch.ai, ch.aj, hb ? ch.bi : 0, hb ? ch.bj : 0};
+  const T f[4] = {occ[ch.ai], occ[ch.aj], hb ? occ[ch.bi] : T(0), hb ? occ[ch.bj] : T(0)};
+  int into[4] = {0, 1, 2, 3};  // which slot a contribution is added to
+#pragma unroll
+  for (int k = 1; k < 4; ++k)
+#pragma unroll
+    for (int m = 0; m < k; ++m)
+      if (into[k] == k && tgt[k] >= 0 && tgt[m] == tgt[k]) into[k] = m;
+  const T* ps[4];
+  T* wt[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    ps[k] = psi + (int64_t)src[k] * g.ntot + plane0;
+    wt[k] = W + (int64_t)(tgt[k] >= 0 ? tgt[k] : 0) * g.ntot + plane0;
+  }
+  if constexpr (sizeof(T) == 4) {
+    static_assert(N % 4 == 0, "vector updates need N divisible by 4");
+    for (int e4 = threadIdx.x; e4 < N * N / 4; e4 += blockDim.x) {
+      const int e = 4 * e4;
+      const int i2 = e / N, i3 = e - i2 * N;
+      float4 phia, phib;
+      {
+        const C z0 = P[i2 * RP + i3], z1 = P[i2 * RP + i3 + 1], z2 = P[i2 * RP + i3 + 2],
+                z3 = P[i2 * RP + i3 + 3];
+        phia = make_float4(z0.x, z1.x, z2.x, z3.x);
+        phib = make_float4(z0.y, z1.y, z2.y, z3.y);
+      }
+      float4 c[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        c[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tgt[k] < 0) continue;
+        const float4 p = *reinterpret_cast<const float4*>(ps[k] + e);
+        const float4 ph = k < 2 ? phia : phib;
+        const float m = -f[k];
+        c[k] = make_float4(m * p.x * ph.x, m * p.y * ph.y, m * p.z * ph.z, m * p.w * ph.w);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (tgt[r] < 0 || into[r] != r) continue;
+        float4 a = c[r];
+#pragma unroll
+        for (int k = r + 1; k < 4; ++k) {
+          if (into[k] == r) {
+            a.x += c[k].x;
+            a.y += c[k].y;
+            a.z += c[k].z;
+            a.w += c[k].w;
+          }
+        }
+        float* dst = wt[r] + e;
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(a.x), "f"(a.y),
+                     "f"(a.z), "f"(a.w)
+                     : "memory");
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+      const int i2 = e / N, i3 = e - i2 * N;
+      const C z = P[i2 * RP + i3];
+      T c[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) c[k] = tgt[k] < 0 ? T(0) : -f[k] * ps[k][e] * (k < 2 ? z.x : z.y);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (tgt[r] < 0 || into[r] != r) continue;
+        T a = c[r];
+#pragma unroll
+        for (int k = r + 1; k < 4; ++k)
+          if (into[k] == r) a += c[k];
+        atomic_add_real(wt[r] + e, a);
+      }
     }
   }
 }

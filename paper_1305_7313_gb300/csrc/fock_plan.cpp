@@ -77,6 +77,7 @@ struct fock_plan {
   int* d_gidxneg = nullptr;
   void* d_tw = nullptr;
   void* d_vtab = nullptr;
+  void* d_dvtab = nullptr;
   double* d_vtab64 = nullptr;
   double* d_dvtab64 = nullptr;
   double* d_result = nullptr;
@@ -214,18 +215,26 @@ void kernel_value(const fock_plan* p, double g2, double* v, double* dv) {
 // Unique pairs i <= j in band blocks of kBandBlock (block rows outer), i outer and j
 // inner inside a block, so consecutive pairs share psi_i and a batch of chains
 // touches a few blocks of orbitals.  Chain k holds pairs 2k and 2k+1.
-void build_schedule(fock_plan* p, int nb) {
-  p->pairs.clear();
-  p->pairs.reserve((size_t)nb * (nb + 1) / 2);
+void schedule_pairs(int nb, std::vector<int2>& pairs) {
+  pairs.clear();
+  pairs.reserve((size_t)nb * (nb + 1) / 2);
   const int nblk = (nb + kBandBlock - 1) / kBandBlock;
   for (int bi = 0; bi < nblk; ++bi) {
     for (int bj = bi; bj < nblk; ++bj) {
       const int i0 = bi * kBandBlock, i1 = std::min(nb, i0 + kBandBlock);
       const int j0 = bj * kBandBlock, j1 = std::min(nb, j0 + kBandBlock);
       for (int i = i0; i < i1; ++i)
-        for (int j = std::max(i, j0); j < j1; ++j) p->pairs.push_back(make_int2(i, j));
+        for (int j = std::max(i, j0); j < j1; ++j) pairs.push_back(make_int2(i, j));
     }
   }
+}
+
+void build_schedule(fock_plan* p, int nb) { schedule_pairs(nb, p->pairs); }
+
+// Chains [c0, c1) of shard `shard` of `nshards` over nch chains.
+void shard_range(int nch, int shard, int nshards, int* c0, int* c1) {
+  *c0 = (int)((int64_t)nch * shard / nshards);
+  *c1 = (int)((int64_t)nch * (shard + 1) / nshards);
 }
 
 void chains_from_pairs(const std::vector<int2>& pairs, std::vector<Chain>& chains) {
@@ -429,8 +438,8 @@ fock_status apply_impl(fock_plan* p, const void* psiG, int nb, const double* occ
   DevPlan dp = p->dp;
   if (!dex) dp.dvtab64 = nullptr;  // skip the dE/domega partials nobody asked for
   const int nch = (int)p->chains.size();
-  const int c0 = (int)((int64_t)nch * shard / nshards);
-  const int c1 = (int)((int64_t)nch * (shard + 1) / nshards);
+  int c0 = 0, c1 = 0;
+  shard_range(nch, shard, nshards, &c0, &c1);
   p->stats.chain_batch = p->chain_batch;
   p->stats.chains = c1 - c0;
   p->stats.pairs = std::min(npairs, 2 * c1) - std::min(npairs, 2 * c0);
@@ -648,6 +657,10 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
       for (int t = 0; t < 2 * n; ++t) tw32[t] = (float)tw64[t];
       ok = upload(&p->d_vtab, vs.data(), sizeof(float) * nhalf) &&
            upload(&p->d_tw, tw32.data(), sizeof(float) * tw32.size());
+      if (ok && kind == FOCK_KERNEL_ERFC) {
+        std::vector<float> dvs(dv64.begin(), dv64.end());
+        ok = upload(&p->d_dvtab, dvs.data(), sizeof(float) * nhalf);
+      }
     }
   }
   if (ok) ok = upload((void**)&p->d_result, std::vector<double>(4, 0.0).data(), 4 * sizeof(double));
@@ -675,6 +688,7 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
   d.vtab = p->d_vtab;
   d.vtab64 = p->d_vtab64;
   d.dvtab64 = p->d_dvtab64;
+  d.dvtab = fp64 ? (const void*)p->d_dvtab64 : (const void*)p->d_dvtab;
   d.inv_ntot = 1.0 / (double)ntot;
   d.psi_scale = 1.0 / std::sqrt(p->vol);
   d.out_scale = std::sqrt(p->vol) / (double)ntot;
@@ -723,6 +737,31 @@ fock_status fock_gsphere(const int grid[3], const double cell[9], double ecut_ha
       return fail(nullptr, FOCK_ERR_INVALID_ARG, "miller buffer too small");
     for (size_t k = 0; k < sph.size(); ++k)
       for (int a = 0; a < 3; ++a) miller[3 * k + a] = sph[k].m[a];
+  }
+  return FOCK_OK;
+}
+
+fock_status fock_schedule(int nb, int shard, int nshards, int32_t* pairs, int64_t capacity,
+                          int64_t* npairs) {
+  g_create_error.clear();
+  if (!npairs) return fail(nullptr, FOCK_ERR_INVALID_ARG, "npairs is NULL");
+  if (nb < 1 || nb > (1 << 15)) return fail(nullptr, FOCK_ERR_INVALID_ARG, "nb out of range");
+  if (nshards < 1 || shard < 0 || shard >= nshards)
+    return fail(nullptr, FOCK_ERR_INVALID_ARG, "shard must satisfy 0 <= shard < nshards");
+  std::vector<int2> all;
+  schedule_pairs(nb, all);
+  const int np = (int)all.size();
+  const int nch = (np + 1) / 2;
+  int c0 = 0, c1 = 0;
+  shard_range(nch, shard, nshards, &c0, &c1);
+  const int p0 = std::min(np, 2 * c0), p1 = std::min(np, 2 * c1);
+  *npairs = p1 - p0;
+  if (pairs) {
+    if (capacity < p1 - p0) return fail(nullptr, FOCK_ERR_INVALID_ARG, "pairs buffer too small");
+    for (int k = p0; k < p1; ++k) {
+      pairs[2 * (k - p0)] = all[k].x;
+      pairs[2 * (k - p0) + 1] = all[k].y;
+    }
   }
   return FOCK_OK;
 }
@@ -861,6 +900,7 @@ fock_status fock_destroy(fock_plan_t plan) {
   cudaFree(plan->d_tw);
   cudaFree(plan->d_vtab);
   cudaFree(plan->d_vtab64);
+  cudaFree(plan->d_dvtab);
   cudaFree(plan->d_dvtab64);
   cudaFree(plan->d_result);
   if (plan->h_result) cudaFreeHost(plan->h_result);
