@@ -238,6 +238,72 @@ fock_status fock_pair_energies_static(fock_plan_t plan, const void* psi_G, int n
                                       const int32_t* pairs, int npairs, double* e, double* d,
                                       fock_stream_t stream);
 
+/* ---------------------------------------------------------------- batches
+ *
+ * Many independent systems (uneven grids and band counts) in one batched
+ * apply: the O(nb) transforms of every system, then the pair passes of all
+ * systems in one persistent kernel launch that takes (chain x plane/row)
+ * tasks in dependency order from a global ticket counter, then V_x psi and
+ * E_x of every system; the whole sequence is captured once into a CUDA graph
+ * and replayed by fock_batch_run.  This is the band-pair distribution of §5
+ * applied across systems as well as across bands: no data dependency between
+ * pairs except the final sums.
+ */
+typedef struct fock_batch* fock_batch_t;
+
+typedef struct {
+  int slot_chains;      /* chains of the largest grid per transform-buffer slot (default 8) */
+  int ring;             /* transform-buffer slots in the ring, >= 3 (default 3) */
+  int ctas_per_sm;      /* resident CTAs per SM of the persistent launch (0: as many as fit) */
+  int use_graph;        /* 1: capture once into a CUDA graph and replay it (default 1) */
+  int want_dex;         /* 1: also produce dE_x/domega (erfc plans) */
+  double wait_limit_s;  /* bound on each device-side dependency wait (default 10 s) */
+  int stall_segment;    /* >= 0: that segment waits for itself, which can never finish: a
+                           test hook for the bounded-wait path (FOCK_ERR_TIMEOUT); -1 normally */
+} fock_batch_options;
+
+/* Fill `opt` with the defaults above. */
+fock_status fock_batch_default_options(fock_batch_options* opt);
+
+/*
+ * fock_batch_create — set up a batched apply over nsys systems.
+ *   plans    host [nsys] distinct plans of one precision on the current device,
+ *            each on a grid of 24, 32, 48, 64, 72 or 96 points per axis.  While
+ *            the batch exists it owns the plans' workspaces: do not call other
+ *            entry points on them.
+ *   nb       host [nsys] band counts.
+ *   psi_G    host [nsys] device pointers, complex128 [nb_s][npw_s] each.
+ *   occ      host [nsys] host pointers, double [nb_s] each (copied now).
+ *   vpsi_G   host [nsys] device pointers, complex128 [nb_s][npw_s] each.
+ *   opt      NULL for the defaults.
+ * The device buffers are captured by address: fock_batch_run reads psi_G and
+ * writes vpsi_G at those addresses every time (update their contents in
+ * place between runs).
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA.
+ */
+fock_status fock_batch_create(fock_batch_t* out, int nsys, const fock_plan_t* plans, const int* nb,
+                              const void* const* psi_G, const double* const* occ,
+                              void* const* vpsi_G, const fock_batch_options* opt);
+
+/*
+ * fock_batch_run — run the batched apply on `stream` and wait for it.
+ *   ex, dex  host double [nsys] or NULL; E_x and dE_x/domega per system.
+ * Errors: CUDA, TIMEOUT (a device-side wait gave up; the outputs are invalid,
+ * the batch and the device stay usable).
+ */
+fock_status fock_batch_run(fock_batch_t batch, double* ex, double* dex, fock_stream_t stream);
+
+/* Kernel launches per run (the persistent launch counts once), tasks of the
+ * persistent launch, its grid size and the number of segments.  Host outputs. */
+fock_status fock_batch_info(fock_batch_t batch, int64_t* launches, int64_t* tasks, int* grid,
+                            int* segments);
+
+/* Description of the last failure of this batch ("" if none). */
+const char* fock_batch_last_error(fock_batch_t batch);
+
+/* Release the batch (not the plans).  NULL is accepted. */
+fock_status fock_batch_destroy(fock_batch_t batch);
+
 /* Release the plan and everything it holds.  NULL is accepted. */
 fock_status fock_destroy(fock_plan_t plan);
 

@@ -16,6 +16,12 @@ from ._lib import (  # noqa: F401
     SPENCER_ALAVI,
     FockError,
     fock_apply,
+    fock_batch_create,
+    fock_batch_default_options,
+    fock_batch_destroy,
+    fock_batch_info,
+    fock_batch_last_error,
+    fock_batch_run,
     fock_apply_shard,
     fock_destroy,
     fock_gsphere,
@@ -33,4 +39,4 @@ from ._lib import (  # noqa: F401
     fock_plan_stats,
     fock_status_string,
 )
-from .plan import FockPlan  # noqa: F401
+from .plan import FockBatch, FockPlan  # noqa: F401

@@ -54,6 +54,18 @@ class FockStats(ctypes.Structure):
     ]
 
 
+class BatchOptions(ctypes.Structure):
+    _fields_ = [
+        ("slot_chains", ctypes.c_int),
+        ("ring", ctypes.c_int),
+        ("ctas_per_sm", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+        ("want_dex", ctypes.c_int),
+        ("wait_limit_s", ctypes.c_double),
+        ("stall_segment", ctypes.c_int),
+    ]
+
+
 _SIGNATURES = {
     "fock_plan_create": [ctypes.POINTER(_vp), _c_int_p, _c_dbl_p, ctypes.c_double, ctypes.c_int,
                          _c_dbl_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint],
@@ -72,6 +84,14 @@ _SIGNATURES = {
     "fock_pair_energies": [_vp, _vp, ctypes.c_int, _c_i32_p, ctypes.c_int, _c_dbl_p, _c_dbl_p, _vp],
     "fock_pair_energies_static": [_vp, _vp, ctypes.c_int, _c_i32_p, ctypes.c_int, _c_dbl_p, _c_dbl_p,
                                   _vp],
+    "fock_batch_default_options": [ctypes.POINTER(BatchOptions)],
+    "fock_batch_create": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), _c_int_p,
+                          ctypes.POINTER(_vp), ctypes.POINTER(_c_dbl_p), ctypes.POINTER(_vp),
+                          ctypes.POINTER(BatchOptions)],
+    "fock_batch_run": [_vp, _c_dbl_p, _c_dbl_p, _vp],
+    "fock_batch_info": [_vp, _c_i64_p, _c_i64_p, _c_int_p, _c_int_p],
+    "fock_batch_last_error": [_vp],
+    "fock_batch_destroy": [_vp],
     "fock_destroy": [_vp],
     "fock_status_string": [ctypes.c_int],
     "fock_last_error": [_vp],
@@ -96,7 +116,8 @@ def load():
     for name, args in _SIGNATURES.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name in ("fock_status_string", "fock_last_error") else ctypes.c_int
+        fn.restype = (ctypes.c_char_p if name in ("fock_status_string", "fock_last_error",
+                                                   "fock_batch_last_error") else ctypes.c_int)
     _lib = lib
     return lib
 
@@ -273,6 +294,60 @@ def fock_pair_energies_static(plan, psi_G, pairs, want_d=False, stream=None):
                                             d.ctypes.data_as(_c_dbl_p) if want_d else None,
                                             _stream(stream)), plan)
     return (e, d) if want_d else e
+
+
+def _check_batch(status, batch=None):
+    if status != 0:
+        raise FockError(status, load().fock_batch_last_error(batch).decode())
+
+
+def fock_batch_default_options():
+    o = BatchOptions()
+    _check_batch(load().fock_batch_default_options(ctypes.byref(o)))
+    return {f: getattr(o, f) for f, _ in BatchOptions._fields_}
+
+
+def fock_batch_create(plans, psi_G, occ, vpsi_G, **options):
+    """Batch handle for systems (plan handles, device psi/vpsi tensors, host occupations)."""
+    n = len(plans)
+    o = BatchOptions()
+    _check_batch(load().fock_batch_default_options(ctypes.byref(o)))
+    for k, v in options.items():
+        setattr(o, k, v)
+    ph = (_vp * n)(*plans)
+    nb = (ctypes.c_int * n)(*[int(p.shape[0]) for p in psi_G])
+    pp = (_vp * n)(*[_dev_ptr(p, "psi_G").value for p in psi_G])
+    vp = (_vp * n)(*[_dev_ptr(v, "vpsi_G", tuple(p.shape)).value for v, p in zip(vpsi_G, psi_G)])
+    occ_arrays = [np.ascontiguousarray(np.asarray(x, dtype=np.float64)) for x in occ]
+    op = (_c_dbl_p * n)(*[a.ctypes.data_as(_c_dbl_p) for a in occ_arrays])
+    h = _vp()
+    _check_batch(load().fock_batch_create(ctypes.byref(h), n, ph, nb, pp, op, vp, ctypes.byref(o)))
+    return h.value
+
+
+def fock_batch_run(batch, nsys, stream=None):
+    """Run the batch; returns (E_x[nsys], dE_x/domega[nsys]) as numpy arrays."""
+    ex = np.empty(nsys)
+    dex = np.empty(nsys)
+    _check_batch(load().fock_batch_run(batch, ex.ctypes.data_as(_c_dbl_p), dex.ctypes.data_as(_c_dbl_p),
+                                       _stream(stream)), batch)
+    return ex, dex
+
+
+def fock_batch_info(batch):
+    la, ta = ctypes.c_int64(), ctypes.c_int64()
+    gr, sg = ctypes.c_int(), ctypes.c_int()
+    _check_batch(load().fock_batch_info(batch, ctypes.byref(la), ctypes.byref(ta), ctypes.byref(gr),
+                                        ctypes.byref(sg)), batch)
+    return {"launches": la.value, "tasks": ta.value, "grid": gr.value, "segments": sg.value}
+
+
+def fock_batch_last_error(batch=None):
+    return load().fock_batch_last_error(batch).decode()
+
+
+def fock_batch_destroy(batch):
+    _check_batch(load().fock_batch_destroy(batch))
 
 
 def fock_destroy(plan):

@@ -59,6 +59,10 @@ def _jobs():
                  ["-c", os.path.join(CSRC, "fock_plan.cpp")]))
     jobs.append(("fock_common.o", nv + ["-c", os.path.join(CSRC, "fock_common.cu")]))
     jobs.append(("fock_static.o", nv + ["-c", os.path.join(CSRC, "fock_static.cu")]))
+    for tag, t in (("f64", "double"), ("f32", "float")):
+        jobs.append(("fock_persist_%s.o" % tag,
+                     nv + ["-DFOCK_T=" + t, "-DFOCK_OPS_NAME=kPersist_%s" % tag,
+                           "-c", os.path.join(CSRC, "fock_persist_inst.cu")]))
     for n in grid_sizes():
         for tag, t in (("f64", "double"), ("f32", "float")):
             jobs.append(("fock_%s_%d.o" % (tag, n),

@@ -52,16 +52,17 @@ __host__ __device__ constexpr int cgcd(int a, int b) {
   return a;
 }
 
-__host__ __device__ constexpr int best_tl(int n, const int* r, int nst, int nlines) {
+__host__ __device__ constexpr int best_tl(int n, const int* r, int nst, int nlines, int maxt) {
   int g = 0;
   for (int s = 0; s < nst; ++s) g = cgcd(g, n / r[s]);
   for (int t = g; t >= 1; --t)
-    if (g % t == 0 && n / t <= kEmax && nlines * t <= kMaxThreads) return t;
+    if (g % t == 0 && n / t <= kEmax && (nlines * t + 31) / 32 * 32 <= maxt) return t;
   return 0;
 }
 
-// Fewest stages first, then the most threads per line.
-__host__ __device__ constexpr RadixPlan make_radix_plan(int n) {
+// Fewest stages first, then the most threads per line, with CTAs of at most
+// maxt threads.
+__host__ __device__ constexpr RadixPlan make_radix_plan(int n, int maxt = kMaxThreads) {
   int a = 0, b = 0, m = n;
   while (m % 2 == 0) { m /= 2; ++a; }
   while (m % 3 == 0) { m /= 3; ++b; }
@@ -79,8 +80,8 @@ __host__ __device__ constexpr RadixPlan make_radix_plan(int n) {
       for (int i = 0; i < n4; ++i) p.r[p.nst++] = 4;
       for (int i = 0; i < n2; ++i) p.r[p.nst++] = 2;
       for (int i = 0; i < b; ++i) p.r[p.nst++] = 3;
-      p.tl_plane = best_tl(n, p.r, p.nst, n);
-      p.tl_colh = best_tl(n, p.r, p.nst, 2 * (n / 2 + 1));
+      p.tl_plane = best_tl(n, p.r, p.nst, n, maxt);
+      p.tl_colh = best_tl(n, p.r, p.nst, 2 * (n / 2 + 1), maxt);
       if (p.tl_plane == 0 || p.tl_colh == 0) continue;
       const int score = p.nst * 4096 - p.tl_plane;
       if (score < best_score) {
@@ -212,26 +213,27 @@ __device__ __forceinline__ void fft_stage(cplx<T>* base, int t, bool active, con
   __syncthreads();
 }
 
-template <class T, int N, int SIGN, int TL, int ES, int S, int P>
+template <class T, int N, int SIGN, int TL, int ES, int S, int P, int MAXT>
 __device__ __forceinline__ void fft_stages(cplx<T>* base, int t, bool active, const cplx<T>* tw) {
-  constexpr RadixPlan pl = make_radix_plan(N);
+  constexpr RadixPlan pl = make_radix_plan(N, MAXT);
   if constexpr (S < pl.nst) {
     constexpr int R = pl.r[S];
     fft_stage<T, N, R, P, TL, ES, SIGN>(base, t, active, tw);
-    fft_stages<T, N, SIGN, TL, ES, S + 1, P * R>(base, t, active, tw);
+    fft_stages<T, N, SIGN, TL, ES, S + 1, P * R, MAXT>(base, t, active, tw);
   }
 }
 
 // FFT of NLINES lines of length N in shared memory: line l starts at buf + l*LS,
 // its elements are ES apart.  Every thread of the CTA must call this (it
 // synchronises); threads with tid >= NLINES*TL idle.
-template <class T, int N, int SIGN, int NLINES, int TL, int LS, int ES>
+// MAXT names the radix plan (make_radix_plan(N, MAXT)) that TL was chosen for.
+template <class T, int N, int SIGN, int NLINES, int TL, int LS, int ES, int MAXT = kMaxThreads>
 __device__ __forceinline__ void fft_lines(cplx<T>* buf, const cplx<T>* tw) {
   const int tid = threadIdx.x;
   const int line = tid % NLINES;
   const int t = tid / NLINES;
   const bool active = t < TL;
-  fft_stages<T, N, SIGN, TL, ES, 0, 1>(buf + line * LS, t, active, tw);
+  fft_stages<T, N, SIGN, TL, ES, 0, 1, MAXT>(buf + line * LS, t, active, tw);
 }
 
 }  // namespace fockx

@@ -19,6 +19,15 @@ const KernelOps* find_kernel_ops(int prec, int n) {
   return nullptr;
 }
 
+extern const PersistOps kPersist_f64;
+extern const PersistOps kPersist_f32;
+
+const PersistOps* find_persist_ops(int prec) { return prec == 0 ? &kPersist_f64 : &kPersist_f32; }
+
+bool persist_supports(int n) {
+  return n == 24 || n == 32 || n == 48 || n == 64 || n == 72 || n == 96;
+}
+
 // E_x = scale * sum over the unique pairs of f_i f_j (2 if i != j) e_ij, with
 // scale = -(Omega/2) / Ntot^2; summed by one CTA in a fixed order, so the
 // result does not depend on launch timing.

@@ -64,6 +64,46 @@ struct KernelOps {
 // Kernels for grid size n and precision (0: FP64, 1: mixed); NULL if not built.
 const KernelOps* find_kernel_ops(int prec, int n);
 
+// One system of a batch as the persistent kernel sees it.
+struct SysDesc {
+  DevPlan g;
+  const void* psi;
+  void* W;
+  const void* occT;
+  const Chain* chains;
+  double* epair;
+  double* dpair;
+};
+
+// A run of tasks of one pass kind over consecutive chains of one system.
+struct Segment {
+  int kind;    // 0: forward plane pass, 1: column pass, 2: inverse plane pass
+  int sys;     // system index
+  int chain0;  // first chain (index into the system's chain list)
+  int nch;     // chains
+  int slot;    // transform-buffer slot; chain k of the run uses slot + k * hsize elements
+  int dep;     // segment that must be complete first (-1: none)
+  int dep2;    // second such segment (-1: none)
+  int task0;   // first ticket
+  int ntasks;  // N * nch
+  int pad;
+};
+
+struct PersistOps {
+  int real_bytes;
+  size_t smem;
+  cudaError_t (*configure)();
+  cudaError_t (*occupancy)(int* ctas_per_sm);
+  cudaError_t (*launch)(int grid, const SysDesc* sys, const Segment* seg, int nseg, int ntasks,
+                        unsigned* counters, unsigned char* hring, size_t slot_bytes,
+                        unsigned long long limit_ns, cudaStream_t s);
+};
+
+// Persistent pair kernel of a precision (0: FP64, 1: mixed).
+const PersistOps* find_persist_ops(int prec);
+// Grid sizes the persistent kernel runs.
+bool persist_supports(int n);
+
 // What code outside fock_plan.cpp may read of a plan.
 struct PlanView {
   int device;

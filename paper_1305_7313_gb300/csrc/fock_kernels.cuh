@@ -54,10 +54,10 @@ __device__ inline void block_sum4(double v[4], double* red) {
 }
 
 // Compile-time geometry of the passes for grid size N.
-template <class T, int N>
+template <class T, int N, int MAXT = kMaxThreads>
 struct Geo {
   using C = cplx<T>;
-  static constexpr RadixPlan pl = make_radix_plan(N);
+  static constexpr RadixPlan pl = make_radix_plan(N, MAXT);
   static_assert(pl.nst > 0, "grid size must be 2^a 3^b and fit the FFT kernels");
   static constexpr int KH = N / 2 + 1;                    // stored half of the last axis
   static constexpr int NC = 2 * KH;                       // stored columns per row (A and B)
@@ -74,7 +74,7 @@ struct Geo {
   // two in FP32 up to N = 96, one in FP64)
   static constexpr int MIN_CTAS = (sizeof(T) == 4) ? 2 : 1;
   static constexpr size_t SMEM_PLANE = sizeof(C) * (size_t)(N * RP + N);
-  static constexpr size_t SMEM_COLH = sizeof(C) * (size_t)(N * NC + N) + (32 + 12) * 4 * sizeof(double);
+  static constexpr size_t SMEM_COLH = sizeof(C) * (size_t)(N * NC + N) + 32 * 4 * sizeof(double);
   static constexpr size_t SMEM_COLF = sizeof(C) * (size_t)(N * N + N);
 };
 
@@ -94,12 +94,11 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float h2, float l2)
   lo = e - (hi - s);
 }
 
-// CTA sum of four float partials, carried in float-float across threads and
-// warps and finished in FP64 by thread 0 (valid there).  Keeps the FP64 pipe
-// out of the FP32 kernels.
-__device__ inline void block_sum4_ff(const float v[4], double out[4], double* red) {
+// CTA sum of four float partials in float-float arithmetic across threads and
+// warps; thread 0 receives (hi, lo) per value.  Uses no FP64 instruction, so
+// the FP64 pipe stays out of the FP32 kernels.  red: 2 * 4 * 32 floats.
+__device__ inline void block_sum4_ff(const float v[4], float hi[4], float lo[4], float* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  float hi[4], lo[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     hi[k] = v[k];
@@ -113,16 +112,53 @@ __device__ inline void block_sum4_ff(const float v[4], double out[4], double* re
   }
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) red[warp * 4 + k] = (double)hi[k] + (double)lo[k];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
     for (int k = 0; k < 4; ++k) {
-      double s = out[k];
-      for (int w = 0; w < nw; ++w) s += red[w * 4 + k];
-      out[k] = s;
+      red[(warp * 4 + k) * 2] = hi[k];
+      red[(warp * 4 + k) * 2 + 1] = lo[k];
     }
   }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      hi[k] = lane < nw ? red[(lane * 4 + k) * 2] : 0.f;
+      lo[k] = lane < nw ? red[(lane * 4 + k) * 2 + 1] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi[k], o);
+        const float l2 = __shfl_down_sync(0xffffffffu, lo[k], o);
+        ff_add(hi[k], lo[k], h2, l2);
+      }
+    }
+  }
+}
+
+// The kernel terms of the smallest |m| (|m|^2 <= msmall2) of one row k2 of the
+// mixed-form column pass, in FP64: at most 3 (m1) x 2 (m3 = 0, 1 in the stored
+// half) x 2 (A, B) points, one per thread t < 12.  Adds its energy terms to the
+// pair slots itself.  Kept out of line so the FP64 instructions are not
+// predicated into every warp of the kernel.
+template <class T, int N>
+__device__ __noinline__ void small_g_terms_fp64(const DevPlan& g, cplx<T>* S, int k2, int t,
+                                                const Chain& ch, double* epair, double* dpair) {
+  constexpr int KH = N / 2 + 1, NC = 2 * KH;
+  const int m2 = freq_of(k2, N);
+  const int s = t & 1, m3 = (t >> 1) & 1, m1 = (t >> 2) - 1;
+  if (m1 * m1 + m2 * m2 + m3 * m3 > g.msmall2) return;
+  if (s == 1 && ch.pb < 0) return;
+  const int k1 = (m1 + N) % N, k3 = m3;
+  const int e = k1 * NC + s * KH + k3;
+  const int64_t vi = ((int64_t)k1 * N + k2) * KH + k3;
+  const double wgt = (k3 == 0 || 2 * k3 == N) ? 1.0 : 2.0;
+  cplx<T> z = S[e];
+  const double zx = z.x, zy = z.y, a2 = zx * zx + zy * zy;
+  const double v = g.vtab64[vi];
+  atomicAdd(&epair[s ? ch.pb : ch.pa], wgt * v * a2);
+  if (g.dvtab64) atomicAdd(&dpair[s ? ch.pb : ch.pa], wgt * g.dvtab64[vi] * a2);
+  const double vs = v * g.inv_ntot;
+  z.x = T(zx * vs);
+  z.y = T(zy * vs);
+  S[e] = z;
 }
 
 template <class T>
@@ -236,18 +272,17 @@ __global__ void k_gather(DevPlan g, const cplx<T>* __restrict__ X, int nb, int b
 
 // ------------------------------------------------------------------ pair passes
 
-template <class T, int N>
-__global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
-    k_pair_fwd(DevPlan g, const T* __restrict__ psi, const Chain* __restrict__ chains,
-               cplx<T>* __restrict__ H) {
+// One task of the forward plane pass: plane i1 of chain `ch`, whose transform
+// buffer is Hc.  Shared memory: Geo::SMEM_PLANE bytes at smem_raw.
+template <class T, int N, int MAXT>
+__device__ __forceinline__ void pair_fwd_task(const DevPlan& g, const T* __restrict__ psi,
+                                              const Chain& ch, cplx<T>* __restrict__ Hc, int i1,
+                                              unsigned char* smem_raw) {
   using C = cplx<T>;
-  using G = Geo<T, N>;
+  using G = Geo<T, N, MAXT>;
   constexpr int RP = G::RP, KH = G::KH, NC = G::NC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* P = reinterpret_cast<C*>(smem_raw);
   C* tw = P + N * RP;
-  const int i1 = blockIdx.x;
-  const Chain ch = chains[blockIdx.y];
   load_twiddles<T>(tw, g);
   const int64_t plane0 = (int64_t)i1 * N * N;
   const bool hb = ch.bi >= 0;
@@ -262,9 +297,9 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
     P[i2 * RP + i3] = cmake<T>(a, b);
   }
   __syncthreads();
-  fft_lines<T, N, -1, N, G::TLP, RP, 1>(P, tw);  // along i3
-  fft_lines<T, N, -1, N, G::TLP, 1, RP>(P, tw);  // along i2
-  C* Hp = H + (int64_t)blockIdx.y * g.hsize + (int64_t)i1 * N * NC;
+  fft_lines<T, N, -1, N, G::TLP, RP, 1, MAXT>(P, tw);  // along i3
+  fft_lines<T, N, -1, N, G::TLP, 1, RP, MAXT>(P, tw);  // along i2
+  C* Hp = Hc + (int64_t)i1 * N * NC;
   for (int e = threadIdx.x; e < N * KH; e += blockDim.x) {
     const int k2 = e / KH, k3 = e - k2 * KH;
     const int m2 = k2 == 0 ? 0 : N - k2, m3 = k3 == 0 ? 0 : N - k3;
@@ -276,26 +311,33 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
 }
 
 template <class T, int N>
-__global__ void __launch_bounds__(Geo<T, N>::THR_COLH, Geo<T, N>::MIN_CTAS)
-    k_pair_col(DevPlan g, cplx<T>* __restrict__ H, const Chain* __restrict__ chains,
-               double* __restrict__ epair, double* __restrict__ dpair) {
-  using C = cplx<T>;
-  using G = Geo<T, N>;
-  constexpr int KH = G::KH, NC = G::NC;
+__global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
+    k_pair_fwd(DevPlan g, const T* __restrict__ psi, const Chain* __restrict__ chains,
+               cplx<T>* __restrict__ H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int k2 = blockIdx.x;
+  const Chain ch = chains[blockIdx.y];
+  pair_fwd_task<T, N, kMaxThreads>(g, psi, ch, H + (int64_t)blockIdx.y * g.hsize, blockIdx.x, smem_raw);
+}
+
+// One task of the column pass: row k2 of chain `ch` (transform buffer Hc).
+// Shared memory: Geo::SMEM_COLH bytes at smem_raw.
+template <class T, int N, int MAXT>
+__device__ __forceinline__ void pair_col_task(const DevPlan& g, cplx<T>* __restrict__ Hc,
+                                              const Chain& ch, int k2, double* __restrict__ epair,
+                                              double* __restrict__ dpair, unsigned char* smem_raw) {
+  using C = cplx<T>;
+  using G = Geo<T, N, MAXT>;
+  constexpr int KH = G::KH, NC = G::NC;
   C* S = reinterpret_cast<C*>(smem_raw);
   C* tw = S + N * NC;
   double* red = reinterpret_cast<double*>(tw + N);
-  const Chain ch = chains[blockIdx.y];
-  C* Hc = H + (int64_t)blockIdx.y * g.hsize;
   load_twiddles<T>(tw, g);
   for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
     const int i1 = e / NC, c = e - i1 * NC;
-    S[e] = Hc[((int64_t)i1 * N + k2) * NC + c];
+    S[e] = __ldcg(Hc + ((int64_t)i1 * N + k2) * NC + c);
   }
   __syncthreads();
-  fft_lines<T, N, -1, NC, G::TLC, 1, NC>(S, tw);  // along i1
+  fft_lines<T, N, -1, NC, G::TLC, 1, NC, MAXT>(S, tw);  // along i1
 
   // kernel multiply and energy partials
   const bool want_d = g.dvtab64 != nullptr;
@@ -327,34 +369,8 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_COLH, Geo<T, N>::MIN_CTAS)
       S[e] = z;
     }
   } else {
-    // The kernel terms of the smallest |m| (|m|^2 <= msmall2) in FP64: at most
-    // 3 (m1) x 2 (m3 = 0, 1 in the stored half) x 2 (A, B) points of this row,
-    // one thread each.  The FP32 loop below skips exactly these points.
-    if (m2 * m2 <= g.msmall2 && threadIdx.x < 12) {
-      const int t = threadIdx.x;
-      const int s = t & 1, m3 = (t >> 1) & 1, m1 = (t >> 2) - 1;
-      if (m1 * m1 + m2 * m2 + m3 * m3 <= g.msmall2) {
-        const int k1 = (m1 + N) % N, k3 = m3;
-        const int e = k1 * NC + s * KH + k3;
-        const int64_t vi = ((int64_t)k1 * N + k2) * KH + k3;
-        const double wgt = (k3 == 0 || 2 * k3 == N) ? 1.0 : 2.0;
-        C z = S[e];
-        const double zx = z.x, zy = z.y, a2 = zx * zx + zy * zy;
-        const double v = g.vtab64[vi];
-        const double te = wgt * v * a2;
-        const double td = want_d ? wgt * g.dvtab64[vi] * a2 : 0.0;
-        if (s) {
-          acc[1] += te;
-          acc[3] += td;
-        } else {
-          acc[0] += te;
-          acc[2] += td;
-        }
-        const double vs = v * g.inv_ntot;
-        z.x = T(zx * vs);
-        z.y = T(zy * vs);
-        S[e] = z;
-      }
+    if (m2 * m2 <= g.msmall2 && threadIdx.x < 32) {  // warp 0 of the few rows with small |m2|
+      if (threadIdx.x < 12) small_g_terms_fp64<T, N>(g, S, k2, threadIdx.x, ch, epair, dpair);
     }
     const T* vt = static_cast<const T*>(g.vtab);    // v / Ntot
     const T* dvt = static_cast<const T*>(g.dvtab);  // dv/domega
@@ -391,7 +407,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_COLH, Geo<T, N>::MIN_CTAS)
     acc_f32[3] = accf[3];
   }
   __syncthreads();
-  fft_lines<T, N, +1, NC, G::TLC, 1, NC>(S, tw);  // inverse along k1
+  fft_lines<T, N, +1, NC, G::TLC, 1, NC, MAXT>(S, tw);  // inverse along k1
   for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
     const int i1 = e / NC, c = e - i1 * NC;
     Hc[((int64_t)i1 * N + k2) * NC + c] = S[e];
@@ -399,21 +415,11 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_COLH, Geo<T, N>::MIN_CTAS)
   if constexpr (sizeof(T) == 8) {
     block_sum4(acc, red);
   } else {
-    double tot[4] = {0.0, 0.0, 0.0, 0.0};
-    block_sum4_ff(acc_f32, tot, red);
-    __syncthreads();
-    if (threadIdx.x < 12) {
-      // the FP64 small-|m| terms live in threads 0..11 only
-      for (int k = 0; k < 4; ++k) red[32 * 4 + threadIdx.x * 4 + k] = acc[k];
-    }
-    __syncthreads();
+    float hi[4], lo[4];
+    block_sum4_ff(acc_f32, hi, lo, reinterpret_cast<float*>(red));
     if (threadIdx.x == 0) {
-      const double ntot = double(g.ntot);
-      for (int k = 0; k < 4; ++k) {
-        double s = (k < 2 ? ntot : 1.0) * tot[k];
-        for (int t = 0; t < 12; ++t) s += red[32 * 4 + t * 4 + k];
-        acc[k] = s;
-      }
+      const double ntot = double(g.ntot);  // the FP32 table holds v / Ntot
+      for (int k = 0; k < 4; ++k) acc[k] = ((double)hi[k] + (double)lo[k]) * (k < 2 ? ntot : 1.0);
     }
   }
   if (threadIdx.x == 0) {
@@ -427,37 +433,47 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_COLH, Geo<T, N>::MIN_CTAS)
 }
 
 template <class T, int N>
-__global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
-    k_pair_inv(DevPlan g, const T* __restrict__ psi, T* __restrict__ W, const T* __restrict__ occ,
-               const Chain* __restrict__ chains, const cplx<T>* __restrict__ H) {
-  using C = cplx<T>;
-  using G = Geo<T, N>;
-  constexpr int RP = G::RP, KH = G::KH, NC = G::NC;
+__global__ void __launch_bounds__(Geo<T, N>::THR_COLH, Geo<T, N>::MIN_CTAS)
+    k_pair_col(DevPlan g, cplx<T>* __restrict__ H, const Chain* __restrict__ chains,
+               double* __restrict__ epair, double* __restrict__ dpair) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Chain ch = chains[blockIdx.y];
+  pair_col_task<T, N, kMaxThreads>(g, H + (int64_t)blockIdx.y * g.hsize, ch, blockIdx.x, epair, dpair,
+                                   smem_raw);
+}
+
+// One task of the inverse plane pass: plane i1 of chain `ch` (transform buffer
+// Hc), accumulating into W.  Shared memory: Geo::SMEM_PLANE bytes at smem_raw.
+template <class T, int N, int MAXT>
+__device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restrict__ psi,
+                                              T* __restrict__ W, const T* __restrict__ occ,
+                                              const Chain& ch, const cplx<T>* __restrict__ Hc, int i1,
+                                              unsigned char* smem_raw) {
+  using C = cplx<T>;
+  using G = Geo<T, N, MAXT>;
+  constexpr int RP = G::RP, KH = G::KH, NC = G::NC;
   C* P = reinterpret_cast<C*>(smem_raw);
   C* tw = P + N * RP;
-  const int i1 = blockIdx.x;
-  const Chain ch = chains[blockIdx.y];
   load_twiddles<T>(tw, g);
-  const C* Hp = H + (int64_t)blockIdx.y * g.hsize + (int64_t)i1 * N * NC;
+  const C* Hp = Hc + (int64_t)i1 * N * NC;
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int k2 = e / N, k3 = e - k2 * N;
     C a, b;
     if (k3 < KH) {
-      a = Hp[k2 * NC + k3];
-      b = Hp[k2 * NC + KH + k3];
+      a = __ldcg(Hp + k2 * NC + k3);
+      b = __ldcg(Hp + k2 * NC + KH + k3);
     } else {
       const int m2 = k2 == 0 ? 0 : N - k2, m3 = N - k3;
-      a = Hp[m2 * NC + m3];
-      b = Hp[m2 * NC + KH + m3];
+      a = __ldcg(Hp + m2 * NC + m3);
+      b = __ldcg(Hp + m2 * NC + KH + m3);
       a.y = -a.y;
       b.y = -b.y;
     }
     P[k2 * RP + k3] = cmake<T>(a.x - b.y, a.y + b.x);
   }
   __syncthreads();
-  fft_lines<T, N, +1, N, G::TLP, 1, RP>(P, tw);  // along k2
-  fft_lines<T, N, +1, N, G::TLP, RP, 1>(P, tw);  // along k3
+  fft_lines<T, N, +1, N, G::TLP, 1, RP, MAXT>(P, tw);  // along k2
+  fft_lines<T, N, +1, N, G::TLP, RP, 1, MAXT>(P, tw);  // along k3
   const int64_t plane0 = (int64_t)i1 * N * N;
   const bool hb = ch.bi >= 0;
   // Up to four updates k, W[tgt_k] -= f[src_k] psi[src_k] phi:
@@ -540,6 +556,16 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
       }
     }
   }
+}
+
+template <class T, int N>
+__global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
+    k_pair_inv(DevPlan g, const T* __restrict__ psi, T* __restrict__ W, const T* __restrict__ occ,
+               const Chain* __restrict__ chains, const cplx<T>* __restrict__ H) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Chain ch = chains[blockIdx.y];
+  pair_inv_task<T, N, kMaxThreads>(g, psi, W, occ, ch, H + (int64_t)blockIdx.y * g.hsize, blockIdx.x,
+                                   smem_raw);
 }
 
 // ------------------------------------------------------------------ launchers

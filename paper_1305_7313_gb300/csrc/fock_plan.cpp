@@ -909,3 +909,336 @@ fock_status fock_destroy(fock_plan_t plan) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batches
+
+struct fock_batch {
+  int nsys = 0;
+  int device = 0;
+  int prec = 0;
+  std::vector<fock_plan*> plans;
+  std::vector<int> nb;
+  std::vector<const void*> psi;
+  std::vector<void*> vpsi;
+  fock_batch_options opt{};
+  const fockx::PersistOps* pops = nullptr;
+  fockx::SysDesc* d_sys = nullptr;
+  fockx::Segment* d_seg = nullptr;
+  unsigned* d_counters = nullptr;
+  unsigned char* d_ring = nullptr;
+  double* d_result = nullptr;
+  double* h_result = nullptr;  // pinned [2 nsys]
+  unsigned* h_err = nullptr;   // pinned
+  std::vector<fockx::Segment> segs;
+  int ntasks = 0;
+  int grid = 0;
+  size_t slot_bytes = 0;
+  int64_t launches = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::string err;
+};
+
+namespace {
+
+fock_status bfail(fock_batch* b, fock_status s, const std::string& msg) {
+  if (b) b->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+fock_status bcuda(fock_batch* b, cudaError_t e, const char* what) {
+  cudaGetLastError();
+  const fock_status s = (e == cudaErrorMemoryAllocation) ? FOCK_ERR_OOM : FOCK_ERR_CUDA;
+  return bfail(b, s, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define FOCK_BCUDA(b, call)                              \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return bcuda(b, e_, #call);   \
+  } while (0)
+
+void batch_free(fock_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  cudaFree(b->d_sys);
+  cudaFree(b->d_seg);
+  cudaFree(b->d_counters);
+  cudaFree(b->d_ring);
+  cudaFree(b->d_result);
+  if (b->h_result) cudaFreeHost(b->h_result);
+  if (b->h_err) cudaFreeHost(b->h_err);
+}
+
+// Queue the whole batched apply on stream s (also used under graph capture).
+fock_status batch_enqueue(fock_batch* b, cudaStream_t s) {
+  const int nseg = (int)b->segs.size();
+  b->launches = 0;
+  FOCK_BCUDA(b, cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned) * (2 + nseg), s));
+  for (int k = 0; k < b->nsys; ++k) {
+    fock_plan* p = b->plans[k];
+    const int nb = b->nb[k];
+    const int npairs = nb * (nb + 1) / 2;
+    const size_t rb = (size_t)p->ops->real_bytes;
+    FOCK_BCUDA(b, cudaMemsetAsync(p->ws.w, 0, (size_t)nb * (size_t)p->dp.ntot * rb, s));
+    FOCK_BCUDA(b, cudaMemsetAsync(p->ws.epair, 0, sizeof(double) * npairs, s));
+    FOCK_BCUDA(b, cudaMemsetAsync(p->ws.dpair, 0, sizeof(double) * npairs, s));
+    const int nbat = bands_per_grid_batch(p);
+    for (int b0 = 0; b0 < nb; b0 += nbat) {
+      FOCK_BCUDA(b, p->ops->to_real(p->dp, static_cast<const double2*>(b->psi[k]), nb, b0,
+                                    std::min(nbat, nb - b0), p->ws.h, p->ws.psi, s));
+      b->launches += 3;
+    }
+  }
+  const unsigned long long limit_ns = (unsigned long long)(b->opt.wait_limit_s * 1e9);
+  FOCK_BCUDA(b, b->pops->launch(b->grid, b->d_sys, b->d_seg, nseg, b->ntasks, b->d_counters,
+                                b->d_ring, b->slot_bytes, limit_ns, s));
+  b->launches += 1;
+  for (int k = 0; k < b->nsys; ++k) {
+    fock_plan* p = b->plans[k];
+    const int nb = b->nb[k];
+    const int npairs = nb * (nb + 1) / 2;
+    const int nbat = bands_per_grid_batch(p);
+    for (int b0 = 0; b0 < nb; b0 += nbat) {
+      FOCK_BCUDA(b, p->ops->to_sphere(p->dp, p->ws.w, nb, b0, std::min(nbat, nb - b0), p->ws.h,
+                                      static_cast<double2*>(b->vpsi[k]), s));
+      b->launches += 3;
+    }
+    const double scale = -0.5 * p->vol / ((double)p->dp.ntot * (double)p->dp.ntot);
+    FOCK_BCUDA(b, fockx::launch_energy_reduce(p->ws.pairs, npairs, p->ws.occ, p->ws.epair,
+                                              b->opt.want_dex && p->dp.dvtab64 ? p->ws.dpair : nullptr,
+                                              scale, b->d_result + 2 * k, s));
+    b->launches += 1;
+  }
+  FOCK_BCUDA(b, cudaMemcpyAsync(b->h_result, b->d_result, sizeof(double) * 2 * b->nsys,
+                                cudaMemcpyDeviceToHost, s));
+  FOCK_BCUDA(b, cudaMemcpyAsync(b->h_err, b->d_counters + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  return FOCK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fock_status fock_batch_default_options(fock_batch_options* opt) {
+  if (!opt) return bfail(nullptr, FOCK_ERR_INVALID_ARG, "opt is NULL");
+  opt->slot_chains = 8;
+  opt->ring = 3;
+  opt->ctas_per_sm = 0;
+  opt->use_graph = 1;
+  opt->want_dex = 0;
+  opt->wait_limit_s = 10.0;
+  opt->stall_segment = -1;
+  return FOCK_OK;
+}
+
+fock_status fock_batch_create(fock_batch_t* out, int nsys, const fock_plan_t* plans, const int* nb,
+                              const void* const* psi_G, const double* const* occ,
+                              void* const* vpsi_G, const fock_batch_options* opt) {
+  g_create_error.clear();
+  if (!out) return bfail(nullptr, FOCK_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nsys < 1 || !plans || !nb || !psi_G || !occ || !vpsi_G)
+    return bfail(nullptr, FOCK_ERR_INVALID_ARG, "empty batch or NULL array");
+  fock_batch_options o;
+  fock_batch_default_options(&o);
+  if (opt) o = *opt;
+  if (o.slot_chains < 1 || o.ring < 3 || o.ctas_per_sm < 0 || !(o.wait_limit_s > 0.0))
+    return bfail(nullptr, FOCK_ERR_INVALID_ARG, "bad batch options");
+  int dev = -1;
+  cudaError_t ge = cudaGetDevice(&dev);
+  if (ge != cudaSuccess) return bcuda(nullptr, ge, "cudaGetDevice");
+  for (int k = 0; k < nsys; ++k) {
+    if (!plans[k] || !psi_G[k] || !vpsi_G[k] || !occ[k] || nb[k] < 1 || nb[k] > (1 << 15))
+      return bfail(nullptr, FOCK_ERR_INVALID_ARG, "system " + std::to_string(k) + ": bad argument");
+    for (int m = 0; m < k; ++m)
+      if (plans[m] == plans[k]) return bfail(nullptr, FOCK_ERR_INVALID_ARG, "a plan appears twice");
+    if (plans[k]->device != dev) return bfail(nullptr, FOCK_ERR_INVALID_ARG, "plans on another device");
+    if (plans[k]->prec != plans[0]->prec)
+      return bfail(nullptr, FOCK_ERR_INVALID_ARG, "plans of different precision");
+    if (!fockx::persist_supports(plans[k]->n))
+      return bfail(nullptr, FOCK_ERR_UNSUPPORTED_SIZE, "batched grids must be 24, 32, 48, 64, 72 or 96");
+  }
+  fock_batch* b = new (std::nothrow) fock_batch();
+  if (!b) return bfail(nullptr, FOCK_ERR_OOM, "host allocation failed");
+  b->nsys = nsys;
+  b->device = dev;
+  b->prec = plans[0]->prec == FOCK_PREC_FP64 ? 0 : 1;
+  b->opt = o;
+  b->plans.assign(plans, plans + nsys);
+  b->nb.assign(nb, nb + nsys);
+  b->psi.assign(psi_G, psi_G + nsys);
+  b->vpsi.assign(vpsi_G, vpsi_G + nsys);
+  auto fail_create = [&](fock_status st) {
+    g_create_error = b->err;
+    batch_free(b);
+    delete b;
+    return st;
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail_create(bcuda(b, e, "cudaStreamCreate"));
+  b->pops = fockx::find_persist_ops(b->prec);
+  if ((e = b->pops->configure()) != cudaSuccess) return fail_create(bcuda(b, e, "configuring the persistent kernel"));
+
+  // per-system workspaces, schedules and occupations
+  int nmax = 0;
+  for (int k = 0; k < nsys; ++k) {
+    fock_plan* p = b->plans[k];
+    const int npairs = nb[k] * (nb[k] + 1) / 2;
+    fock_status st = ensure_workspace(p, nb[k], npairs);
+    if (st != FOCK_OK) return fail_create(bfail(b, st, p->err));
+    build_schedule(p, nb[k]);
+    chains_from_pairs(p->pairs, p->chains);
+    if ((e = cudaMemcpyAsync(p->ws.pairs, p->pairs.data(), sizeof(int2) * npairs, cudaMemcpyHostToDevice,
+                             b->cap_stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(p->ws.chains, p->chains.data(), sizeof(Chain) * p->chains.size(),
+                             cudaMemcpyHostToDevice, b->cap_stream)) != cudaSuccess)
+      return fail_create(bcuda(b, e, "uploading a schedule"));
+    p->sched_nb = nb[k];
+    st = upload_occ(p, occ[k], nb[k], b->cap_stream);
+    if (st != FOCK_OK) return fail_create(bfail(b, st, p->err));
+    if ((e = cudaStreamSynchronize(b->cap_stream)) != cudaSuccess) return fail_create(bcuda(b, e, "sync"));
+    nmax = std::max(nmax, p->n);
+  }
+
+  // runs of chains, one transform-buffer slot each, and the segment list
+  const size_t csz = 2 * (size_t)b->plans[0]->ops->real_bytes;
+  const size_t hmax = (size_t)nmax * nmax * 2 * (nmax / 2 + 1);
+  b->slot_bytes = (size_t)o.slot_chains * hmax * csz;
+  struct Run {
+    int sys, chain0, nch;
+  };
+  std::vector<Run> runs;
+  for (int k = 0; k < nsys; ++k) {
+    fock_plan* p = b->plans[k];
+    const int nch = (int)p->chains.size();
+    const int per = (int)std::max<size_t>(1, b->slot_bytes / ((size_t)p->dp.hsize * csz));
+    for (int c0 = 0; c0 < nch; c0 += per) runs.push_back(Run{k, c0, std::min(per, nch - c0)});
+  }
+  const int R = (int)runs.size(), D = o.ring;
+  std::vector<int> ifwd(R, -1), icol(R, -1), iinv(R, -1);
+  auto emit = [&](int kind, int t, int dep, int dep2) {
+    fockx::Segment sg{};
+    sg.kind = kind;
+    sg.sys = runs[t].sys;
+    sg.chain0 = runs[t].chain0;
+    sg.nch = runs[t].nch;
+    sg.slot = t % D;
+    sg.dep = dep;
+    sg.dep2 = dep2;
+    sg.ntasks = b->plans[sg.sys]->n * sg.nch;
+    b->segs.push_back(sg);
+    return (int)b->segs.size() - 1;
+  };
+  for (int t = 0; t < R + 2; ++t) {
+    if (t < R) ifwd[t] = emit(0, t, -1, t >= D ? iinv[t - D] : -1);
+    if (t - 1 >= 0 && t - 1 < R) icol[t - 1] = emit(1, t - 1, ifwd[t - 1], -1);
+    if (t - 2 >= 0 && t - 2 < R) iinv[t - 2] = emit(2, t - 2, icol[t - 2], -1);
+  }
+  int acc = 0;
+  for (auto& sg : b->segs) {
+    sg.task0 = acc;
+    acc += sg.ntasks;
+  }
+  b->ntasks = acc;
+  const int nseg = (int)b->segs.size();
+  if (o.stall_segment >= 0 && o.stall_segment < nseg) b->segs[o.stall_segment].dep = o.stall_segment;
+
+  std::vector<fockx::SysDesc> sd(nsys);
+  for (int k = 0; k < nsys; ++k) {
+    fock_plan* p = b->plans[k];
+    sd[k].g = p->dp;
+    if (!o.want_dex) sd[k].g.dvtab64 = nullptr;
+    sd[k].psi = p->ws.psi;
+    sd[k].W = p->ws.w;
+    sd[k].occT = p->ws.occT;
+    sd[k].chains = p->ws.chains;
+    sd[k].epair = p->ws.epair;
+    sd[k].dpair = p->ws.dpair;
+  }
+  if ((e = cudaMalloc((void**)&b->d_sys, sizeof(fockx::SysDesc) * nsys)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&b->d_seg, sizeof(fockx::Segment) * nseg)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&b->d_counters, sizeof(unsigned) * (2 + nseg))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&b->d_ring, b->slot_bytes * D)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&b->d_result, sizeof(double) * 2 * nsys)) != cudaSuccess ||
+      (e = cudaMallocHost((void**)&b->h_result, sizeof(double) * 2 * nsys)) != cudaSuccess ||
+      (e = cudaMallocHost((void**)&b->h_err, sizeof(unsigned))) != cudaSuccess)
+    return fail_create(bcuda(b, e, "allocating the batch"));
+  if ((e = cudaMemcpy(b->d_sys, sd.data(), sizeof(fockx::SysDesc) * nsys, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_seg, b->segs.data(), sizeof(fockx::Segment) * nseg, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return fail_create(bcuda(b, e, "uploading the batch"));
+
+  int per_sm = 0, nsm = 0;
+  if ((e = b->pops->occupancy(&per_sm)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return fail_create(bcuda(b, e, "occupancy query"));
+  if (per_sm < 1) return fail_create(bfail(b, FOCK_ERR_UNSUPPORTED_SIZE, "the persistent kernel does not fit an SM"));
+  if (o.ctas_per_sm > 0) per_sm = std::min(per_sm, o.ctas_per_sm);
+  // every CTA of the grid must be resident at once: the waits rely on it
+  b->grid = std::min(b->ntasks, per_sm * nsm);
+
+  if (o.use_graph) {
+    if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return fail_create(bcuda(b, e, "cudaStreamBeginCapture"));
+    fock_status st = batch_enqueue(b, b->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (st != FOCK_OK) {
+      if (g) cudaGraphDestroy(g);
+      return fail_create(st);
+    }
+    if (e != cudaSuccess) return fail_create(bcuda(b, e, "cudaStreamEndCapture"));
+    b->graph = g;
+    if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess)
+      return fail_create(bcuda(b, e, "cudaGraphInstantiate"));
+  }
+  *out = b;
+  return FOCK_OK;
+}
+
+fock_status fock_batch_run(fock_batch_t b, double* ex, double* dex, fock_stream_t stream) {
+  if (!b) return bfail(nullptr, FOCK_ERR_INVALID_ARG, "batch is NULL");
+  int dev = -1;
+  FOCK_BCUDA(b, cudaGetDevice(&dev));
+  if (dev != b->device) return bfail(b, FOCK_ERR_INVALID_ARG, "the batch belongs to another device");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (b->exec) {
+    FOCK_BCUDA(b, cudaGraphLaunch(b->exec, s));
+  } else {
+    fock_status st = batch_enqueue(b, s);
+    if (st != FOCK_OK) return st;
+  }
+  FOCK_BCUDA(b, cudaStreamSynchronize(s));
+  if (*b->h_err != 0u) {
+    return bfail(b, FOCK_ERR_TIMEOUT,
+                 "a dependency wait of segment " + std::to_string(*b->h_err - 1) + " gave up");
+  }
+  for (int k = 0; k < b->nsys; ++k) {
+    if (ex) ex[k] = b->h_result[2 * k];
+    if (dex) dex[k] = b->h_result[2 * k + 1];
+  }
+  return FOCK_OK;
+}
+
+fock_status fock_batch_info(fock_batch_t b, int64_t* launches, int64_t* tasks, int* grid, int* segments) {
+  if (!b) return bfail(nullptr, FOCK_ERR_INVALID_ARG, "batch is NULL");
+  if (launches) *launches = b->launches;
+  if (tasks) *tasks = b->ntasks;
+  if (grid) *grid = b->grid;
+  if (segments) *segments = (int)b->segs.size();
+  return FOCK_OK;
+}
+
+const char* fock_batch_last_error(fock_batch_t b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+fock_status fock_batch_destroy(fock_batch_t b) {
+  if (!b) return FOCK_OK;
+  batch_free(b);
+  delete b;
+  return FOCK_OK;
+}
+
+}  // extern "C"

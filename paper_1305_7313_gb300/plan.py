@@ -108,3 +108,40 @@ class FockPlan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class FockBatch:
+    """Many systems in one batched apply (one persistent pair launch, replayed
+    as a CUDA graph).  ``plans``: distinct :class:`FockPlan` objects of one
+    precision; ``psi``: device complex128 tensors [nb_s, npw_s]; ``occ``: host
+    occupations.  Output tensors are allocated here and kept: every
+    :meth:`run` overwrites ``self.vpsi``.  Options as in ``fock_batch_options``.
+    """
+
+    def __init__(self, plans, psi, occ, **options):
+        import torch
+        self.plans = list(plans)
+        self.psi = list(psi)
+        self.occ = [np.asarray(o, dtype=np.float64).copy() for o in occ]
+        self.vpsi = [torch.empty_like(p) for p in self.psi]
+        self.handle = None
+        self.handle = _lib.fock_batch_create([p.handle for p in self.plans], self.psi, self.occ, self.vpsi,
+                                             **options)
+
+    def run(self, stream=None):
+        """(E_x per system, dE_x/domega per system); V_x psi lands in self.vpsi."""
+        return _lib.fock_batch_run(self.handle, len(self.plans), stream)
+
+    def info(self):
+        return _lib.fock_batch_info(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            _lib.fock_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
