@@ -196,6 +196,81 @@ def roofline(form, plan, res, steps, peaks, peak_src):
             "ms_per_launch": ms_per_launch, "chains_per_launch": chains_per_launch}
 
 
+def tune_on_subset(plan, c, occ, nbands, reps=2):
+    """Pick chain_batch / band_block for `plan` on its first `nbands` orbitals."""
+    import torch
+    from paper_1305_7313_gb300.autotune import tune_apply
+    sub = torch.from_numpy(np.ascontiguousarray(c[:nbands])).cuda()
+    res = tune_apply(plan, sub, occ[:nbands], reps=reps, use_cache=False)
+    del sub
+    return {"chain_batch": res["chain_batch"], "band_block": res["band_block"],
+            "tuned_on_bands": nbands, "candidates": len(res["table"])}
+
+
+def run_batched(args, peaks, peak_src):
+    """16 uneven systems (grids 48/64/72/96, 32-384 bands) in one persistent launch."""
+    import torch
+    from paper_1305_7313_gb300 import FockBatch, FockPlan
+    from paper_1305_7313_gb300.autotune import tune_batch
+    from paper_1305_7313_gb300.workloads import batched_systems, cubic_cell
+    systems = batched_systems()
+    if args.nb:
+        for sy in systems:
+            sy["nb"] = min(sy["nb"], args.nb)
+    plans, psis, occs = [], [], []
+    for sy in systems:
+        p = FockPlan(sy["N"], cubic_cell(sy["L"]), sy["ecut"], sy["kernel"], sy["omega"], sy["prec"])
+        _, c, occ = make_inputs(sy, p.miller)
+        plans.append(p)
+        psis.append(torch.from_numpy(c).cuda())
+        occs.append(occ)
+    pairs = sum(sy["nb"] * (sy["nb"] + 1) // 2 for sy in systems)
+    tuned = {"options": {}, "band_block": 16}
+    if not args.no_tune:
+        tuned = tune_batch(plans, psis, occs, slot_chains=(4, 8, 16), rings=(3,), ctas_per_sm=(0,),
+                           reps=1, use_cache=False)
+    batch = FockBatch(plans, psis, occs, **tuned["options"])
+    for _ in range(args.warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    pms = []
+    with ClockSampler(gpu_id()) as clk:
+        start.record()
+        for _ in range(args.steps):
+            batch.run()
+            pms.append(batch.info()["persist_ms"])
+        end.record()
+        torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    info = batch.info()
+    # algorithmic bytes of the persistent launch: per chain the complex64 half
+    # spectrum is written (fwd), read and written (col) and read (inv)
+    nbytes = 0.0
+    for sy in systems:
+        n = sy["N"]
+        chains = (sy["nb"] * (sy["nb"] + 1) // 2 + 1) // 2
+        nbytes += chains * 4 * n * n * 2 * (n // 2 + 1) * 8.0
+    pm = statistics.median(pms)
+    achieved = nbytes / (pm * 1e-3) / 1e9
+    batch.close()
+    for p in plans:
+        p.close()
+    return {"workload": "batched16_mixed32_sa_N48-96_L13.5-27",
+            "systems": [{"N": sy["N"], "L": sy["L"], "nb": sy["nb"]} for sy in systems],
+            "value": pairs * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "pairs": pairs, "dtype": "f32", "graph": True, "persistent_launches_per_step": 1,
+            "gpu_launches_per_step": info["launches"], "persistent_grid": info["grid"],
+            "segments": info["segments"], "tasks": info["tasks"],
+            "roofline": {"bound": "hbm", "kernel": "k_pair_persistent", "achieved": achieved,
+                         "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                         "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                         "peak_src": peak_src + " (hbm copy)", "ms_per_launch": pm},
+            "tuned": {"options": tuned["options"], "band_block": tuned["band_block"]},
+            "clocks": clk.summary()}
+
+
 def cpu_baseline(w, nbands_sample=32):
     """The FP64 oracle on the first `nbands_sample` bands of the workload."""
     import oracle
@@ -253,6 +328,10 @@ def main():
     ap.add_argument("--ref-bands", type=int, default=32)
     ap.add_argument("--nb", type=int, default=None,
                     help="override the band count of the workloads (small profiling cases)")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--tune-bands", type=int, default=64,
+                    help="band count of the subset the apply's pair-block parameters are tuned on")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -279,6 +358,9 @@ def main():
     from paper_1305_7313_gb300.workloads import cubic_cell
     plan = FockPlan(n, cubic_cell(w["L"]), w["ecut"], w["kernel"], w["omega"], w["prec"])
     cell, c, occ = make_inputs(w, plan.miller)
+    tuned = None
+    if not args.no_tune:
+        tuned = tune_on_subset(plan, c, occ, min(w["nb"], max(8, args.tune_bands // 2)), reps=1)
     psi = torch.from_numpy(c).cuda()
     pairs = w["nb"] * (w["nb"] + 1) // 2
     res = time_form(plan, psi, occ, args.steps, args.warmup, rank=rank, world=world)
@@ -314,6 +396,9 @@ def main():
             wm["nb"] = args.nb
         planm = FockPlan(wm["N"], cubic_cell(wm["L"]), wm["ecut"], wm["kernel"], wm["omega"], wm["prec"])
         _, cm, occm = make_inputs(wm, planm.miller)
+        tunedm = None
+        if not args.no_tune:
+            tunedm = tune_on_subset(planm, cm, occm, min(wm["nb"], args.tune_bands))
         psim = torch.from_numpy(cm).cuda()
         resm = time_form(planm, psim, occm, args.steps, args.warmup, rank=rank, world=world)
         pm = wm["nb"] * (wm["nb"] + 1) // 2
@@ -321,9 +406,15 @@ def main():
                  "ms_per_step": resm["ms"] / args.steps, "dtype": "f32",
                  "roofline": roofline("mixed32", planm, resm, args.steps, peaks, peak_src),
                  "phase_ms_per_step": {k: v / args.steps for k, v in resm["phase_ms"].items()},
-                 "gpu_launches": resm["launches"], "clocks": resm["clocks"]}
+                 "gpu_launches": resm["launches"], "clocks": resm["clocks"], "tuned": tunedm}
         planm.close()
         del psim
+        torch.cuda.empty_cache()
+
+    batched = None
+    if not args.no_batched and world == 1:
+        batched = run_batched(args, peaks, peak_src)
+        torch.cuda.empty_cache()
 
     if rank != 0:
         return
@@ -348,7 +439,9 @@ def main():
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
         "phase_ms_per_step": {k: v / args.steps for k, v in res["phase_ms"].items()},
+        "tuned": tuned,
         "mixed32": mixed,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

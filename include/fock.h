@@ -115,15 +115,17 @@ fock_status fock_gsphere(const int grid[3], const double cell[9], double ecut_ha
 
 /*
  * fock_schedule — the unique pairs (i <= j) that fock_apply_shard(..., shard,
- * nshards, ...) evaluates for nb bands, in the library's fixed schedule (host
- * only, no GPU).  This is the band-group split of §5 (Fig. 3) as the library
+ * nshards, ...) evaluates for nb bands with a plan whose band block is
+ * band_block (0: the default of 16), in the library's fixed schedule (host
+ * only, no GPU).  The schedule visits blocks of band_block x band_block pairs
+ * (block rows outer) so that consecutive pairs share orbitals.  This is the band-group split of §5 (Fig. 3) as the library
  * draws it: the shards are disjoint and together hold every unique pair once.
  *   pairs    host int32 [capacity][2] or NULL (call with NULL to size it).
  *   npairs   host int64; receives the number of pairs of the shard.
  * Errors: INVALID_ARG.
  */
-fock_status fock_schedule(int nb, int shard, int nshards, int32_t* pairs, int64_t capacity,
-                          int64_t* npairs);
+fock_status fock_schedule(int nb, int band_block, int shard, int nshards, int32_t* pairs,
+                          int64_t capacity, int64_t* npairs);
 
 /* Number of plane waves npw in the sphere.  npw: host int64. */
 fock_status fock_plan_npw(fock_plan_t plan, int64_t* npw);
@@ -169,6 +171,11 @@ fock_status fock_plan_set_timing(fock_plan_t plan, int enable);
 /* Counters and (with timing on) per-phase device times of the last call.
  * stats: host.  Errors: INVALID_ARG. */
 fock_status fock_plan_stats(fock_plan_t plan, fock_stats* stats);
+
+/* Bands per block of the pair schedule (default 16): pairs are visited in
+ * band_block x band_block blocks so consecutive chains share orbitals and
+ * accumulators in L2.  Takes effect at the next call.  Errors: INVALID_ARG. */
+fock_status fock_plan_set_band_block(fock_plan_t plan, int band_block);
 
 /* Bytes of device memory the plan holds (tables + workspace).  bytes: host. */
 fock_status fock_plan_device_bytes(fock_plan_t plan, int64_t* bytes);
@@ -294,9 +301,11 @@ fock_status fock_batch_create(fock_batch_t* out, int nsys, const fock_plan_t* pl
 fock_status fock_batch_run(fock_batch_t batch, double* ex, double* dex, fock_stream_t stream);
 
 /* Kernel launches per run (the persistent launch counts once), tasks of the
- * persistent launch, its grid size and the number of segments.  Host outputs. */
+ * persistent launch, its grid size, the number of segments, and the device
+ * time of the persistent launch in the last run (CUDA events; -1 before the
+ * first run).  Host outputs; any may be NULL. */
 fock_status fock_batch_info(fock_batch_t batch, int64_t* launches, int64_t* tasks, int* grid,
-                            int* segments);
+                            int* segments, double* persist_ms);
 
 /* Description of the last failure of this batch ("" if none). */
 const char* fock_batch_last_error(fock_batch_t batch);

@@ -34,6 +34,7 @@ from ._lib import (  # noqa: F401
     fock_plan_gvectors,
     fock_plan_npw,
     fock_plan_reserve,
+    fock_plan_set_band_block,
     fock_plan_set_batch,
     fock_plan_set_timing,
     fock_plan_stats,

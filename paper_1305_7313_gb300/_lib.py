@@ -70,7 +70,9 @@ _SIGNATURES = {
     "fock_plan_create": [ctypes.POINTER(_vp), _c_int_p, _c_dbl_p, ctypes.c_double, ctypes.c_int,
                          _c_dbl_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint],
     "fock_gsphere": [_c_int_p, _c_dbl_p, ctypes.c_double, _c_i64_p, _c_i32_p, ctypes.c_int64],
-    "fock_schedule": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_i32_p, ctypes.c_int64, _c_i64_p],
+    "fock_schedule": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_i32_p, ctypes.c_int64,
+                      _c_i64_p],
+    "fock_plan_set_band_block": [_vp, ctypes.c_int],
     "fock_plan_npw": [_vp, _c_i64_p],
     "fock_plan_gvectors": [_vp, _c_i32_p],
     "fock_plan_reserve": [_vp, ctypes.c_int],
@@ -89,7 +91,7 @@ _SIGNATURES = {
                           ctypes.POINTER(_vp), ctypes.POINTER(_c_dbl_p), ctypes.POINTER(_vp),
                           ctypes.POINTER(BatchOptions)],
     "fock_batch_run": [_vp, _c_dbl_p, _c_dbl_p, _vp],
-    "fock_batch_info": [_vp, _c_i64_p, _c_i64_p, _c_int_p, _c_int_p],
+    "fock_batch_info": [_vp, _c_i64_p, _c_i64_p, _c_int_p, _c_int_p, _c_dbl_p],
     "fock_batch_last_error": [_vp],
     "fock_batch_destroy": [_vp],
     "fock_destroy": [_vp],
@@ -173,15 +175,19 @@ def fock_gsphere(grid, cell, ecut):
     return out
 
 
-def fock_schedule(nb, shard=0, nshards=1):
+def fock_schedule(nb, shard=0, nshards=1, band_block=0):
     """Unique pairs [npairs, 2] (int32) that shard `shard` of `nshards` evaluates (host only)."""
     lib = load()
     n = ctypes.c_int64()
-    _check(lib.fock_schedule(int(nb), int(shard), int(nshards), None, 0, ctypes.byref(n)))
+    _check(lib.fock_schedule(int(nb), int(band_block), int(shard), int(nshards), None, 0, ctypes.byref(n)))
     out = np.empty((n.value, 2), dtype=np.int32)
-    _check(lib.fock_schedule(int(nb), int(shard), int(nshards), out.ctypes.data_as(_c_i32_p), n.value,
-                             ctypes.byref(n)))
+    _check(lib.fock_schedule(int(nb), int(band_block), int(shard), int(nshards),
+                             out.ctypes.data_as(_c_i32_p), n.value, ctypes.byref(n)))
     return out
+
+
+def fock_plan_set_band_block(plan, band_block):
+    _check(load().fock_plan_set_band_block(plan, int(band_block)), plan)
 
 
 def fock_plan_create(grid, cell, ecut, kind=SPENCER_ALAVI, kparams=(), prec=PREC_FP64, flags=GAMMA_REAL):
@@ -337,9 +343,11 @@ def fock_batch_run(batch, nsys, stream=None):
 def fock_batch_info(batch):
     la, ta = ctypes.c_int64(), ctypes.c_int64()
     gr, sg = ctypes.c_int(), ctypes.c_int()
+    ms = ctypes.c_double()
     _check_batch(load().fock_batch_info(batch, ctypes.byref(la), ctypes.byref(ta), ctypes.byref(gr),
-                                        ctypes.byref(sg)), batch)
-    return {"launches": la.value, "tasks": ta.value, "grid": gr.value, "segments": sg.value}
+                                        ctypes.byref(sg), ctypes.byref(ms)), batch)
+    return {"launches": la.value, "tasks": ta.value, "grid": gr.value, "segments": sg.value,
+            "persist_ms": ms.value}
 
 
 def fock_batch_last_error(batch=None):

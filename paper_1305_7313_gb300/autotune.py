@@ -1,0 +1,142 @@
+"""Autotuner for the pair-block parameters of the apply and of the batched form.
+
+The knobs are the ones that decide how pair work maps onto the GPU:
+
+* ``chain_batch`` — band-pair chains (two pairs per complex transform) per
+  launch of the pair passes, i.e. the size of the transform buffer a launch
+  streams through L2/HBM;
+* ``band_block`` — bands per block of the pair schedule (pairs are visited in
+  band_block x band_block blocks, so consecutive chains share orbitals and
+  accumulators in L2);
+* for batches: ``slot_chains`` (chains of the largest grid per transform-buffer
+  slot of the persistent launch), ``ring`` (slots in flight) and
+  ``ctas_per_sm`` (resident CTAs per SM of the persistent launch).
+
+Each candidate is timed on the caller's own inputs with CUDA events (one
+warm-up, then the median of ``reps`` runs) and the fastest is returned.  Results
+are cached in a JSON file keyed by the workload's shape (``FOCK_TUNE_CACHE``,
+default ``~/.cache/fockx/tune.json``) so a second process skips the search.
+"""
+
+import itertools
+import json
+import os
+import statistics
+
+import numpy as np
+
+from . import _lib
+from .plan import FockBatch
+
+
+def _cache_path():
+    return os.environ.get("FOCK_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "fockx",
+                                                          "tune.json"))
+
+
+def _load_cache():
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store_cache(key, value):
+    path = _cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        data = _load_cache()
+        data[key] = value
+        tmp = path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def _gpu_name():
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def _time_ms(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b))
+    return statistics.median(out)
+
+
+def tune_apply(plan, psi, occ, chain_batches=(4, 8, 17, 32), band_blocks=(8, 16, 32), reps=2,
+               use_cache=True):
+    """Fastest (chain_batch, band_block) for ``plan.apply(psi, occ)``; sets it on the plan.
+
+    Returns ``{"chain_batch", "band_block", "ms", "table"}``.
+    """
+    key = "apply|%s|N%d|prec%d|nb%d" % (_gpu_name(), plan.grid[0], plan.precision, psi.shape[0])
+    if use_cache:
+        hit = _load_cache().get(key)
+        if hit:
+            plan.set_batch(hit["chain_batch"])
+            plan.set_band_block(hit["band_block"])
+            return dict(hit, cached=True)
+    table = []
+    for cb, bb in itertools.product(chain_batches, band_blocks):
+        plan.set_batch(cb)
+        plan.set_band_block(bb)
+        ms = _time_ms(lambda: plan.apply(psi, occ, want_ex=True), reps)
+        table.append({"chain_batch": cb, "band_block": bb, "ms": ms})
+    best = min(table, key=lambda r: r["ms"])
+    plan.set_batch(best["chain_batch"])
+    plan.set_band_block(best["band_block"])
+    res = {"chain_batch": best["chain_batch"], "band_block": best["band_block"], "ms": best["ms"],
+           "table": table}
+    if use_cache:
+        _store_cache(key, res)
+    return res
+
+
+def tune_batch(plans, psi, occ, slot_chains=(4, 8, 16), rings=(3, 4), ctas_per_sm=(0, 1),
+               band_blocks=(16,), reps=1, use_cache=True, **fixed):
+    """Fastest batch options for the systems ``plans``/``psi``/``occ``.
+
+    Returns ``{"options": {...}, "ms": ..., "table": [...]}``; build the final
+    batch with ``FockBatch(plans, psi, occ, **result["options"])``.
+    """
+    import torch
+    shape = ",".join("%dx%d" % (p.grid[0], x.shape[0]) for p, x in zip(plans, psi))
+    key = "batch|%s|prec%d|%s|%s" % (_gpu_name(), plans[0].precision, shape,
+                                     json.dumps(fixed, sort_keys=True))
+    if use_cache:
+        hit = _load_cache().get(key)
+        if hit:
+            for p in plans:
+                p.set_band_block(hit["band_block"])
+            return dict(hit, cached=True)
+    table = []
+    for bb, sc, ring, cps in itertools.product(band_blocks, slot_chains, rings, ctas_per_sm):
+        for p in plans:
+            p.set_band_block(bb)
+        opts = dict(fixed, slot_chains=sc, ring=ring, ctas_per_sm=cps)
+        b = FockBatch(plans, psi, occ, **opts)
+        ms = _time_ms(b.run, reps)
+        table.append({"band_block": bb, "options": opts, "ms": ms, "grid": b.info()["grid"]})
+        b.close()
+        torch.cuda.synchronize()
+    best = min(table, key=lambda r: r["ms"])
+    for p in plans:
+        p.set_band_block(best["band_block"])
+    res = {"options": best["options"], "band_block": best["band_block"], "ms": best["ms"], "table": table}
+    if use_cache:
+        _store_cache(key, res)
+    return res

@@ -25,7 +25,7 @@ namespace {
 
 constexpr double kTwoPi = 2.0 * 3.14159265358979323846;
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kBandBlock = 16;                  // bands per block of the pair schedule
+constexpr int kBandBlock = 16;                  // default bands per block of the pair schedule
 constexpr size_t kChainBufferBytes = 120u << 20;  // default size of the pair-transform buffer
 constexpr int kMsmall2 = 3;                     // |m|^2 of the kernel terms kept in FP64 (mixed)
 
@@ -72,6 +72,7 @@ struct fock_plan {
   const KernelOps* ops = nullptr;
   DevPlan dp{};
   int chain_batch = 1;
+  int band_block = kBandBlock;
   // device tables
   int* d_gidx = nullptr;
   int* d_gidxneg = nullptr;
@@ -215,21 +216,21 @@ void kernel_value(const fock_plan* p, double g2, double* v, double* dv) {
 // Unique pairs i <= j in band blocks of kBandBlock (block rows outer), i outer and j
 // inner inside a block, so consecutive pairs share psi_i and a batch of chains
 // touches a few blocks of orbitals.  Chain k holds pairs 2k and 2k+1.
-void schedule_pairs(int nb, std::vector<int2>& pairs) {
+void schedule_pairs(int nb, int bb, std::vector<int2>& pairs) {
   pairs.clear();
   pairs.reserve((size_t)nb * (nb + 1) / 2);
-  const int nblk = (nb + kBandBlock - 1) / kBandBlock;
+  const int nblk = (nb + bb - 1) / bb;
   for (int bi = 0; bi < nblk; ++bi) {
     for (int bj = bi; bj < nblk; ++bj) {
-      const int i0 = bi * kBandBlock, i1 = std::min(nb, i0 + kBandBlock);
-      const int j0 = bj * kBandBlock, j1 = std::min(nb, j0 + kBandBlock);
+      const int i0 = bi * bb, i1 = std::min(nb, i0 + bb);
+      const int j0 = bj * bb, j1 = std::min(nb, j0 + bb);
       for (int i = i0; i < i1; ++i)
         for (int j = std::max(i, j0); j < j1; ++j) pairs.push_back(make_int2(i, j));
     }
   }
 }
 
-void build_schedule(fock_plan* p, int nb) { schedule_pairs(nb, p->pairs); }
+void build_schedule(fock_plan* p, int nb) { schedule_pairs(nb, p->band_block, p->pairs); }
 
 // Chains [c0, c1) of shard `shard` of `nshards` over nch chains.
 void shard_range(int nch, int shard, int nshards, int* c0, int* c1) {
@@ -741,15 +742,17 @@ fock_status fock_gsphere(const int grid[3], const double cell[9], double ecut_ha
   return FOCK_OK;
 }
 
-fock_status fock_schedule(int nb, int shard, int nshards, int32_t* pairs, int64_t capacity,
-                          int64_t* npairs) {
+fock_status fock_schedule(int nb, int band_block, int shard, int nshards, int32_t* pairs,
+                          int64_t capacity, int64_t* npairs) {
   g_create_error.clear();
   if (!npairs) return fail(nullptr, FOCK_ERR_INVALID_ARG, "npairs is NULL");
   if (nb < 1 || nb > (1 << 15)) return fail(nullptr, FOCK_ERR_INVALID_ARG, "nb out of range");
+  if (band_block == 0) band_block = kBandBlock;
+  if (band_block < 1) return fail(nullptr, FOCK_ERR_INVALID_ARG, "band_block must be >= 1");
   if (nshards < 1 || shard < 0 || shard >= nshards)
     return fail(nullptr, FOCK_ERR_INVALID_ARG, "shard must satisfy 0 <= shard < nshards");
   std::vector<int2> all;
-  schedule_pairs(nb, all);
+  schedule_pairs(nb, band_block, all);
   const int np = (int)all.size();
   const int nch = (np + 1) / 2;
   int c0 = 0, c1 = 0;
@@ -762,6 +765,17 @@ fock_status fock_schedule(int nb, int shard, int nshards, int32_t* pairs, int64_
       pairs[2 * (k - p0)] = all[k].x;
       pairs[2 * (k - p0) + 1] = all[k].y;
     }
+  }
+  return FOCK_OK;
+}
+
+fock_status fock_plan_set_band_block(fock_plan_t plan, int band_block) {
+  if (!plan) return fail(nullptr, FOCK_ERR_INVALID_ARG, "plan is NULL");
+  if (band_block < 1 || band_block > (1 << 15))
+    return fail(plan, FOCK_ERR_INVALID_ARG, "band_block must be in [1, 32768]");
+  if (band_block != plan->band_block) {
+    plan->band_block = band_block;
+    plan->sched_nb = -1;  // rebuilt at the next call
   }
   return FOCK_OK;
 }
@@ -935,6 +949,7 @@ struct fock_batch {
   size_t slot_bytes = 0;
   int64_t launches = 0;
   cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the persistent launch
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::string err;
@@ -964,6 +979,8 @@ void batch_free(fock_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
   cudaFree(b->d_sys);
   cudaFree(b->d_seg);
   cudaFree(b->d_counters);
@@ -994,8 +1011,11 @@ fock_status batch_enqueue(fock_batch* b, cudaStream_t s) {
     }
   }
   const unsigned long long limit_ns = (unsigned long long)(b->opt.wait_limit_s * 1e9);
+  // external event nodes when captured, so the elapsed time is readable after a replay
+  FOCK_BCUDA(b, cudaEventRecordWithFlags(b->ev0, s, cudaEventRecordExternal));
   FOCK_BCUDA(b, b->pops->launch(b->grid, b->d_sys, b->d_seg, nseg, b->ntasks, b->d_counters,
                                 b->d_ring, b->slot_bytes, limit_ns, s));
+  FOCK_BCUDA(b, cudaEventRecordWithFlags(b->ev1, s, cudaEventRecordExternal));
   b->launches += 1;
   for (int k = 0; k < b->nsys; ++k) {
     fock_plan* p = b->plans[k];
@@ -1080,6 +1100,8 @@ fock_status fock_batch_create(fock_batch_t* out, int nsys, const fock_plan_t* pl
   };
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return fail_create(bcuda(b, e, "cudaStreamCreate"));
+  if ((e = cudaEventCreate(&b->ev0)) != cudaSuccess || (e = cudaEventCreate(&b->ev1)) != cudaSuccess)
+    return fail_create(bcuda(b, e, "cudaEventCreate"));
   b->pops = fockx::find_persist_ops(b->prec);
   if ((e = b->pops->configure()) != cudaSuccess) return fail_create(bcuda(b, e, "configuring the persistent kernel"));
 
@@ -1223,8 +1245,14 @@ fock_status fock_batch_run(fock_batch_t b, double* ex, double* dex, fock_stream_
   return FOCK_OK;
 }
 
-fock_status fock_batch_info(fock_batch_t b, int64_t* launches, int64_t* tasks, int* grid, int* segments) {
+fock_status fock_batch_info(fock_batch_t b, int64_t* launches, int64_t* tasks, int* grid, int* segments,
+                            double* persist_ms) {
   if (!b) return bfail(nullptr, FOCK_ERR_INVALID_ARG, "batch is NULL");
+  if (persist_ms) {
+    float ms = 0.f;
+    *persist_ms = cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess ? (double)ms : -1.0;
+    cudaGetLastError();
+  }
   if (launches) *launches = b->launches;
   if (tasks) *tasks = b->ntasks;
   if (grid) *grid = b->grid;

@@ -41,6 +41,9 @@ class FockPlan:
     def set_batch(self, chain_batch):
         _lib.fock_plan_set_batch(self.handle, chain_batch)
 
+    def set_band_block(self, band_block):
+        _lib.fock_plan_set_band_block(self.handle, band_block)
+
     def set_timing(self, enable):
         _lib.fock_plan_set_timing(self.handle, enable)
 

@@ -43,6 +43,7 @@ def test_batch_matches_single_applies_and_oracle(prec, tol_v, tol_e, use_graph):
     assert info["segments"] > 3 * len(SYSTEMS)
     for _ in range(2):  # replay
         ex, dex = batch.run()
+        assert batch.info()["persist_ms"] > 0.0
         for k in range(len(SYSTEMS)):
             v = batch.vpsi[k].cpu().numpy()
             assert rel_inf(v, singles[k][0]) <= tol_v
@@ -98,3 +99,24 @@ def test_batch_rejects_bad_input():
     with pytest.raises(_lib.FockError) as err:
         FockBatch([p16], [c16], [np.ones(2)])
     assert err.value.status == 2
+
+
+def test_autotuner_picks_a_candidate_and_keeps_results(tmp_path, monkeypatch):
+    monkeypatch.setenv("FOCK_TUNE_CACHE", str(tmp_path / "tune.json"))
+    from paper_1305_7313_gb300.autotune import tune_apply, tune_batch
+    torch, plans, psis, occs, cs = make_systems(_lib.PREC_MIXED32)
+    v0, e0, _ = plans[2].apply(psis[2], occs[2])
+    v0 = v0.cpu().numpy()
+    r = tune_apply(plans[2], psis[2], occs[2], chain_batches=(2, 5), band_blocks=(4, 16), reps=1)
+    assert (r["chain_batch"], r["band_block"]) in [(2, 4), (2, 16), (5, 4), (5, 16)]
+    assert len(r["table"]) == 4
+    v1, e1, _ = plans[2].apply(psis[2], occs[2])
+    assert rel_inf(v1.cpu().numpy(), v0) <= 2e-5 and abs(e1 - e0) <= 5e-6 * abs(e0)
+    again = tune_apply(plans[2], psis[2], occs[2], chain_batches=(2, 5), band_blocks=(4, 16))
+    assert again.get("cached") and again["chain_batch"] == r["chain_batch"]
+    rb = tune_batch(plans, psis, occs, slot_chains=(1, 3), rings=(3, 4), ctas_per_sm=(0,))
+    assert len(rb["table"]) == 4
+    b = FockBatch(plans, psis, occs, **rb["options"])
+    ex, _ = b.run()
+    assert abs(ex[2] - e0) <= 5e-6 * abs(e0)
+    b.close()
