@@ -39,6 +39,7 @@ from .fock import (
     pair_potential,
     pair_energy,
     fock_apply,
+    fock_apply_to,
     overlap_matrix_vx,
     exchange_energy_from_vpsi,
 )
@@ -57,6 +58,7 @@ __all__ = [
     "pair_potential",
     "pair_energy",
     "fock_apply",
+    "fock_apply_to",
     "overlap_matrix_vx",
     "exchange_energy_from_vpsi",
 ]

@@ -147,6 +147,29 @@ def fock_apply(c, occ, miller, grid, cell, kind, omega=None, out_bands=None, rea
     return vpsi, -0.5 * vol * esum, -0.5 * vol * dsum
 
 
+def fock_apply_to(c_occ, occ, c_trial, miller, grid, cell, kind, omega=None, real=True):
+    """V_x phi_a for trial orbitals phi_a, with V_x defined by the occupied set.
+
+    (V_x phi_a)(r) = - sum_i f_i psi_i(r) ifft(v fft(psi_i* phi_a))(r): the
+    operator of the V_x equation of §4 applied to a function that is not one
+    of the occupied orbitals, as in the inner loop of the paper's nested SCF
+    (V_x fixed while the Kohn-Sham orbitals converge).  Returns [nt, npw].
+    """
+    grid = tuple(int(n) for n in grid)
+    occ = np.asarray(occ, dtype=np.float64)
+    psi = orbitals_to_real(c_occ, miller, grid, cell, real=real)
+    phi = orbitals_to_real(c_trial, miller, grid, cell, real=real)
+    vgrid, _ = kernel_grid(kind, grid, cell, omega)
+    out = np.empty((phi.shape[0], len(miller)), dtype=np.complex128)
+    for a in range(phi.shape[0]):
+        acc = np.zeros(grid, dtype=phi.dtype)
+        for i in range(psi.shape[0]):
+            pot = _ifftn(vgrid * _fftn(np.conj(psi[i]) * phi[a]))
+            acc -= occ[i] * psi[i] * (pot.real if real else pot)
+        out[a] = real_to_sphere(acc, miller, grid, cell)
+    return out
+
+
 def overlap_matrix_vx(c, vpsi):
     """M_ab = <psi_a | V_x psi_b> = sum_G c_a(G)* (V_x psi_b)(G)."""
     return np.conj(np.asarray(c)) @ np.asarray(vpsi).T

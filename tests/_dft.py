@@ -57,3 +57,25 @@ def fock_direct(c, occ, miller, grid, cell, vfun):
             ex += occ[i] * occ[j] * np.sum(v * np.abs(rhot) ** 2)
     vpsi = (w @ np.conj(e_sphere).T) * np.sqrt(vol) / ntot
     return vpsi, -0.5 * vol * ex
+
+
+def fock_direct_to(c_occ, occ, c_trial, miller, grid, cell, vfun):
+    """V_x phi_a on the sphere for trial orbitals, from direct sums."""
+    a = np.asarray(cell, dtype=np.float64).reshape(3, 3)
+    vol = abs(np.linalg.det(a))
+    pts = grid_points(grid)
+    ntot = pts.shape[0]
+    fr = grid_freqs(grid)
+    b = recip(cell)
+    g2 = np.einsum("gx,gx->g", fr @ b, fr @ b)
+    v = vfun(g2)
+    e_sphere = phase(np.asarray(miller), pts, grid)
+    fwd = np.conj(phase(fr, pts, grid))
+    psi = (c_occ @ e_sphere) / np.sqrt(vol)
+    phi = (c_trial @ e_sphere) / np.sqrt(vol)
+    w = np.zeros_like(phi)
+    for t in range(phi.shape[0]):
+        for i in range(psi.shape[0]):
+            rhot = fwd @ (np.conj(psi[i]) * phi[t]) / ntot
+            w[t] -= occ[i] * psi[i] * (np.conj(fwd).T @ (v * rhot))
+    return (w @ np.conj(e_sphere).T) * np.sqrt(vol) / ntot

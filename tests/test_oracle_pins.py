@@ -262,3 +262,35 @@ def test_omega_derivative_matches_central_differences():
     ep = oracle.fock_apply(c, occ, mill, grid, cell, ERFC, 0.3 + h)[1]
     em = oracle.fock_apply(c, occ, mill, grid, cell, ERFC, 0.3 - h)[1]
     assert abs((ep - em) / (2 * h) - dex) <= 1e-7 * abs(dex)
+
+
+# ------------------------------------------- V_x applied to trial orbitals
+
+def test_fixed_operator_on_trial_orbitals_matches_direct_dft():
+    grid = (8, 8, 8)
+    cell, mill, c = small_case(grid, 6.0, 4.0, 5, seed=21)
+    occ = np.array([2.0, 1.5, 1.0, 0.5, 0.25])
+    trial = synth.orbitals(mill, cell, 3, 77)
+    v = oracle.fock_apply_to(c, occ, trial, mill, grid, cell, ERFC, 0.6)
+    vref = _dft.fock_direct_to(c, occ, trial, mill, grid, cell,
+                               lambda g2: oracle.coulomb_kernel(ERFC, g2, 6.0 ** 3, 0.6))
+    assert np.max(np.abs(v - vref)) <= 1e-12 * np.max(np.abs(vref))
+
+
+def test_fixed_operator_on_the_occupied_set_is_the_fock_apply(cfg_small):
+    v = oracle.fock_apply_to(cfg_small["c"], cfg_small["occ"], cfg_small["c"], cfg_small["mill"],
+                             cfg_small["grid"], cfg_small["cell"], SPENCER_ALAVI)
+    assert np.max(np.abs(v - cfg_small["vpsi"])) <= 1e-13 * np.max(np.abs(v))
+
+
+def test_fixed_operator_is_linear_and_hermitian_on_trial_functions():
+    grid = (12, 12, 12)
+    cell, mill, c = small_case(grid, 7.0, 6.0, 4, seed=5)
+    occ = np.full(4, 2.0)
+    t = synth.orbitals(mill, cell, 3, 6)
+    v = oracle.fock_apply_to(c, occ, t, mill, grid, cell, SPENCER_ALAVI)
+    m = np.conj(t) @ v.T
+    assert np.max(np.abs(m - m.conj().T)) <= 1e-13 * np.max(np.abs(m))
+    comb = 0.3 * t[0] - 1.7 * t[2]
+    vc = oracle.fock_apply_to(c, occ, comb[None, :], mill, grid, cell, SPENCER_ALAVI)[0]
+    assert np.max(np.abs(vc - (0.3 * v[0] - 1.7 * v[2]))) <= 1e-13 * np.max(np.abs(vc))
