@@ -212,6 +212,30 @@ fock_status fock_apply_shard(fock_plan_t plan, const void* psi_G, int nb, const 
                              fock_stream_t stream);
 
 /*
+ * fock_set_occupied / fock_apply_fixed — the operator held fixed and applied
+ * many times: the inner loop of the nested SCF of §4 (the Kohn-Sham equations
+ * are converged at fixed V_x; the outer loop updates V_x).
+ *
+ * fock_set_occupied fixes the occupied orbitals (psi_G device complex128
+ * [nb][npw], occ host [nb]) that define V_x; they are transformed to real
+ * space once and kept in the plan.  fock_apply_fixed then returns, for nt
+ * trial orbitals phi_a (phi_G device complex128 [nt][npw]),
+ *   (V_x phi_a)(r) = - sum_i f_i psi_i(r) IFFT[v FFT(psi_i* phi_a)](r)
+ * on the sphere (vphi_G device complex128 [nt][npw], must not overlap phi_G):
+ * nb*nt pairs, two per complex transform, the occupied orbitals are not
+ * transformed again.  With phi = psi it equals fock_apply's V_x psi.
+ * Any other apply on the plan (fock_apply, fock_apply_shard,
+ * fock_pair_energies) replaces the occupied set; fock_apply_fixed then
+ * fails with INVALID_ARG until fock_set_occupied is called again.
+ * Both are stream-ordered and return without synchronising.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+fock_status fock_set_occupied(fock_plan_t plan, const void* psi_G, int nb, const double* occ,
+                              fock_stream_t stream);
+fock_status fock_apply_fixed(fock_plan_t plan, const void* phi_G, int nt, void* vphi_G,
+                             fock_stream_t stream);
+
+/*
  * fock_pair_energies — the pair terms of the §4 E_x sum,
  *   e_ij = sum_G v(G) |FFT(psi_i psi_j)(G)/Ntot|^2,   d_ij = the same with dv/domega,
  * for an explicit list of pairs.

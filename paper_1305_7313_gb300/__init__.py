@@ -16,6 +16,8 @@ from ._lib import (  # noqa: F401
     SPENCER_ALAVI,
     FockError,
     fock_apply,
+    fock_apply_fixed,
+    fock_set_occupied,
     fock_batch_create,
     fock_batch_default_options,
     fock_batch_destroy,

@@ -84,6 +84,8 @@ _SIGNATURES = {
     "fock_apply_shard": [_vp, _vp, ctypes.c_int, _c_dbl_p, ctypes.c_int, ctypes.c_int, _vp,
                          _c_dbl_p, _c_dbl_p, _vp],
     "fock_pair_energies": [_vp, _vp, ctypes.c_int, _c_i32_p, ctypes.c_int, _c_dbl_p, _c_dbl_p, _vp],
+    "fock_set_occupied": [_vp, _vp, ctypes.c_int, _c_dbl_p, _vp],
+    "fock_apply_fixed": [_vp, _vp, ctypes.c_int, _vp, _vp],
     "fock_pair_energies_static": [_vp, _vp, ctypes.c_int, _c_i32_p, ctypes.c_int, _c_dbl_p, _c_dbl_p,
                                   _vp],
     "fock_batch_default_options": [ctypes.POINTER(BatchOptions)],
@@ -272,6 +274,24 @@ def fock_apply_shard(plan, psi_G, occ, shard, nshards, vpsi_G, want_ex=True, wan
                                    ctypes.byref(ex) if want_ex else None,
                                    ctypes.byref(dex) if want_dex else None, _stream(stream)), plan)
     return (ex.value if want_ex else None), (dex.value if want_dex else None)
+
+
+def fock_set_occupied(plan, psi_G, occ, stream=None):
+    """Fix the occupied orbitals (device [nb, npw] complex128) that define V_x."""
+    nb = psi_G.shape[0]
+    a = _dev_ptr(psi_G, "psi_G")
+    o, op = _dbl_array(occ)
+    if o.shape != (nb,):
+        raise ValueError("occ must have one entry per band")
+    _check(load().fock_set_occupied(plan, a, nb, op, _stream(stream)), plan)
+
+
+def fock_apply_fixed(plan, phi_G, vphi_G, stream=None):
+    """V_x phi for trial orbitals with the V_x fixed by fock_set_occupied."""
+    nt, npw = phi_G.shape
+    a = _dev_ptr(phi_G, "phi_G")
+    b = _dev_ptr(vphi_G, "vphi_G", (nt, npw))
+    _check(load().fock_apply_fixed(plan, a, nt, b, _stream(stream)), plan)
 
 
 def fock_pair_energies(plan, psi_G, pairs, want_d=False, stream=None):

@@ -12,12 +12,16 @@ namespace fockx {
 
 // Two band pairs that share one complex transform: pair a = (ai, aj) in the
 // real part, pair b = (bi, bj) in the imaginary part (bi < 0: no pair b).
-// pa / pb index the per-pair energy slots.
+// pa / pb index the per-pair energy slots (< 0: no energy wanted).
+// flags bit 0 / bit 1: pair a / b updates only W_aj / W_bj (the operator
+// applied to a trial orbital j), not the symmetric partner W_ai / W_bi.
 struct Chain {
   int ai, aj, bi, bj;
   int pa, pb;
-  int pad0, pad1;
+  int flags, pad1;
 };
+constexpr int kChainOneSidedA = 1;
+constexpr int kChainOneSidedB = 2;
 
 // Everything a kernel needs to know about a plan (device pointers included).
 struct DevPlan {

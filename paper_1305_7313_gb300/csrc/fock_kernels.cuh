@@ -145,7 +145,7 @@ __device__ __noinline__ void small_g_terms_fp64(const DevPlan& g, cplx<T>* S, in
   const int m2 = freq_of(k2, N);
   const int s = t & 1, m3 = (t >> 1) & 1, m1 = (t >> 2) - 1;
   if (m1 * m1 + m2 * m2 + m3 * m3 > g.msmall2) return;
-  if (s == 1 && ch.pb < 0) return;
+  if (s == 1 && ch.bi < 0) return;
   const int k1 = (m1 + N) % N, k3 = m3;
   const int e = k1 * NC + s * KH + k3;
   const int64_t vi = ((int64_t)k1 * N + k2) * KH + k3;
@@ -153,8 +153,11 @@ __device__ __noinline__ void small_g_terms_fp64(const DevPlan& g, cplx<T>* S, in
   cplx<T> z = S[e];
   const double zx = z.x, zy = z.y, a2 = zx * zx + zy * zy;
   const double v = g.vtab64[vi];
-  atomicAdd(&epair[s ? ch.pb : ch.pa], wgt * v * a2);
-  if (g.dvtab64) atomicAdd(&dpair[s ? ch.pb : ch.pa], wgt * g.dvtab64[vi] * a2);
+  const int slot = s ? ch.pb : ch.pa;
+  if (slot >= 0) {
+    atomicAdd(&epair[slot], wgt * v * a2);
+    if (g.dvtab64) atomicAdd(&dpair[slot], wgt * g.dvtab64[vi] * a2);
+  }
   const double vs = v * g.inv_ntot;
   z.x = T(zx * vs);
   z.y = T(zy * vs);
@@ -423,10 +426,10 @@ __device__ __forceinline__ void pair_col_task(const DevPlan& g, cplx<T>* __restr
     }
   }
   if (threadIdx.x == 0) {
-    atomicAdd(&epair[ch.pa], acc[0]);
+    if (ch.pa >= 0) atomicAdd(&epair[ch.pa], acc[0]);
     if (ch.pb >= 0) atomicAdd(&epair[ch.pb], acc[1]);
     if (want_d) {
-      atomicAdd(&dpair[ch.pa], acc[2]);
+      if (ch.pa >= 0) atomicAdd(&dpair[ch.pa], acc[2]);
       if (ch.pb >= 0) atomicAdd(&dpair[ch.pb], acc[3]);
     }
   }
@@ -481,7 +484,8 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
   //   k = 2: W_bj -= f_bi psi_bi phi_b      k = 3: W_bi -= f_bj psi_bj phi_b (i != j)
   // Updates of the same band are summed first (into[k] = first slot with that
   // band), so each distinct band costs one atomic per point.
-  int tgt[4] = {ch.aj, ch.ai != ch.aj ? ch.ai : -1, hb ? ch.bj : -1, (hb && ch.bi != ch.bj) ? ch.bi : -1};
+  int tgt[4] = {ch.aj, (ch.ai != ch.aj && !(ch.flags & kChainOneSidedA)) ? ch.ai : -1, hb ? ch.bj : -1,
+                (hb && ch.bi != ch.bj && !(ch.flags & kChainOneSidedB)) ? ch.bi : -1};
   const int src[4] = {ch.ai, ch.aj, hb ? ch.bi : 0, hb ? ch.bj : 0};
   const T f[4] = {occ[ch.ai], occ[ch.aj], hb ? occ[ch.bi] : T(0), hb ? occ[ch.bj] : T(0)};
   int into[4] = {0, 1, 2, 3};  // which slot a contribution is added to

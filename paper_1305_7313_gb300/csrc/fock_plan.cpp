@@ -90,6 +90,11 @@ struct fock_plan {
   std::vector<int2> pairs;
   std::vector<Chain> chains;
   std::vector<double> occ_host;
+  // fixed operator (fock_set_occupied): the first fixed_nb bands of the
+  // real-space workspace hold the occupied orbitals that define V_x
+  int fixed_nb = 0;
+  int fixed_sched_nt = -1;
+  int fixed_sched_bb = 0;
   // launch accounting and optional per-launch event timing
   fock_stats stats{};
   bool timing = false;
@@ -351,12 +356,56 @@ fock_status ensure_workspace(fock_plan* p, int nb, int npairs) {
     w.chains = nullptr;
     w.npair_cap = 0;
     p->sched_nb = -1;
+    p->fixed_sched_nt = -1;
     FOCK_CUDA(p, dev_alloc(&w.epair, sizeof(double) * npairs));
     FOCK_CUDA(p, dev_alloc(&w.dpair, sizeof(double) * npairs));
     FOCK_CUDA(p, dev_alloc(&w.pairs, sizeof(int2) * npairs));
     FOCK_CUDA(p, dev_alloc(&w.chains, sizeof(Chain) * ((npairs + 1) / 2)));
     w.npair_cap = npairs;
   }
+  return FOCK_OK;
+}
+
+// Grow the real-space workspace to `nb` bands, keeping the first `keep` bands
+// of the orbitals (the fixed occupied set).
+fock_status grow_keeping(fock_plan* p, int nb, int keep) {
+  Workspace& w = p->ws;
+  if (nb <= w.nb_cap) return FOCK_OK;
+  const size_t rb = (size_t)p->ops->real_bytes;
+  const size_t bytes = (size_t)nb * (size_t)p->dp.ntot * rb;
+  void *psi = nullptr, *wacc = nullptr, *occT = nullptr;
+  double* occ = nullptr;
+  cudaError_t e;
+  if ((e = dev_alloc(&psi, bytes)) != cudaSuccess || (e = dev_alloc(&wacc, bytes)) != cudaSuccess ||
+      (e = dev_alloc(&occ, sizeof(double) * nb)) != cudaSuccess || (e = dev_alloc(&occT, rb * nb)) != cudaSuccess) {
+    cudaFree(psi);
+    cudaFree(wacc);
+    cudaFree(occ);
+    cudaFree(occT);
+    return cuda_fail(p, e, "growing the workspace");
+  }
+  if (keep > 0 && w.psi) {
+    e = cudaMemcpy(psi, w.psi, (size_t)keep * (size_t)p->dp.ntot * rb, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(occ, w.occ, sizeof(double) * keep, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(occT, w.occT, rb * keep, cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(psi);
+      cudaFree(wacc);
+      cudaFree(occ);
+      cudaFree(occT);
+      return cuda_fail(p, e, "copying the occupied orbitals");
+    }
+  }
+  cudaFree(w.psi);
+  cudaFree(w.w);
+  cudaFree(w.occ);
+  cudaFree(w.occT);
+  w.psi = psi;
+  w.w = wacc;
+  w.occ = occ;
+  w.occT = occT;
+  w.psi_bytes = bytes;
+  w.nb_cap = nb;
   return FOCK_OK;
 }
 
@@ -414,12 +463,14 @@ fock_status apply_impl(fock_plan* p, const void* psiG, int nb, const double* occ
   if (a < b + bytes && b < a + bytes) return fail(p, FOCK_ERR_INVALID_ARG, "psi_G and vpsi_G overlap");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   stats_reset(p);
+  p->fixed_nb = 0;  // the real-space workspace is about to be overwritten
   const int npairs = nb * (nb + 1) / 2;
   st = ensure_workspace(p, nb, npairs);
   if (st != FOCK_OK) return st;
   if (p->sched_nb != nb) {
     build_schedule(p, nb);
     chains_from_pairs(p->pairs, p->chains);
+    p->fixed_sched_nt = -1;
     FOCK_CUDA(p, cudaMemcpyAsync(p->ws.pairs, p->pairs.data(), sizeof(int2) * npairs,
                                  cudaMemcpyHostToDevice, s));
     FOCK_CUDA(p, cudaMemcpyAsync(p->ws.chains, p->chains.data(), sizeof(Chain) * p->chains.size(),
@@ -847,6 +898,109 @@ fock_status fock_apply_shard(fock_plan_t plan, const void* psi_G, int nb, const 
   return apply_impl(plan, psi_G, nb, occ, shard, nshards, vpsi_G, ex, dex, stream);
 }
 
+fock_status fock_set_occupied(fock_plan_t plan, const void* psi_G, int nb, const double* occ,
+                              fock_stream_t stream) {
+  fock_status st = validate_apply(plan, psi_G, nb, psi_G);
+  if (st != FOCK_OK) return st;
+  if (!occ) return fail(plan, FOCK_ERR_INVALID_ARG, "occ is NULL");
+  for (int i = 0; i < nb; ++i)
+    if (!std::isfinite(occ[i])) return fail(plan, FOCK_ERR_INVALID_ARG, "occupations must be finite");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  stats_reset(plan);
+  plan->fixed_nb = 0;
+  st = ensure_workspace(plan, nb, 1);
+  if (st != FOCK_OK) return st;
+  st = upload_occ(plan, occ, nb, s);
+  if (st != FOCK_OK) return st;
+  st = orbitals_to_real(plan, psi_G, nb, s);
+  if (st != FOCK_OK) return st;
+  plan->fixed_nb = nb;
+  plan->fixed_sched_nt = -1;
+  return FOCK_OK;
+}
+
+fock_status fock_apply_fixed(fock_plan_t plan, const void* phi_G, int nt, void* vphi_G,
+                             fock_stream_t stream) {
+  fock_plan* p = plan;
+  fock_status st = validate_apply(p, phi_G, nt, vphi_G);
+  if (st != FOCK_OK) return st;
+  if (p->fixed_nb < 1) return fail(p, FOCK_ERR_INVALID_ARG, "no occupied set: call fock_set_occupied first");
+  const size_t bytes = (size_t)nt * (size_t)p->npw * 16;
+  const char* a = static_cast<const char*>(phi_G);
+  const char* b = static_cast<const char*>(vphi_G);
+  if (a < b + bytes && b < a + bytes) return fail(p, FOCK_ERR_INVALID_ARG, "phi_G and vphi_G overlap");
+  const int nb = p->fixed_nb;
+  if ((int64_t)nb * nt > (int64_t)1 << 30) return fail(p, FOCK_ERR_INVALID_ARG, "too many pairs");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  stats_reset(p);
+  st = grow_keeping(p, nb + nt, nb);
+  if (st != FOCK_OK) return st;
+  const int npairs = nb * nt;
+  st = ensure_workspace(p, nb + nt, npairs);
+  if (st != FOCK_OK) return st;
+  if (p->fixed_sched_nt != nt || p->fixed_sched_bb != p->band_block) {
+    // pairs (occupied i, trial a) in band_block x band_block blocks, one-sided
+    std::vector<int2> pairs;
+    pairs.reserve(npairs);
+    const int bb = p->band_block;
+    for (int i0 = 0; i0 < nb; i0 += bb)
+      for (int a0 = 0; a0 < nt; a0 += bb)
+        for (int i = i0; i < std::min(nb, i0 + bb); ++i)
+          for (int t = a0; t < std::min(nt, a0 + bb); ++t) pairs.push_back(make_int2(i, nb + t));
+    chains_from_pairs(pairs, p->chains);
+    for (Chain& c : p->chains) {
+      c.flags = fockx::kChainOneSidedA | fockx::kChainOneSidedB;
+      c.pa = c.pb = -1;
+    }
+    FOCK_CUDA(p, cudaMemcpyAsync(p->ws.chains, p->chains.data(), sizeof(Chain) * p->chains.size(),
+                                 cudaMemcpyHostToDevice, s));
+    FOCK_CUDA(p, cudaStreamSynchronize(s));
+    p->sched_nb = -1;  // the symmetric schedule on the device is gone
+    p->fixed_sched_nt = nt;
+    p->fixed_sched_bb = p->band_block;
+  }
+  const size_t rb = (size_t)p->ops->real_bytes;
+  const size_t off = (size_t)nb * (size_t)p->dp.ntot * rb;
+  char* psi_trial = static_cast<char*>(p->ws.psi) + off;
+  char* w_trial = static_cast<char*>(p->ws.w) + off;
+  FOCK_CUDA(p, cudaMemsetAsync(w_trial, 0, (size_t)nt * (size_t)p->dp.ntot * rb, s));
+  const int nbat = bands_per_grid_batch(p);
+  p->stats.band_batch = nbat;
+  for (int b0 = 0; b0 < nt; b0 += nbat) {
+    PhaseScope ps(p, FOCK_PHASE_TO_REAL, 3, s);
+    FOCK_CUDA(p, p->ops->to_real(p->dp, static_cast<const double2*>(phi_G), nt, b0, std::min(nbat, nt - b0),
+                                 p->ws.h, psi_trial, s));
+  }
+  DevPlan dp = p->dp;
+  dp.dvtab64 = nullptr;
+  const int nch = (int)p->chains.size();
+  p->stats.chain_batch = p->chain_batch;
+  p->stats.chains = nch;
+  p->stats.pairs = npairs;
+  for (int c = 0; c < nch; c += p->chain_batch) {
+    const int cnt = std::min(p->chain_batch, nch - c);
+    const Chain* ch = p->ws.chains + c;
+    {
+      PhaseScope ps(p, FOCK_PHASE_PAIR_FWD, 1, s);
+      FOCK_CUDA(p, p->ops->pair_fwd(dp, p->ws.psi, ch, cnt, p->ws.h, s));
+    }
+    {
+      PhaseScope ps(p, FOCK_PHASE_PAIR_COL, 1, s);
+      FOCK_CUDA(p, p->ops->pair_col(dp, p->ws.h, ch, cnt, p->ws.epair, p->ws.dpair, s));
+    }
+    {
+      PhaseScope ps(p, FOCK_PHASE_PAIR_INV, 1, s);
+      FOCK_CUDA(p, p->ops->pair_inv(dp, p->ws.psi, p->ws.w, p->ws.occT, ch, cnt, p->ws.h, s));
+    }
+  }
+  for (int b0 = 0; b0 < nt; b0 += nbat) {
+    PhaseScope ps(p, FOCK_PHASE_TO_SPHERE, 3, s);
+    FOCK_CUDA(p, p->ops->to_sphere(p->dp, w_trial, nt, b0, std::min(nbat, nt - b0), p->ws.h,
+                                   static_cast<double2*>(vphi_G), s));
+  }
+  return collect_timing(p, s);
+}
+
 fock_status fock_pair_energies(fock_plan_t plan, const void* psi_G, int nb, const int32_t* pairs,
                                int npairs, double* e, double* d, fock_stream_t stream) {
   fock_status st = validate_apply(plan, psi_G, nb, e);
@@ -865,6 +1019,8 @@ fock_status fock_pair_energies(fock_plan_t plan, const void* psi_G, int nb, cons
   std::vector<Chain> chains;
   chains_from_pairs(list, chains);
   plan->sched_nb = -1;  // the device chain list is overwritten below
+  plan->fixed_nb = 0;   // and the real-space workspace
+  plan->fixed_sched_nt = -1;
   stats_reset(plan);
   FOCK_CUDA(plan, cudaMemcpyAsync(plan->ws.chains, chains.data(), sizeof(Chain) * chains.size(),
                                   cudaMemcpyHostToDevice, s));
@@ -1012,10 +1168,13 @@ fock_status batch_enqueue(fock_batch* b, cudaStream_t s) {
   }
   const unsigned long long limit_ns = (unsigned long long)(b->opt.wait_limit_s * 1e9);
   // external event nodes when captured, so the elapsed time is readable after a replay
-  FOCK_BCUDA(b, cudaEventRecordWithFlags(b->ev0, s, cudaEventRecordExternal));
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  FOCK_BCUDA(b, cudaStreamIsCapturing(s, &cap));
+  const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+  FOCK_BCUDA(b, cudaEventRecordWithFlags(b->ev0, s, ev_flags));
   FOCK_BCUDA(b, b->pops->launch(b->grid, b->d_sys, b->d_seg, nseg, b->ntasks, b->d_counters,
                                 b->d_ring, b->slot_bytes, limit_ns, s));
-  FOCK_BCUDA(b, cudaEventRecordWithFlags(b->ev1, s, cudaEventRecordExternal));
+  FOCK_BCUDA(b, cudaEventRecordWithFlags(b->ev1, s, ev_flags));
   b->launches += 1;
   for (int k = 0; k < b->nsys; ++k) {
     fock_plan* p = b->plans[k];

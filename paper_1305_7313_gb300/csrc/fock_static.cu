@@ -56,7 +56,7 @@ __global__ void k_chains_from_pairs(const int2* __restrict__ pairs, int npairs,
       c.bi = c.bj = -1;
       c.pb = -1;
     }
-    c.pad0 = c.pad1 = 0;
+    c.flags = c.pad1 = 0;
     chains[k] = c;
   }
 }

@@ -64,6 +64,18 @@ class FockPlan:
         ex, dex = _lib.fock_apply(self.handle, psi_G, occ, vpsi_G, want_ex, want_dex, stream)
         return vpsi_G, ex, dex
 
+    def set_occupied(self, psi_G, occ, stream=None):
+        """Fix the occupied set that defines V_x (kept in real space in the plan)."""
+        _lib.fock_set_occupied(self.handle, psi_G, occ, stream)
+
+    def apply_fixed(self, phi_G, vphi_G=None, stream=None):
+        """V_x phi for trial orbitals with the operator fixed by :meth:`set_occupied`."""
+        import torch
+        if vphi_G is None:
+            vphi_G = torch.empty_like(phi_G)
+        _lib.fock_apply_fixed(self.handle, phi_G, vphi_G, stream)
+        return vphi_G
+
     def apply_shard(self, psi_G, occ, shard, nshards, vpsi_G=None, want_ex=True, want_dex=False,
                     stream=None):
         import torch
