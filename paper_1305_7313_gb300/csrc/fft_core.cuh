@@ -43,6 +43,50 @@ struct RadixPlan {
   int tl_colh;             // sub-threads per line, half-spectrum column pass (2(N/2+1) lines)
 };
 
+// sin and cos of 2 pi m / R for integers, evaluated at compile time from their
+// Taylor series after reducing the angle to [0, pi/4] with the octant
+// symmetries (exact for the multiples of pi/4).
+__host__ __device__ constexpr double ct_taylor_sin(double x) {
+  double term = x, sum = x;
+  for (int k = 1; k < 14; ++k) {
+    term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+    sum += term;
+  }
+  return sum;
+}
+__host__ __device__ constexpr double ct_taylor_cos(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 14; ++k) {
+    term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+    sum += term;
+  }
+  return sum;
+}
+// cos(2 pi m / R) (want_sin = false) or sin(2 pi m / R) (want_sin = true)
+__host__ __device__ constexpr double ct_trig(int m, int R, bool want_sin) {
+  m = ((m % R) + R) % R;
+  // angle = 2 pi m / R = (pi / 4) * (8 m / R): octant o and remainder in [0, 1)
+  const int num = 8 * m;
+  const int o = num / R;
+  const double f = (double)(num - o * R) / (double)R;  // fraction of an octant
+  const double quarter_pi = 0.78539816339744830961566084581987572;
+  double c = 0.0, s = 0.0;
+  // angle within the octant, measured from its start (even octant) or its end (odd)
+  const double y = ((o & 1) ? (1.0 - f) : f) * quarter_pi;
+  const double cy = ct_taylor_cos(y), sy = ct_taylor_sin(y);
+  switch (o) {  // angle = o * pi/4 + f * pi/4
+    case 0: c = cy; s = sy; break;      // [0, 45)
+    case 1: c = sy; s = cy; break;      // [45, 90): 90 - y
+    case 2: c = -sy; s = cy; break;     // [90, 135): 90 + y
+    case 3: c = -cy; s = sy; break;     // [135, 180): 180 - y
+    case 4: c = -cy; s = -sy; break;    // [180, 225): 180 + y
+    case 5: c = -sy; s = -cy; break;    // [225, 270): 270 - y
+    case 6: c = sy; s = -cy; break;     // [270, 315): 270 + y
+    default: c = cy; s = -sy; break;    // [315, 360): 360 - y
+  }
+  return want_sin ? s : c;
+}
+
 __host__ __device__ constexpr int cgcd(int a, int b) {
   while (b != 0) {
     const int t = a % b;
@@ -60,36 +104,44 @@ __host__ __device__ constexpr int best_tl(int n, const int* r, int nst, int nlin
   return 0;
 }
 
+constexpr int kRadices[8] = {16, 12, 9, 8, 6, 4, 3, 2};
+
+// Depth-first search over radix multisets (in descending order) whose product
+// is n; keeps the plan with the fewest stages, then the most threads per line.
+__host__ __device__ constexpr void radix_search(int n, int rem, int first, RadixPlan& cur, RadixPlan& best,
+                                                int& best_score, int maxt) {
+  if (rem == 1) {
+    RadixPlan p = cur;
+    p.tl_plane = best_tl(n, p.r, p.nst, n, maxt);
+    p.tl_colh = best_tl(n, p.r, p.nst, 2 * (n / 2 + 1), maxt);
+    if (p.tl_plane == 0 || p.tl_colh == 0) return;
+    const int score = p.nst * 4096 - p.tl_plane;
+    if (score < best_score) {
+      best_score = score;
+      best = p;
+    }
+    return;
+  }
+  if (cur.nst >= 4) return;
+  for (int k = first; k < 8; ++k) {
+    const int r = kRadices[k];
+    if (rem % r != 0) continue;
+    cur.r[cur.nst++] = r;
+    radix_search(n, rem / r, k, cur, best, best_score, maxt);
+    --cur.nst;
+  }
+}
+
 // Fewest stages first, then the most threads per line, with CTAs of at most
-// maxt threads.
+// maxt threads.  Radices 6, 9, 12 and 16 are done in registers as two small
+// DFTs, so a plan such as 96 = 12 x 8 needs two shared-memory stages.
 __host__ __device__ constexpr RadixPlan make_radix_plan(int n, int maxt = kMaxThreads) {
-  int a = 0, b = 0, m = n;
-  while (m % 2 == 0) { m /= 2; ++a; }
-  while (m % 3 == 0) { m /= 3; ++b; }
   RadixPlan best{};
   best.nst = 0;
-  if (m != 1) return best;
+  RadixPlan cur{};
+  cur.nst = 0;
   int best_score = 1 << 30;
-  for (int n8 = 0; 3 * n8 <= a; ++n8) {
-    for (int n4 = 0; 3 * n8 + 2 * n4 <= a; ++n4) {
-      const int n2 = a - 3 * n8 - 2 * n4;
-      if (n8 + n4 + n2 + b > kMaxStages) continue;
-      RadixPlan p{};
-      p.nst = 0;
-      for (int i = 0; i < n8; ++i) p.r[p.nst++] = 8;
-      for (int i = 0; i < n4; ++i) p.r[p.nst++] = 4;
-      for (int i = 0; i < n2; ++i) p.r[p.nst++] = 2;
-      for (int i = 0; i < b; ++i) p.r[p.nst++] = 3;
-      p.tl_plane = best_tl(n, p.r, p.nst, n, maxt);
-      p.tl_colh = best_tl(n, p.r, p.nst, 2 * (n / 2 + 1), maxt);
-      if (p.tl_plane == 0 || p.tl_colh == 0) continue;
-      const int score = p.nst * 4096 - p.tl_plane;
-      if (score < best_score) {
-        best_score = score;
-        best = p;
-      }
-    }
-  }
+  radix_search(n, n, 0, cur, best, best_score, maxt);
   return best;
 }
 
@@ -166,11 +218,65 @@ template <int SIGN, class T> struct Dft {
     x[3] = cadd(e3, t3);
     x[7] = csub(e3, t3);
   }
+  // x *= exp(SIGN 2 pi i M / R) with compile-time M, R (exact for the quarter turns)
+  template <int M, int R> static __device__ __forceinline__ C twiddle(C x) {
+    constexpr int m = ((M % R) + R) % R;
+    if constexpr (m == 0) {
+      return x;
+    } else if constexpr (4 * m == R) {
+      return cmul_si<SIGN>(x);
+    } else if constexpr (2 * m == R) {
+      return cmake<T>(-x.x, -x.y);
+    } else if constexpr (4 * m == 3 * R) {
+      return cmul_si<-SIGN>(x);
+    } else {
+      constexpr T c = T(ct_trig(m, R, false));
+      constexpr T s = T(SIGN * ct_trig(m, R, true));
+      return cmake<T>(c * x.x - s * x.y, c * x.y + s * x.x);
+    }
+  }
+  // R = R1 R2 in registers: R2 DFTs of length R1 over x[R2 n1 + n2], twiddle
+  // w_R^(n2 k1), R1 DFTs of length R2; output k = k1 + R1 k2.
+  template <int R1, int R2, int N2 = 0>
+  static __device__ __forceinline__ void inner(C* x, C* a) {
+    if constexpr (N2 < R2) {
+      C t[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) t[n1] = x[R2 * n1 + N2];
+      run<R1>(t);
+      twiddle_row<R1, R2, N2, 0>(t, a);
+      inner<R1, R2, N2 + 1>(x, a);
+    }
+  }
+  template <int R1, int R2, int N2, int K1>
+  static __device__ __forceinline__ void twiddle_row(const C* t, C* a) {
+    if constexpr (K1 < R1) {
+      a[N2 * R1 + K1] = twiddle<N2 * K1, R1 * R2>(t[K1]);
+      twiddle_row<R1, R2, N2, K1 + 1>(t, a);
+    }
+  }
+  template <int R1, int R2> static __device__ __forceinline__ void composite(C* x) {
+    C a[R1 * R2];
+    inner<R1, R2>(x, a);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      C t[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) t[n2] = a[n2 * R1 + k1];
+      run<R2>(t);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) x[k1 + R1 * k2] = t[k2];
+    }
+  }
   template <int R> static __device__ __forceinline__ void run(C* x) {
     if constexpr (R == 2) r2(x);
     else if constexpr (R == 3) r3(x);
     else if constexpr (R == 4) r4(x);
-    else r8(x);
+    else if constexpr (R == 8) r8(x);
+    else if constexpr (R == 6) composite<2, 3>(x);
+    else if constexpr (R == 9) composite<3, 3>(x);
+    else if constexpr (R == 12) composite<4, 3>(x);
+    else composite<4, 4>(x);  // R == 16
   }
 };
 
