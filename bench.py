@@ -228,7 +228,7 @@ def run_batched(args, peaks, peak_src):
     tuned = {"options": {}, "band_block": 16}
     if not args.no_tune:
         tuned = tune_batch(plans, psis, occs, slot_chains=(4, 8, 16), rings=(3,), ctas_per_sm=(0,),
-                           reps=1, use_cache=False)
+                           persistent=(1, 0), reps=1, use_cache=False)
     batch = FockBatch(plans, psis, occs, **tuned["options"])
     for _ in range(args.warmup):
         batch.run()
@@ -257,17 +257,25 @@ def run_batched(args, peaks, peak_src):
     batch.close()
     for p in plans:
         p.close()
-    return {"workload": "batched16_mixed32_sa_N48-96_L13.5-27",
+    persistent = bool(tuned["options"].get("persistent", 1))
+    if not persistent:
+        # the pair passes ran as size-specialised launches: time them as a whole
+        nbytes_kernel = "pair passes (graph branches)"
+    else:
+        nbytes_kernel = "k_pair_persistent"
+    return {"workload": "batched16_mixed32_sa_N48-96_L13.5-27", "mode": "persistent" if persistent else
+            "graph branches of size-specialised launches",
             "systems": [{"N": sy["N"], "L": sy["L"], "nb": sy["nb"]} for sy in systems],
             "value": pairs * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
             "pairs": pairs, "dtype": "f32", "graph": True, "persistent_launches_per_step": 1,
             "gpu_launches_per_step": info["launches"], "persistent_grid": info["grid"],
             "segments": info["segments"], "tasks": info["tasks"],
-            "roofline": {"bound": "hbm", "kernel": "k_pair_persistent", "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": nbytes_kernel, "achieved": achieved,
                          "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                          "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
                          "peak_src": peak_src + " (hbm copy)", "ms_per_launch": pm},
-            "tuned": {"options": tuned["options"], "band_block": tuned["band_block"]},
+            "tuned": {"options": tuned["options"], "band_block": tuned["band_block"],
+                      "candidates_ms": [(r["options"], r["ms"]) for r in tuned.get("table", [])]},
             "clocks": clk.summary()}
 
 

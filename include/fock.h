@@ -291,6 +291,9 @@ typedef struct {
   double wait_limit_s;  /* bound on each device-side dependency wait (default 10 s) */
   int stall_segment;    /* >= 0: that segment waits for itself, which can never finish: a
                            test hook for the bounded-wait path (FOCK_ERR_TIMEOUT); -1 normally */
+  int persistent;       /* 1: the pair passes of all systems in one persistent launch (default);
+                           0: each system's pair passes as size-specialised launches on its own
+                           branch of the graph (branches run concurrently) */
 } fock_batch_options;
 
 /* Fill `opt` with the defaults above. */

@@ -63,6 +63,7 @@ class BatchOptions(ctypes.Structure):
         ("want_dex", ctypes.c_int),
         ("wait_limit_s", ctypes.c_double),
         ("stall_segment", ctypes.c_int),
+        ("persistent", ctypes.c_int),
     ]
 
 

@@ -8,9 +8,11 @@ The knobs are the ones that decide how pair work maps onto the GPU:
 * ``band_block`` — bands per block of the pair schedule (pairs are visited in
   band_block x band_block blocks, so consecutive chains share orbitals and
   accumulators in L2);
-* for batches: ``slot_chains`` (chains of the largest grid per transform-buffer
-  slot of the persistent launch), ``ring`` (slots in flight) and
-  ``ctas_per_sm`` (resident CTAs per SM of the persistent launch).
+* for batches: ``persistent`` (one persistent launch for all systems, or
+  size-specialised launches on one graph branch per system), ``slot_chains``
+  (chains of the largest grid per transform-buffer slot of the persistent
+  launch), ``ring`` (slots in flight) and ``ctas_per_sm`` (resident CTAs per
+  SM of the persistent launch).
 
 Each candidate is timed on the caller's own inputs with CUDA events (one
 warm-up, then the median of ``reps`` runs) and the fastest is returned.  Results
@@ -107,7 +109,7 @@ def tune_apply(plan, psi, occ, chain_batches=(4, 8, 17, 32), band_blocks=(8, 16,
 
 
 def tune_batch(plans, psi, occ, slot_chains=(4, 8, 16), rings=(3, 4), ctas_per_sm=(0, 1),
-               band_blocks=(16,), reps=1, use_cache=True, **fixed):
+               band_blocks=(16,), persistent=(1,), reps=1, use_cache=True, **fixed):
     """Fastest batch options for the systems ``plans``/``psi``/``occ``.
 
     Returns ``{"options": {...}, "ms": ..., "table": [...]}``; build the final
@@ -124,10 +126,17 @@ def tune_batch(plans, psi, occ, slot_chains=(4, 8, 16), rings=(3, 4), ctas_per_s
                 p.set_band_block(hit["band_block"])
             return dict(hit, cached=True)
     table = []
-    for bb, sc, ring, cps in itertools.product(band_blocks, slot_chains, rings, ctas_per_sm):
+    combos = []
+    for pers in persistent:
+        if pers:
+            combos += [(bb, sc, ring, cps, 1) for bb, sc, ring, cps in
+                       itertools.product(band_blocks, slot_chains, rings, ctas_per_sm)]
+        else:  # the persistent-launch knobs do not apply
+            combos += [(bb, slot_chains[0], rings[0], 0, 0) for bb in band_blocks]
+    for bb, sc, ring, cps, pers in combos:
         for p in plans:
             p.set_band_block(bb)
-        opts = dict(fixed, slot_chains=sc, ring=ring, ctas_per_sm=cps)
+        opts = dict(fixed, slot_chains=sc, ring=ring, ctas_per_sm=cps, persistent=pers)
         b = FockBatch(plans, psi, occ, **opts)
         ms = _time_ms(b.run, reps)
         table.append({"band_block": bb, "options": opts, "ms": ms, "grid": b.info()["grid"]})

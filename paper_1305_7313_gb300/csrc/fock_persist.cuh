@@ -68,7 +68,10 @@ __device__ inline bool bounded_wait(const unsigned* p, unsigned target, const un
 // it gets the register allocation of a stand-alone kernel.
 template <class T, int N, int KIND>
 __device__ __noinline__ void persist_task(const SysDesc* __restrict__ sys, int sysi, int chain, int idx,
-                                          cplx<T>* Hc, unsigned char* smem) {
+                                          cplx<T>* Hc) {
+  // the dynamic shared array by name (not through a pointer argument), so its
+  // accesses stay shared-memory accesses with 32-bit addresses
+  extern __shared__ __align__(16) unsigned char smem[];
   const SysDesc& sd = sys[sysi];
   const Chain ch = sd.chains[chain];
   if constexpr (KIND == 0) {
@@ -83,12 +86,12 @@ __device__ __noinline__ void persist_task(const SysDesc* __restrict__ sys, int s
 
 template <class T, int N>
 __device__ __forceinline__ void run_task(const SysDesc* sys, const Segment& sg, int local, cplx<T>* hslot,
-                                         int64_t hsize, unsigned char* smem) {
+                                         int64_t hsize) {
   const int c = local / N, idx = local - c * N;
   cplx<T>* Hc = hslot + (int64_t)c * hsize;
-  if (sg.kind == 0) persist_task<T, N, 0>(sys, sg.sys, sg.chain0 + c, idx, Hc, smem);
-  else if (sg.kind == 1) persist_task<T, N, 1>(sys, sg.sys, sg.chain0 + c, idx, Hc, smem);
-  else persist_task<T, N, 2>(sys, sg.sys, sg.chain0 + c, idx, Hc, smem);
+  if (sg.kind == 0) persist_task<T, N, 0>(sys, sg.sys, sg.chain0 + c, idx, Hc);
+  else if (sg.kind == 1) persist_task<T, N, 1>(sys, sg.sys, sg.chain0 + c, idx, Hc);
+  else persist_task<T, N, 2>(sys, sg.sys, sg.chain0 + c, idx, Hc);
 }
 
 // counters[0]: next ticket; counters[1]: error word (segment + 1 of the wait that
@@ -129,12 +132,12 @@ __global__ void __launch_bounds__(kPersistMaxT, PersistGeo<T>::MIN_CTAS)
     const int n = sys[sg.sys].g.n;
     const int64_t hsize = sys[sg.sys].g.hsize;
     switch (n) {
-      case 24: run_task<T, 24>(sys, sg, local, hslot, hsize, smem_raw); break;
-      case 32: run_task<T, 32>(sys, sg, local, hslot, hsize, smem_raw); break;
-      case 48: run_task<T, 48>(sys, sg, local, hslot, hsize, smem_raw); break;
-      case 64: run_task<T, 64>(sys, sg, local, hslot, hsize, smem_raw); break;
-      case 72: run_task<T, 72>(sys, sg, local, hslot, hsize, smem_raw); break;
-      case 96: run_task<T, 96>(sys, sg, local, hslot, hsize, smem_raw); break;
+      case 24: run_task<T, 24>(sys, sg, local, hslot, hsize); break;
+      case 32: run_task<T, 32>(sys, sg, local, hslot, hsize); break;
+      case 48: run_task<T, 48>(sys, sg, local, hslot, hsize); break;
+      case 64: run_task<T, 64>(sys, sg, local, hslot, hsize); break;
+      case 72: run_task<T, 72>(sys, sg, local, hslot, hsize); break;
+      case 96: run_task<T, 96>(sys, sg, local, hslot, hsize); break;
       default: break;  // the host admits only the sizes above
     }
     __syncthreads();

@@ -1105,7 +1105,9 @@ struct fock_batch {
   size_t slot_bytes = 0;
   int64_t launches = 0;
   cudaStream_t cap_stream = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the persistent launch
+  std::vector<cudaStream_t> branch;          // per-system streams (non-persistent mode)
+  std::vector<cudaEvent_t> branch_ev;        // fork / join events of the branches
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the pair passes
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::string err;
@@ -1137,6 +1139,8 @@ void batch_free(fock_batch* b) {
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
+  for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->branch_ev) cudaEventDestroy(ev);
   cudaFree(b->d_sys);
   cudaFree(b->d_seg);
   cudaFree(b->d_counters);
@@ -1172,10 +1176,34 @@ fock_status batch_enqueue(fock_batch* b, cudaStream_t s) {
   FOCK_BCUDA(b, cudaStreamIsCapturing(s, &cap));
   const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
   FOCK_BCUDA(b, cudaEventRecordWithFlags(b->ev0, s, ev_flags));
-  FOCK_BCUDA(b, b->pops->launch(b->grid, b->d_sys, b->d_seg, nseg, b->ntasks, b->d_counters,
-                                b->d_ring, b->slot_bytes, limit_ns, s));
+  if (b->opt.persistent) {
+    FOCK_BCUDA(b, b->pops->launch(b->grid, b->d_sys, b->d_seg, nseg, b->ntasks, b->d_counters,
+                                  b->d_ring, b->slot_bytes, limit_ns, s));
+    b->launches += 1;
+  } else {
+    // fork one branch per system, each running its size-specialised pair passes
+    // over its own transform buffer, and join them back into s
+    FOCK_BCUDA(b, cudaEventRecord(b->branch_ev[0], s));
+    for (int k = 0; k < b->nsys; ++k) {
+      fock_plan* p = b->plans[k];
+      cudaStream_t bs = b->branch[k];
+      FOCK_BCUDA(b, cudaStreamWaitEvent(bs, b->branch_ev[0], 0));
+      fockx::DevPlan dp = p->dp;
+      if (!b->opt.want_dex) dp.dvtab64 = nullptr;
+      const int nch = (int)p->chains.size();
+      for (int c = 0; c < nch; c += p->chain_batch) {
+        const int cnt = std::min(p->chain_batch, nch - c);
+        const Chain* ch = p->ws.chains + c;
+        FOCK_BCUDA(b, p->ops->pair_fwd(dp, p->ws.psi, ch, cnt, p->ws.h, bs));
+        FOCK_BCUDA(b, p->ops->pair_col(dp, p->ws.h, ch, cnt, p->ws.epair, p->ws.dpair, bs));
+        FOCK_BCUDA(b, p->ops->pair_inv(dp, p->ws.psi, p->ws.w, p->ws.occT, ch, cnt, p->ws.h, bs));
+        b->launches += 3;
+      }
+      FOCK_BCUDA(b, cudaEventRecord(b->branch_ev[1 + k], bs));
+      FOCK_BCUDA(b, cudaStreamWaitEvent(s, b->branch_ev[1 + k], 0));
+    }
+  }
   FOCK_BCUDA(b, cudaEventRecordWithFlags(b->ev1, s, ev_flags));
-  b->launches += 1;
   for (int k = 0; k < b->nsys; ++k) {
     fock_plan* p = b->plans[k];
     const int nb = b->nb[k];
@@ -1211,6 +1239,7 @@ fock_status fock_batch_default_options(fock_batch_options* opt) {
   opt->want_dex = 0;
   opt->wait_limit_s = 10.0;
   opt->stall_segment = -1;
+  opt->persistent = 1;
   return FOCK_OK;
 }
 
@@ -1261,6 +1290,20 @@ fock_status fock_batch_create(fock_batch_t* out, int nsys, const fock_plan_t* pl
   if (e != cudaSuccess) return fail_create(bcuda(b, e, "cudaStreamCreate"));
   if ((e = cudaEventCreate(&b->ev0)) != cudaSuccess || (e = cudaEventCreate(&b->ev1)) != cudaSuccess)
     return fail_create(bcuda(b, e, "cudaEventCreate"));
+  if (!o.persistent) {
+    for (int k = 0; k < nsys; ++k) {
+      cudaStream_t st = nullptr;
+      if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
+        return fail_create(bcuda(b, e, "cudaStreamCreate"));
+      b->branch.push_back(st);
+    }
+    for (int k = 0; k < nsys + 1; ++k) {
+      cudaEvent_t ev = nullptr;
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+        return fail_create(bcuda(b, e, "cudaEventCreate"));
+      b->branch_ev.push_back(ev);
+    }
+  }
   b->pops = fockx::find_persist_ops(b->prec);
   if ((e = b->pops->configure()) != cudaSuccess) return fail_create(bcuda(b, e, "configuring the persistent kernel"));
 

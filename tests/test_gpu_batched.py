@@ -30,15 +30,18 @@ def make_systems(prec, kind=_lib.SPENCER_ALAVI, omega=None, seed=50):
 
 @pytest.mark.parametrize("prec,tol_v,tol_e", [(_lib.PREC_FP64, 1e-10, 1e-10),
                                               (_lib.PREC_MIXED32, 2e-5, 5e-6)])
-@pytest.mark.parametrize("use_graph", [1, 0])
-def test_batch_matches_single_applies_and_oracle(prec, tol_v, tol_e, use_graph):
+@pytest.mark.parametrize("use_graph,persistent", [(1, 1), (0, 1), (1, 0)])
+def test_batch_matches_single_applies_and_oracle(prec, tol_v, tol_e, use_graph, persistent):
     torch, plans, psis, occs, cs = make_systems(prec, _lib.ERFC, 0.3)
     singles = []
     for p, psi, occ in zip(plans, psis, occs):
         v, e, d = p.apply(psi, occ, want_dex=True)
         singles.append((v.cpu().numpy(), e, d))
     # small slots force many segments, slot reuse across systems and ragged runs
-    batch = FockBatch(plans, psis, occs, slot_chains=2, ring=3, use_graph=use_graph, want_dex=1)
+    for p in plans:
+        p.set_batch(3)  # several launches per system in the non-persistent mode
+    batch = FockBatch(plans, psis, occs, slot_chains=2, ring=3, use_graph=use_graph, want_dex=1,
+                      persistent=persistent)
     info = batch.info()
     assert info["segments"] > 3 * len(SYSTEMS)
     for _ in range(2):  # replay
