@@ -31,7 +31,7 @@ translation, permutation and partition invariances, and brute-force counts of
 the G-sphere.  No function here is "parity unpinned".
 """
 
-from .lattice import reciprocal_lattice, cell_volume, gsphere, grid_miller, grid_g2
+from .lattice import reciprocal_lattice, cell_volume, gsphere, gsphere_k, grid_miller, grid_g2
 from .kernels import coulomb_kernel, coulomb_kernel_domega, spencer_alavi_rc
 from .fock import (
     orbitals_to_real,
@@ -40,6 +40,7 @@ from .fock import (
     pair_energy,
     fock_apply,
     fock_apply_to,
+    fock_apply_kpoints,
     overlap_matrix_vx,
     exchange_energy_from_vpsi,
 )
@@ -48,6 +49,7 @@ __all__ = [
     "reciprocal_lattice",
     "cell_volume",
     "gsphere",
+    "gsphere_k",
     "grid_miller",
     "grid_g2",
     "coulomb_kernel",
@@ -59,6 +61,7 @@ __all__ = [
     "pair_energy",
     "fock_apply",
     "fock_apply_to",
+    "fock_apply_kpoints",
     "overlap_matrix_vx",
     "exchange_energy_from_vpsi",
 ]

@@ -179,3 +179,49 @@ def exchange_energy_from_vpsi(c, occ, vpsi):
     """E_x = 1/2 sum_j f_j <psi_j | V_x psi_j>."""
     d = np.einsum("jg,jg->j", np.conj(np.asarray(c)), np.asarray(vpsi)).real
     return 0.5 * float(np.dot(np.asarray(occ, dtype=np.float64), d))
+
+
+def fock_apply_kpoints(c_list, occ, miller_list, kfrac, weights, grid, cell, kind, omega=None):
+    """V_x psi_nk and E_x with Brillouin-zone sampling (the first two equations of §4).
+
+    Bloch orbitals psi_nk(r) = exp(i k.r) u_nk(r), with
+    psi_nk(r) = Omega^-1/2 sum_{G in S_k} c_nk(G) exp(i (k + G).r).  With q = k - k':
+      rho(r)      = u_{mk'}*(r) u_{nk}(r)
+      phi(r)      = ifft(v(G + q) fft(rho))(r)
+      W_nk(r)     = - sum_k' w_k' sum_m f_mk' u_mk'(r) phi(r)    (periodic part of V_x psi_nk)
+      (V_x psi_nk)(G) = (sqrt(Omega)/Ntot) fft(W_nk)(G),  G in S_k
+      E_x = -(Omega/2) sum_{k,k'} w_k w_k' sum_{n,m} f_nk f_mk' sum_G v(G + q) |fft(rho)(G)/Ntot|^2
+    ``c_list[k]``: [nb, npw_k]; ``occ``: [nk, nb]; ``miller_list[k]``: the sphere S_k;
+    ``kfrac``: [nk, 3] reduced coordinates; ``weights``: [nk].  Every ordered
+    pair of states is evaluated with its own transforms.  Returns (list of
+    [nb, npw_k] arrays, E_x).
+    """
+    from .lattice import reciprocal_lattice, g2_of_miller_k
+    grid = tuple(int(n) for n in grid)
+    nk = len(c_list)
+    occ = np.asarray(occ, dtype=np.float64).reshape(nk, -1)
+    w = np.asarray(weights, dtype=np.float64)
+    kf = np.asarray(kfrac, dtype=np.float64).reshape(nk, 3)
+    vol = cell_volume(cell)
+    b = reciprocal_lattice(cell)
+    ntot = grid[0] * grid[1] * grid[2]
+    u = [orbitals_to_real(c_list[k], miller_list[k], grid, cell, real=False) for k in range(nk)]
+    from .lattice import grid_miller
+    gm = np.moveaxis(grid_miller(grid), 0, -1)
+    out = []
+    esum = 0.0
+    for k in range(nk):
+        nb = u[k].shape[0]
+        vk = np.empty((nb, len(miller_list[k])), dtype=np.complex128)
+        for n in range(nb):
+            acc = np.zeros(grid, dtype=np.complex128)
+            for kp in range(nk):
+                vq = coulomb_kernel(kind, g2_of_miller_k(gm, b, kf[k] - kf[kp]), vol, omega)
+                for m in range(u[kp].shape[0]):
+                    rho_g = _fftn(np.conj(u[kp][m]) * u[k][n])
+                    acc -= w[kp] * occ[kp, m] * u[kp][m] * _ifftn(vq * rho_g)
+                    esum += w[k] * w[kp] * occ[k, n] * occ[kp, m] * float(
+                        np.sum(vq * (rho_g * np.conj(rho_g)).real)) / (ntot * ntot)
+            vk[n] = real_to_sphere(acc, miller_list[k], grid, cell)
+        out.append(vk)
+    return out, -0.5 * vol * esum

@@ -97,3 +97,39 @@ def grid_g2(grid, cell):
     """|G|^2 on every point of the full FFT grid (fftfreq order)."""
     m = grid_miller(grid)
     return g2_of_miller(np.moveaxis(m, 0, -1), reciprocal_lattice(cell))
+
+
+def g2_of_miller_k(miller, recip, kfrac):
+    """|k + G|^2 with k = kf1 b1 + kf2 b2 + kf3 b3 (reduced coordinates).
+
+    Each Cartesian component is ((m1 + kf1) b1x + (m2 + kf2) b2x) + (m3 + kf3) b3x,
+    the sum m + kf formed first; kf = 0 gives exactly g2_of_miller.
+    """
+    m = np.asarray(miller, dtype=np.float64)
+    k = np.asarray(kfrac, dtype=np.float64)
+    b = np.asarray(recip, dtype=np.float64)
+    u = [m[..., a] + k[a] for a in range(3)]
+    comps = [(u[0] * b[0, x] + u[1] * b[1, x]) + u[2] * b[2, x] for x in range(3)]
+    return (comps[0] * comps[0] + comps[1] * comps[1]) + comps[2] * comps[2]
+
+
+def gsphere_k(grid, cell, ecut, kfrac):
+    """Miller indices of {G : |k + G|^2 <= 2 Ecut} in canonical order
+    (ascending FP64 |k + G|^2, ties lexicographic on (m1, m2, m3))."""
+    grid = [int(n) for n in grid]
+    b = reciprocal_lattice(cell)
+    a = np.asarray(cell, dtype=np.float64).reshape(3, 3)
+    gmax = np.sqrt(2.0 * ecut)
+    kf = np.asarray(kfrac, dtype=np.float64)
+    mmax = [int(np.floor(gmax * np.linalg.norm(a[i]) / (2.0 * np.pi) + abs(kf[i]))) + 1 for i in range(3)]
+    r = [np.arange(-mm, mm + 1) for mm in mmax]
+    m1, m2, m3 = np.meshgrid(r[0], r[1], r[2], indexing="ij")
+    mill = np.stack([m1.ravel(), m2.ravel(), m3.ravel()], axis=1)
+    g2 = g2_of_miller_k(mill, b, kf)
+    keep = g2 <= 2.0 * ecut
+    mill, g2 = mill[keep], g2[keep]
+    for ax in range(3):
+        if mill.size and 2 * int(np.abs(mill[:, ax]).max()) >= grid[ax]:
+            raise ValueError("G-sphere does not fit on the FFT grid")
+    order = np.lexsort((mill[:, 2], mill[:, 1], mill[:, 0], g2))
+    return mill[order].astype(np.int32), g2[order]

@@ -67,3 +67,22 @@ def gaussian_orbital(miller, cell, sigma, center=(0.0, 0.0, 0.0)):
     c = c * np.exp(-1j * (g @ np.asarray(center, dtype=np.float64)))
     c = c / np.sqrt(np.sum(np.abs(c) ** 2))
     return c[None, :].astype(np.complex128)
+
+
+def orbitals_k(miller, cell, kfrac, nbands, seed):
+    """Orthonormal Bloch orbitals at k (reduced coordinates kfrac), complex128 [nbands, npw].
+
+    c(G) = (N(0,1) + i N(0,1)) exp(-|k + G|^2 / 4), Loewdin-orthonormalised with
+    the Hermitian overlap S = C* C^T; no symmetry between G and -G.
+    """
+    m = np.asarray(miller, dtype=np.float64) + np.asarray(kfrac, dtype=np.float64)[None, :]
+    g = m @ _recip(cell)
+    g2 = np.einsum("gx,gx->g", g, g)
+    rng = np.random.default_rng(seed)
+    npw = m.shape[0]
+    c = rng.standard_normal((nbands, npw)) + 1j * rng.standard_normal((nbands, npw))
+    c = c * np.exp(-0.25 * g2)[None, :]
+    s = np.conj(c) @ c.T
+    w, u = np.linalg.eigh(s)
+    x = (u * (1.0 / np.sqrt(w))[None, :]) @ np.conj(u).T
+    return np.ascontiguousarray(x.T @ c)
