@@ -11,7 +11,8 @@ from paper_1305_7313_gb300 import synth
 
 
 def test_single_gamma_point_is_the_gamma_oracle_with_complex_orbitals():
-    grid = (8, 8, 8)
+    # a grid that holds the pair-density sphere, so the Nyquist planes carry nothing
+    grid = (12, 12, 12)
     cell = (6.0 * np.eye(3)).ravel()
     mill, _ = oracle.gsphere(grid, cell, 4.0)
     mk, _ = oracle.gsphere_k(grid, cell, 4.0, (0.0, 0.0, 0.0))
@@ -27,8 +28,9 @@ def test_single_gamma_point_is_the_gamma_oracle_with_complex_orbitals():
 def test_two_k_points_equal_the_gamma_point_of_the_doubled_cell():
     # cell (L1, L, L) sampled at k = 0 and k = b1/2 (weights 1/2) is the Gamma
     # point of the supercell (2 L1, L, L): k + G = 2 (m1 + kf1) b1' + m2 b2 + m3 b3
+    # grids that hold the pair-density sphere, so the Nyquist planes carry nothing
     L1, L, ecut, nb = 5.0, 6.0, 3.0, 3
-    grid, sgrid = (8, 8, 8), (16, 8, 8)
+    grid, sgrid = (12, 12, 12), (24, 12, 12)
     cell = np.diag([L1, L, L]).ravel()
     scell = np.diag([2 * L1, L, L]).ravel()
     kf = np.array([[0.0, 0, 0], [0.5, 0, 0]])
@@ -76,3 +78,20 @@ def test_kpoint_operator_is_hermitian_per_k_and_gives_the_energy():
         assert np.linalg.eigvalsh(0.5 * (m + m.conj().T)).max() <= 1e-12 * np.max(np.abs(m))
         e2 += 0.5 * w[k] * float(np.sum(occ[k] * np.diag(m).real))
     assert abs(e2 - ek) <= 1e-12 * abs(ek)
+
+
+def test_pair_reversal_symmetry_holds_with_nyquist_planes_dropped():
+    # on a grid too small for the pair densities (aliasing), V_x stays Hermitian
+    # per k because the kernel is zero on the Nyquist planes
+    grid = (8, 8, 8)
+    cell = (6.0 * np.eye(3)).ravel()
+    kf = np.array([[0.0, 0, 0], [0.5, 0.25, 0]])
+    mills, cs = [], []
+    for k in range(2):
+        m, _ = oracle.gsphere_k(grid, cell, 4.0, kf[k])
+        mills.append(m)
+        cs.append(synth.orbitals_k(m, cell, kf[k], 3, 70 + k))
+    vk, ek = oracle.fock_apply_kpoints(cs, np.full((2, 3), 2.0), mills, kf, [0.5, 0.5], grid, cell, ERFC, 0.7)
+    for k in range(2):
+        m = np.conj(cs[k]) @ vk[k].T
+        assert np.max(np.abs(m - m.conj().T)) <= 1e-13 * np.max(np.abs(m))
