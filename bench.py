@@ -279,6 +279,48 @@ def run_batched(args, peaks, peak_src):
             "clocks": clk.summary()}
 
 
+def run_kpoints(args, peaks, peak_src):
+    """2x2x2 Monkhorst-Pack mesh (k in {0, 1/2}^3, weights 1/8), 48^3 grid,
+    L = 13.5 bohr, Ecut = 12 Ha, 32 bands per k, erfc kernel, mixed form."""
+    import itertools
+    import torch
+    from paper_1305_7313_gb300 import FockKPlan, PREC_MIXED32, synth
+    from paper_1305_7313_gb300.workloads import ERFC, cubic_cell
+    n, L, ecut, nb, omega = 48, 13.5, 12.0, 32, 0.106
+    if args.nb:
+        nb = min(nb, args.nb)
+    kpts = np.array(list(itertools.product([0.0, 0.5], repeat=3)))
+    wk = np.full(len(kpts), 1.0 / len(kpts))
+    cell = cubic_cell(L)
+    plan = FockKPlan(n, cell, ecut, kpts, wk, ERFC, omega, PREC_MIXED32)
+    psi = [torch.from_numpy(synth.orbitals_k(plan.miller(k), cell, kpts[k], nb, 2300 + k)).cuda()
+           for k in range(len(kpts))]
+    occ = np.full((len(kpts), nb), 2.0)
+    for _ in range(args.warmup):
+        plan.apply(psi, occ)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record()
+    for _ in range(args.steps):
+        plan.apply(psi, occ)
+    end.record()
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    ns = len(kpts) * nb
+    pairs = ns * (ns + 1) // 2
+    nbytes = pairs * 4.0 * n**3 * 8.0  # complex64 full spectrum: written, read + written, read
+    achieved = nbytes * args.steps / (ms * 1e-3) / 1e9
+    plan.close()
+    return {"workload": "kpoints8_mixed32_erfc_L13.5_N48_nb32", "kpoints": len(kpts), "bands_per_k": nb,
+            "value": pairs * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "pairs": pairs, "dtype": "f32",
+            "roofline": {"bound": "hbm", "kernel": "pair passes (whole step)", "achieved": achieved,
+                         "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                         "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                         "peak_src": peak_src + " (hbm copy)"}}
+
+
 def cpu_baseline(w, nbands_sample=32):
     """The FP64 oracle on the first `nbands_sample` bands of the workload."""
     import oracle
@@ -337,6 +379,7 @@ def main():
     ap.add_argument("--nb", type=int, default=None,
                     help="override the band count of the workloads (small profiling cases)")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-kpoints", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--tune-bands", type=int, default=64,
                     help="band count of the subset the apply's pair-block parameters are tuned on")
@@ -424,6 +467,11 @@ def main():
         batched = run_batched(args, peaks, peak_src)
         torch.cuda.empty_cache()
 
+    kpoints = None
+    if not args.no_kpoints and world == 1:
+        kpoints = run_kpoints(args, peaks, peak_src)
+        torch.cuda.empty_cache()
+
     if rank != 0:
         return
     cpu = None
@@ -450,6 +498,7 @@ def main():
         "tuned": tuned,
         "mixed32": mixed,
         "batched": batched,
+        "kpoints": kpoints,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

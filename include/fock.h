@@ -340,6 +340,70 @@ const char* fock_batch_last_error(fock_batch_t batch);
 /* Release the batch (not the plans).  NULL is accepted. */
 fock_status fock_batch_destroy(fock_batch_t batch);
 
+/* ---------------------------------------------------------------- k points
+ *
+ * The general form of §4's E_x and V_x equations: Bloch orbitals
+ * psi_nk(r) = exp(i k.r) u_nk(r) at nk points k of the Brillouin zone, the sums
+ * over k and q = k - k', and the kernel at |G + q| (the 1/|G+q|^2 of §4, made
+ * finite as in fock_kernel).  With states s = k * nb + n and weights w_k:
+ *   psi_nk(r)       = Omega^-1/2 sum_{G in S_k} c_nk(G) exp(i (k + G).r),
+ *                     S_k = {G : |k + G|^2 / 2 <= Ecut}
+ *   phi(r)          = IFFT[v(G + q) FFT(u_{mk'}* u_{nk})](r)
+ *   (V_x psi_nk)(G) = (sqrt(Omega)/Ntot) FFT[- sum_k' w_k' sum_m f_mk' u_mk' phi](G),  G in S_k
+ *   E_x             = 1/2 sum_k w_k sum_n f_nk <psi_nk | V_x psi_nk>
+ * Orbitals are general complex functions (no Gamma symmetry); every unique
+ * pair of states takes one complex transform (the reverse pair is its complex
+ * conjugate).  The kernel is zero on the Nyquist planes (frequency -N/2 of an
+ * even axis): there the reverse pair is not the conjugate for q != 0.  Grids
+ * that hold the pair-density sphere (N > 2 max |m|) have nothing on them.  Each S_k is in canonical order: ascending |k + G|^2 evaluated
+ * as in fock_plan_create with m_a replaced by (m_a + k_a) formed first, ties
+ * lexicographic on (m1, m2, m3).
+ */
+typedef struct fock_kplan* fock_kplan_t;
+
+/*
+ * fock_kplan_create — spheres, v(G + q) tables for every distinct q = k_b - k_a,
+ * and the FFT plan.
+ *   kpts   host double [nk][3]: k in reduced coordinates (k = sum_a kpts_a b_a).
+ *   wk     host double [nk]: k-point weights (usually summing to 1).
+ *   Other arguments as fock_plan_create (the grid must hold every S_k).
+ * Errors: INVALID_ARG, UNSUPPORTED_SIZE, GRID_TOO_SMALL, OOM, CUDA.
+ */
+fock_status fock_kplan_create(fock_kplan_t* out, const int grid[3], const double cell[9], double ecut_ha,
+                              int nk, const double* kpts, const double* wk, fock_kernel kind,
+                              const double* kparams, int nkparams, fock_precision prec);
+
+/* The sphere S_k = {G : |k + G|^2 / 2 <= Ecut} (kpt host double[3], reduced)
+ * in canonical order without creating a plan; as fock_gsphere otherwise. */
+fock_status fock_gsphere_k(const int grid[3], const double cell[9], double ecut_ha, const double* kpt,
+                           int64_t* npw, int32_t* miller, int64_t capacity);
+
+/* Plane waves and Miller indices of S_k (host outputs; miller int32 [npw_k][3]). */
+fock_status fock_kplan_npw(fock_kplan_t plan, int k, int64_t* npw);
+fock_status fock_kplan_gvectors(fock_kplan_t plan, int k, int32_t* miller);
+
+/* Pairs per launch of the pair passes (one pair per chain here).  INVALID_ARG. */
+fock_status fock_kplan_set_batch(fock_kplan_t plan, int chain_batch);
+
+/*
+ * fock_kplan_apply — V_x psi_nk for every k and E_x.
+ *   psi_G    host array [nk] of device pointers, complex128 [nb][npw_k] each.
+ *   nb       bands per k point.
+ *   occ      host double [nk][nb]: occupations f_nk.
+ *   vpsi_G   host array [nk] of device pointers, complex128 [nb][npw_k] each
+ *            (each must not overlap its psi_G).
+ *   ex       host double or NULL.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+fock_status fock_kplan_apply(fock_kplan_t plan, const void* const* psi_G, int nb, const double* occ,
+                             void* const* vpsi_G, double* ex, fock_stream_t stream);
+
+/* Description of the last failure ("" if none); plan may be NULL for create. */
+const char* fock_kplan_last_error(fock_kplan_t plan);
+
+/* Release the k-point plan.  NULL is accepted. */
+fock_status fock_kplan_destroy(fock_kplan_t plan);
+
 /* Release the plan and everything it holds.  NULL is accepted. */
 fock_status fock_destroy(fock_plan_t plan);
 

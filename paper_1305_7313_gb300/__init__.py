@@ -27,6 +27,11 @@ from ._lib import (  # noqa: F401
     fock_apply_shard,
     fock_destroy,
     fock_gsphere,
+    fock_kplan_apply,
+    fock_kplan_create,
+    fock_kplan_destroy,
+    fock_kplan_gvectors,
+    fock_kplan_set_batch,
     fock_last_error,
     fock_pair_energies,
     fock_pair_energies_static,
@@ -42,4 +47,4 @@ from ._lib import (  # noqa: F401
     fock_plan_stats,
     fock_status_string,
 )
-from .plan import FockBatch, FockPlan  # noqa: F401
+from .plan import FockBatch, FockKPlan, FockPlan  # noqa: F401

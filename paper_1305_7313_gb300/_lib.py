@@ -97,6 +97,15 @@ _SIGNATURES = {
     "fock_batch_info": [_vp, _c_i64_p, _c_i64_p, _c_int_p, _c_int_p, _c_dbl_p],
     "fock_batch_last_error": [_vp],
     "fock_batch_destroy": [_vp],
+    "fock_kplan_create": [ctypes.POINTER(_vp), _c_int_p, _c_dbl_p, ctypes.c_double, ctypes.c_int, _c_dbl_p,
+                          _c_dbl_p, ctypes.c_int, _c_dbl_p, ctypes.c_int, ctypes.c_int],
+    "fock_gsphere_k": [_c_int_p, _c_dbl_p, ctypes.c_double, _c_dbl_p, _c_i64_p, _c_i32_p, ctypes.c_int64],
+    "fock_kplan_npw": [_vp, ctypes.c_int, _c_i64_p],
+    "fock_kplan_gvectors": [_vp, ctypes.c_int, _c_i32_p],
+    "fock_kplan_set_batch": [_vp, ctypes.c_int],
+    "fock_kplan_apply": [_vp, ctypes.POINTER(_vp), ctypes.c_int, _c_dbl_p, ctypes.POINTER(_vp), _c_dbl_p, _vp],
+    "fock_kplan_last_error": [_vp],
+    "fock_kplan_destroy": [_vp],
     "fock_destroy": [_vp],
     "fock_status_string": [ctypes.c_int],
     "fock_last_error": [_vp],
@@ -122,7 +131,8 @@ def load():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = (ctypes.c_char_p if name in ("fock_status_string", "fock_last_error",
-                                                   "fock_batch_last_error") else ctypes.c_int)
+                                                   "fock_batch_last_error", "fock_kplan_last_error")
+                       else ctypes.c_int)
     _lib = lib
     return lib
 
@@ -377,6 +387,66 @@ def fock_batch_last_error(batch=None):
 
 def fock_batch_destroy(batch):
     _check_batch(load().fock_batch_destroy(batch))
+
+
+def _check_k(status, plan=None):
+    if status != 0:
+        raise FockError(status, load().fock_kplan_last_error(plan).decode())
+
+
+def fock_kplan_create(grid, cell, ecut, kpts, weights, kind=SPENCER_ALAVI, kparams=(), prec=PREC_FP64):
+    lib = load()
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    c, cp = _dbl_array(np.asarray(cell, dtype=np.float64).ravel())
+    k, kp = _dbl_array(np.asarray(kpts, dtype=np.float64).reshape(-1, 3).ravel())
+    w, wp = _dbl_array(np.asarray(weights, dtype=np.float64).ravel())
+    pr, prp = _dbl_array(list(kparams) if len(kparams) else [0.0])
+    h = _vp()
+    _check_k(lib.fock_kplan_create(ctypes.byref(h), g, cp, float(ecut), len(w), kp, wp, int(kind), prp,
+                                   len(kparams), int(prec)))
+    return h.value
+
+
+def fock_gsphere_k(grid, cell, ecut, kpt):
+    """Miller indices [npw, 3] of S_k in canonical order (host only)."""
+    lib = load()
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    c, cp = _dbl_array(np.asarray(cell, dtype=np.float64).ravel())
+    k, kp = _dbl_array(np.asarray(kpt, dtype=np.float64).ravel())
+    n = ctypes.c_int64()
+    _check_k(lib.fock_gsphere_k(g, cp, float(ecut), kp, ctypes.byref(n), None, 0))
+    out = np.empty((n.value, 3), dtype=np.int32)
+    _check_k(lib.fock_gsphere_k(g, cp, float(ecut), kp, ctypes.byref(n), out.ctypes.data_as(_c_i32_p), n.value))
+    return out
+
+
+def fock_kplan_gvectors(plan, k):
+    n = ctypes.c_int64()
+    _check_k(load().fock_kplan_npw(plan, int(k), ctypes.byref(n)), plan)
+    out = np.empty((n.value, 3), dtype=np.int32)
+    _check_k(load().fock_kplan_gvectors(plan, int(k), out.ctypes.data_as(_c_i32_p)), plan)
+    return out
+
+
+def fock_kplan_set_batch(plan, chain_batch):
+    _check_k(load().fock_kplan_set_batch(plan, int(chain_batch)), plan)
+
+
+def fock_kplan_apply(plan, psi_G, occ, vpsi_G, want_ex=True, stream=None):
+    """V_x psi for every k (lists of device tensors [nb, npw_k]); returns E_x or None."""
+    nk = len(psi_G)
+    nb = int(psi_G[0].shape[0])
+    pp = (_vp * nk)(*[_dev_ptr(p, "psi_G").value for p in psi_G])
+    vp = (_vp * nk)(*[_dev_ptr(v, "vpsi_G", tuple(p.shape)).value for v, p in zip(vpsi_G, psi_G)])
+    o, op = _dbl_array(np.asarray(occ, dtype=np.float64).reshape(nk, nb).ravel())
+    ex = ctypes.c_double()
+    _check_k(load().fock_kplan_apply(plan, pp, nb, op, vp, ctypes.byref(ex) if want_ex else None,
+                                     _stream(stream)), plan)
+    return ex.value if want_ex else None
+
+
+def fock_kplan_destroy(plan):
+    _check_k(load().fock_kplan_destroy(plan))
 
 
 def fock_destroy(plan):

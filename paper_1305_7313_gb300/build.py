@@ -57,6 +57,9 @@ def _jobs():
     jobs.append(("fock_plan.o", [cxx, "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall",
                                  "-I" + os.path.join(cuda, "include")] + inc +
                  ["-c", os.path.join(CSRC, "fock_plan.cpp")]))
+    jobs.append(("fock_kpoints.o", [cxx, "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall",
+                                    "-I" + os.path.join(cuda, "include")] + inc +
+                 ["-c", os.path.join(CSRC, "fock_kpoints.cpp")]))
     jobs.append(("fock_common.o", nv + ["-c", os.path.join(CSRC, "fock_common.cu")]))
     jobs.append(("fock_static.o", nv + ["-c", os.path.join(CSRC, "fock_static.cu")]))
     for tag, t in (("f64", "double"), ("f32", "float")):
@@ -67,6 +70,7 @@ def _jobs():
         for tag, t in (("f64", "double"), ("f32", "float")):
             jobs.append(("fock_%s_%d.o" % (tag, n),
                          nv + ["-DFOCK_T=" + t, "-DFOCK_N=%d" % n, "-DFOCK_OPS_NAME=kOps_%s_%d" % (tag, n),
+                               "-DFOCK_KOPS_NAME=kKOps_%s_%d" % (tag, n),
                                "-c", os.path.join(CSRC, "fock_kernels_inst.cu")]))
     return nvcc, jobs
 

@@ -7,7 +7,9 @@ namespace fockx {
 
 #define FOCK_DECLARE(N)                 \
   extern const KernelOps kOps_f64_##N; \
-  extern const KernelOps kOps_f32_##N;
+  extern const KernelOps kOps_f32_##N; \
+  extern const KOps kKOps_f64_##N;     \
+  extern const KOps kKOps_f32_##N;
 FOCK_GRID_SIZES(FOCK_DECLARE)
 #undef FOCK_DECLARE
 
@@ -16,6 +18,14 @@ const KernelOps* find_kernel_ops(int prec, int n) {
   if (n == N) return prec == 0 ? &kOps_f64_##N : &kOps_f32_##N;
   FOCK_GRID_SIZES(FOCK_FIND)
 #undef FOCK_FIND
+  return nullptr;
+}
+
+const KOps* find_kops(int prec, int n) {
+#define FOCK_FINDK(N) \
+  if (n == N) return prec == 0 ? &kKOps_f64_##N : &kKOps_f32_##N;
+  FOCK_GRID_SIZES(FOCK_FINDK)
+#undef FOCK_FINDK
   return nullptr;
 }
 

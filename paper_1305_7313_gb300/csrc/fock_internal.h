@@ -41,6 +41,9 @@ struct DevPlan {
   double psi_scale;    // 1 / sqrt(Omega)
   double out_scale;    // sqrt(Omega) / Ntot
   int msmall2;         // |m|^2 at or below which kernel terms are done in FP64 (mixed form)
+  // Brillouin-zone sampling: full-grid tables [nq][N][N][N] of v(G + q)
+  const void* vtabq;      // v / Ntot in the working precision
+  const double* vtabq64;  // v in FP64
 };
 
 struct KernelOps {
@@ -67,6 +70,22 @@ struct KernelOps {
 
 // Kernels for grid size n and precision (0: FP64, 1: mixed); NULL if not built.
 const KernelOps* find_kernel_ops(int prec, int n);
+
+// Kernels of the Brillouin-zone-sampled apply (complex periodic parts, one pair
+// per transform; band0 is a global state index, psiG / vpsiG point at the
+// first band of the batch).
+struct KOps {
+  cudaError_t (*configure)();
+  cudaError_t (*to_real)(const DevPlan&, const double2* psiG, int npw, const int* gidx, int band0, int nbat,
+                         void* X, void* u, cudaStream_t);
+  cudaError_t (*pair_fwd)(const DevPlan&, const void* u, const Chain* ch, int nch, void* H, cudaStream_t);
+  cudaError_t (*pair_col)(const DevPlan&, void* H, const Chain* ch, int nch, double* epair, cudaStream_t);
+  cudaError_t (*pair_inv)(const DevPlan&, const void* u, void* W, const void* occw, const Chain* ch, int nch,
+                          const void* H, cudaStream_t);
+  cudaError_t (*to_sphere)(const DevPlan&, const void* W, int band0, int nbat, int npw, const int* gidx,
+                           void* X, double2* vpsiG, cudaStream_t);
+};
+const KOps* find_kops(int prec, int n);
 
 // One system of a batch as the persistent kernel sees it.
 struct SysDesc {

@@ -29,6 +29,10 @@ namespace fockx {
 
 __device__ __forceinline__ int freq_of(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
 
+// Rounds of global loads each thread issues before storing them to shared
+// memory in the pass prologues (memory-level parallelism).
+constexpr int kLoadUnroll = 4;
+
 template <class T> __device__ __forceinline__ void atomic_add_real(T* p, T v) { atomicAdd(p, v); }
 
 // Sum of four doubles over the CTA; the result is valid in thread 0.
@@ -293,11 +297,25 @@ __device__ __forceinline__ void pair_fwd_task(const DevPlan& g, const T* __restr
   const T* paj = psi + (int64_t)ch.aj * g.ntot + plane0;
   const T* pbi = psi + (int64_t)(hb ? ch.bi : 0) * g.ntot + plane0;
   const T* pbj = psi + (int64_t)(hb ? ch.bj : 0) * g.ntot + plane0;
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int i2 = e / N, i3 = e - i2 * N;
-    const T a = pai[e] * paj[e];
-    const T b = hb ? pbi[e] * pbj[e] : T(0);
-    P[i2 * RP + i3] = cmake<T>(a, b);
+  // kLoadUnroll rounds of loads are issued before their shared-memory stores
+  for (int e0 = threadIdx.x; e0 < N * N; e0 += kLoadUnroll * blockDim.x) {
+    T a[kLoadUnroll], b[kLoadUnroll];
+#pragma unroll
+    for (int u = 0; u < kLoadUnroll; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < N * N) {
+        a[u] = pai[e] * paj[e];
+        b[u] = hb ? pbi[e] * pbj[e] : T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadUnroll; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < N * N) {
+        const int i2 = e / N, i3 = e - i2 * N;
+        P[i2 * RP + i3] = cmake<T>(a[u], b[u]);
+      }
+    }
   }
   __syncthreads();
   fft_lines<T, N, -1, N, G::TLP, RP, 1, MAXT>(P, tw);  // along i3
@@ -335,9 +353,21 @@ __device__ __forceinline__ void pair_col_task(const DevPlan& g, cplx<T>* __restr
   C* tw = S + N * NC;
   double* red = reinterpret_cast<double*>(tw + N);
   load_twiddles<T>(tw, g);
-  for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
-    const int i1 = e / NC, c = e - i1 * NC;
-    S[e] = __ldcg(Hc + ((int64_t)i1 * N + k2) * NC + c);
+  for (int e0 = threadIdx.x; e0 < N * NC; e0 += kLoadUnroll * blockDim.x) {
+    C v[kLoadUnroll];
+#pragma unroll
+    for (int u = 0; u < kLoadUnroll; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < N * NC) {
+        const int i1 = e / NC, c = e - i1 * NC;
+        v[u] = __ldcg(Hc + ((int64_t)i1 * N + k2) * NC + c);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadUnroll; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < N * NC) S[e] = v[u];
+    }
   }
   __syncthreads();
   fft_lines<T, N, -1, NC, G::TLC, 1, NC, MAXT>(S, tw);  // along i1
@@ -459,20 +489,32 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
   C* tw = P + N * RP;
   load_twiddles<T>(tw, g);
   const C* Hp = Hc + (int64_t)i1 * N * NC;
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int k2 = e / N, k3 = e - k2 * N;
-    C a, b;
-    if (k3 < KH) {
-      a = __ldcg(Hp + k2 * NC + k3);
-      b = __ldcg(Hp + k2 * NC + KH + k3);
-    } else {
-      const int m2 = k2 == 0 ? 0 : N - k2, m3 = N - k3;
-      a = __ldcg(Hp + m2 * NC + m3);
-      b = __ldcg(Hp + m2 * NC + KH + m3);
-      a.y = -a.y;
-      b.y = -b.y;
+  for (int e0 = threadIdx.x; e0 < N * N; e0 += kLoadUnroll * blockDim.x) {
+    C a[kLoadUnroll], b[kLoadUnroll];
+#pragma unroll
+    for (int u = 0; u < kLoadUnroll; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < N * N) {
+        const int k2 = e / N, k3 = e - k2 * N;
+        // k3 > N/2 is the mirror image of the stored half: A(-k) = A(k)*
+        const bool lo = k3 < KH;
+        const int r = lo ? k2 : (k2 == 0 ? 0 : N - k2), c = lo ? k3 : N - k3;
+        a[u] = __ldcg(Hp + r * NC + c);
+        b[u] = __ldcg(Hp + r * NC + KH + c);
+        if (!lo) {
+          a[u].y = -a[u].y;
+          b[u].y = -b[u].y;
+        }
+      }
     }
-    P[k2 * RP + k3] = cmake<T>(a.x - b.y, a.y + b.x);
+#pragma unroll
+    for (int u = 0; u < kLoadUnroll; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < N * N) {
+        const int k2 = e / N, k3 = e - k2 * N;
+        P[k2 * RP + k3] = cmake<T>(a[u].x - b[u].y, a[u].y + b[u].x);
+      }
+    }
   }
   __syncthreads();
   fft_lines<T, N, +1, N, G::TLP, 1, RP, MAXT>(P, tw);  // along k2

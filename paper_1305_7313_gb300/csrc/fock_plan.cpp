@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "fock_internal.h"
+#include "fock_lattice.h"
 
 using fockx::Chain;
 using fockx::DevPlan;
@@ -23,21 +24,17 @@ using fockx::KernelOps;
 
 namespace {
 
-constexpr double kTwoPi = 2.0 * 3.14159265358979323846;
-constexpr double kPi = 3.14159265358979323846;
 constexpr int kBandBlock = 16;                  // default bands per block of the pair schedule
 constexpr size_t kChainBufferBytes = 120u << 20;  // default size of the pair-transform buffer
 constexpr int kMsmall2 = 3;                     // |m|^2 of the kernel terms kept in FP64 (mixed)
 
 thread_local std::string g_create_error;
 
-void cross3(const double* a, const double* b, double* c) {
-  c[0] = a[1] * b[2] - a[2] * b[1];
-  c[1] = a[2] * b[0] - a[0] * b[2];
-  c[2] = a[0] * b[1] - a[1] * b[0];
-}
-
-int freq_of(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
+using fockx::lattice::GEntry;
+using fockx::lattice::build_sphere;
+using fockx::lattice::freq_of;
+using fockx::lattice::g2_of;
+using fockx::lattice::kPi;
 
 struct Workspace {
   int nb_cap = 0;
@@ -143,79 +140,12 @@ void free_ws(Workspace& w) {
   w = Workspace{};
 }
 
-// G = m1 b1 + m2 b2 + m3 b3 componentwise as ((m1 b1x + m2 b2x) + m3 b3x);
-// |G|^2 = (Gx^2 + Gy^2) + Gz^2.
-double g2_of(const double* b, int m1, int m2, int m3) {
-  double c[3];
-  for (int x = 0; x < 3; ++x) c[x] = (double(m1) * b[0 + x] + double(m2) * b[3 + x]) + double(m3) * b[6 + x];
-  return (c[0] * c[0] + c[1] * c[1]) + c[2] * c[2];
-}
-
-struct GEntry {
-  double g2;
-  int m[3];
-};
-
 void reciprocal(const double* cell, double* recip, double* vol_signed) {
-  double c23[3], c31[3], c12[3];
-  cross3(cell + 3, cell + 6, c23);
-  cross3(cell + 6, cell + 0, c31);
-  cross3(cell + 0, cell + 3, c12);
-  const double vol = (cell[0] * c23[0] + cell[1] * c23[1]) + cell[2] * c23[2];
-  const double fac = kTwoPi / vol;
-  for (int x = 0; x < 3; ++x) {
-    recip[0 + x] = c23[x] * fac;
-    recip[3 + x] = c31[x] * fac;
-    recip[6 + x] = c12[x] * fac;
-  }
-  *vol_signed = vol;
-}
-
-// The sphere |G|^2 <= 2 Ecut sorted by (|G|^2, m1, m2, m3); false if it does not
-// fit on an N^3 grid (2 |m_a| >= N).
-bool build_sphere(const double* cell, const double* recip, double ecut, int n,
-                  std::vector<GEntry>& sph) {
-  const double gmax = std::sqrt(2.0 * ecut);
-  int mmax[3];
-  for (int i = 0; i < 3; ++i) {
-    const double* a = cell + 3 * i;
-    const double len = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-    mmax[i] = (int)std::floor(gmax * len / kTwoPi) + 1;
-  }
-  sph.clear();
-  for (int m1 = -mmax[0]; m1 <= mmax[0]; ++m1)
-    for (int m2 = -mmax[1]; m2 <= mmax[1]; ++m2)
-      for (int m3 = -mmax[2]; m3 <= mmax[2]; ++m3) {
-        const double g2 = g2_of(recip, m1, m2, m3);
-        if (g2 <= 2.0 * ecut) sph.push_back(GEntry{g2, {m1, m2, m3}});
-      }
-  std::sort(sph.begin(), sph.end(), [](const GEntry& x, const GEntry& y) {
-    if (x.g2 != y.g2) return x.g2 < y.g2;
-    if (x.m[0] != y.m[0]) return x.m[0] < y.m[0];
-    if (x.m[1] != y.m[1]) return x.m[1] < y.m[1];
-    return x.m[2] < y.m[2];
-  });
-  for (const GEntry& e : sph)
-    for (int a = 0; a < 3; ++a)
-      if (2 * std::abs(e.m[a]) >= n) return false;
-  return true;
+  *vol_signed = fockx::lattice::reciprocal(cell, recip);
 }
 
 void kernel_value(const fock_plan* p, double g2, double* v, double* dv) {
-  if (p->kind == FOCK_KERNEL_SPENCER_ALAVI) {
-    const double rc = std::cbrt(3.0 * p->vol / (4.0 * kPi));
-    if (g2 == 0.0) {
-      *v = 2.0 * kPi * rc * rc;
-    } else {
-      const double s = std::sin(0.5 * std::sqrt(g2) * rc);
-      *v = 8.0 * kPi * s * s / g2;
-    }
-    *dv = 0.0;
-  } else {
-    const double w = p->omega;
-    *v = (g2 == 0.0) ? kPi / (w * w) : -4.0 * kPi * std::expm1(-g2 / (4.0 * w * w)) / g2;
-    *dv = -(2.0 * kPi / (w * w * w)) * std::exp(-g2 / (4.0 * w * w));
-  }
+  fockx::lattice::kernel_value(p->kind, p->vol, p->omega, g2, v, dv);
 }
 
 // Unique pairs i <= j in band blocks of kBandBlock (block rows outer), i outer and j

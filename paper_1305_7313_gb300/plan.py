@@ -160,3 +160,46 @@ class FockBatch:
             self.close()
         except Exception:
             pass
+
+
+class FockKPlan:
+    """Brillouin-zone-sampled cell: ``kpts`` [nk, 3] in reduced coordinates with
+    ``weights`` [nk]; one plane-wave sphere per k point (``miller(k)``)."""
+
+    def __init__(self, grid, cell, ecut, kpts, weights, kernel=_lib.SPENCER_ALAVI, omega=None,
+                 precision=_lib.PREC_FP64):
+        if isinstance(grid, int):
+            grid = (grid, grid, grid)
+        kp = () if kernel == _lib.SPENCER_ALAVI else (float(omega),)
+        self.grid = tuple(int(g) for g in grid)
+        self.kpts = np.asarray(kpts, dtype=np.float64).reshape(-1, 3)
+        self.weights = np.asarray(weights, dtype=np.float64).ravel()
+        self.handle = None
+        self.handle = _lib.fock_kplan_create(self.grid, cell, ecut, self.kpts, self.weights, kernel, kp, precision)
+        self._miller = {}
+
+    def miller(self, k):
+        if k not in self._miller:
+            self._miller[k] = _lib.fock_kplan_gvectors(self.handle, k)
+        return self._miller[k]
+
+    def set_batch(self, chain_batch):
+        _lib.fock_kplan_set_batch(self.handle, chain_batch)
+
+    def apply(self, psi, occ, stream=None):
+        """(list of V_x psi tensors, E_x) for device orbitals ``psi`` (one tensor per k)."""
+        import torch
+        out = [torch.empty_like(p) for p in psi]
+        ex = _lib.fock_kplan_apply(self.handle, psi, occ, out, True, stream)
+        return out, ex
+
+    def close(self):
+        if self.handle is not None:
+            _lib.fock_kplan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

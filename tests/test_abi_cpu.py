@@ -101,3 +101,12 @@ def test_null_arguments_are_rejected(lib):
     assert lib.fock_apply(None, None, 1, None, None, None, None, None) == 1
     assert lib.fock_destroy(None) == 0
     assert lib.fock_plan_set_batch(None, 4) == 1
+
+
+def test_kpoint_spheres_are_bit_identical_to_the_oracle(lib):
+    cells = [np.diag([7.0, 7.0, 7.0]), np.array([[6.0, 0.4, 0.0], [0.0, 6.5, 0.3], [0.2, 0.0, 5.5]])]
+    for cell in cells:
+        for kf in [(0.0, 0.0, 0.0), (0.5, 0.0, 0.0), (0.25, -0.25, 0.5), (1.0 / 3.0, 0.1, -0.45)]:
+            m = _lib.fock_gsphere_k((24, 24, 24), cell.ravel(), 6.0, kf)
+            mo, _ = oracle.gsphere_k((24, 24, 24), cell.ravel(), 6.0, kf)
+            assert np.array_equal(m, mo)

@@ -1,0 +1,93 @@
+"""Brillouin-zone-sampled apply (complex periodic parts, v(G + q)) against the
+FP64 k-point oracle."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1305_7313_gb300 import FockKPlan, _lib, synth
+from tests._common import cubic, rel_inf, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+KPTS = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [0.0, 0.5, 0.5], [0.25, -0.25, 0.5]])
+WK = np.array([0.4, 0.2, 0.3, 0.1])
+
+
+def kcase(N, L, ecut, nb, kind, omega, prec, kpts=KPTS, wk=WK, seed=40):
+    torch = require_gpu()
+    cell = cubic(L)
+    plan = FockKPlan(N, cell, ecut, kpts, wk, kind, omega, prec)
+    cs, mills, psi = [], [], []
+    for k in range(len(kpts)):
+        m = plan.miller(k)
+        mo, _ = oracle.gsphere_k((N, N, N), cell, ecut, kpts[k])
+        assert np.array_equal(m, mo)
+        c = synth.orbitals_k(m, cell, kpts[k], nb, seed + k)
+        cs.append(c)
+        mills.append(m)
+        psi.append(torch.from_numpy(c).cuda())
+    occ = np.linspace(2.0, 0.5, nb)[None, :].repeat(len(kpts), 0)
+    return torch, plan, cs, mills, psi, occ, cell
+
+
+@pytest.mark.parametrize("prec,tol_v,tol_e", [(_lib.PREC_FP64, 1e-10, 1e-10), (_lib.PREC_MIXED32, 2e-5, 5e-6)])
+def test_kpoints_match_the_oracle(prec, tol_v, tol_e):
+    N = 16
+    torch, plan, cs, mills, psi, occ, cell = kcase(N, 7.0, 6.0, 3, _lib.ERFC, 0.5, prec)
+    plan.set_batch(4)  # several pair launches, ragged tail
+    vk, ex = plan.apply(psi, occ)
+    vref, eref = oracle.fock_apply_kpoints(cs, occ, mills, KPTS, WK, (N, N, N), cell, "erfc", 0.5)
+    assert abs(ex - eref) <= tol_e * abs(eref)
+    vmax = max(np.max(np.abs(v)) for v in vref)
+    for k in range(len(KPTS)):
+        assert np.max(np.abs(vk[k].cpu().numpy() - vref[k])) <= tol_v * vmax
+
+
+def test_gamma_only_complex_orbitals_match_the_gamma_oracle():
+    # Ecut 6 at L = 10: the pair densities reach |m| = 10 < 12, so the Nyquist
+    # planes (where the k-point kernel is zero) carry nothing
+    N = 24
+    kp = np.zeros((1, 3))
+    torch, plan, cs, mills, psi, occ, cell = kcase(N, 10.0, 6.0, 5, _lib.SPENCER_ALAVI, None, _lib.PREC_FP64,
+                                                    kpts=kp, wk=[1.0])
+    vk, ex = plan.apply(psi, occ)
+    vref, eref, _ = oracle.fock_apply(cs[0], occ[0], mills[0], (N, N, N), cell, "spencer_alavi", real=False)
+    assert abs(ex - eref) <= 1e-10 * abs(eref)
+    assert rel_inf(vk[0].cpu().numpy(), vref) <= 1e-10
+
+
+@pytest.mark.parametrize("prec,tol_v,tol_e", [(_lib.PREC_FP64, 1e-10, 1e-10), (_lib.PREC_MIXED32, 2e-5, 5e-6)])
+def test_two_k_points_spencer_alavi_several_launches(prec, tol_v, tol_e):
+    # 2 k points x 6 bands: 78 unique pairs in launches of 5 chains (ragged tail of 3)
+    N = 24
+    kp = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.5]])
+    wk = np.array([0.75, 0.25])
+    torch, plan, cs, mills, psi, occ, cell = kcase(N, 9.0, 8.0, 6, _lib.SPENCER_ALAVI, None, prec, kpts=kp,
+                                                    wk=wk, seed=90)
+    plan.set_batch(5)
+    vk, ex = plan.apply(psi, occ)
+    vref, eref = oracle.fock_apply_kpoints(cs, occ, mills, kp, wk, (N, N, N), cell, "spencer_alavi")
+    assert abs(ex - eref) <= tol_e * abs(eref)
+    vmax = max(np.max(np.abs(v)) for v in vref)
+    for k in range(2):
+        assert np.max(np.abs(vk[k].cpu().numpy() - vref[k])) <= tol_v * vmax
+
+
+def test_one_band_per_k_point_and_empty_bands():
+    # nb = 1 (only pairs across k points and self pairs), then a zero occupation
+    N = 16
+    torch, plan, cs, mills, psi, occ, cell = kcase(N, 7.0, 6.0, 1, _lib.ERFC, 0.5, _lib.PREC_FP64, seed=120)
+    vk, ex = plan.apply(psi, occ)
+    vref, eref = oracle.fock_apply_kpoints(cs, occ, mills, KPTS, WK, (N, N, N), cell, "erfc", 0.5)
+    assert abs(ex - eref) <= 1e-10 * abs(eref)
+    vmax = max(np.max(np.abs(v)) for v in vref)
+    for k in range(len(KPTS)):
+        assert np.max(np.abs(vk[k].cpu().numpy() - vref[k])) <= 1e-10 * vmax
+    occ0 = occ.copy()
+    occ0[1, 0] = 0.0
+    vk, ex = plan.apply(psi, occ0)
+    vref, eref = oracle.fock_apply_kpoints(cs, occ0, mills, KPTS, WK, (N, N, N), cell, "erfc", 0.5)
+    assert abs(ex - eref) <= 1e-10 * abs(eref)
+    for k in range(len(KPTS)):
+        assert np.max(np.abs(vk[k].cpu().numpy() - vref[k])) <= 1e-10 * vmax
