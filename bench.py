@@ -39,6 +39,11 @@ def load_peaks():
 # maximum SM clock, i.e. 604 FP64 flops per clock over the 152 SMs (2 FMA per SM
 # per clock).
 FP64_FLOPS_PER_CLK = 1.25e12 / 2.070e9
+# Double-float form: the FP32 pipe issues 128 lanes per SM per clock (152 SMs);
+# a double-float add costs 11 FP32 instructions, a multiply 7, so the radix-2
+# mix of the 5 n log2 n count (6 adds, 4 multiplies per 10 flops) costs 9.4
+# FP32 instructions per flop.
+DF64_FLOPS_PER_CLK = 152 * 128 / 9.4
 
 
 def workload(name):
@@ -173,17 +178,20 @@ def roofline(form, plan, res, steps, peaks, peak_src):
     ms_per_launch = res["phase_ms"][dom] / max(1, launches)
     chains_per_launch = st["chains"] / max(1, st["phase_launches"][dom])
     log2n = np.log2(n)
-    if form == "fp64":
+    if form in ("fp64", "df64"):
         # 5 n log2 n flops per complex line transform of length n; the plane passes
         # do 2 N^2 lines, the column pass N (N+2) lines forward and as many inverse
         per_chain = {"pair_fwd": 5 * ntot * 2 * log2n, "pair_inv": 5 * ntot * 2 * log2n,
                      "pair_col": 2 * 5 * ntot * log2n * nc / n}[dom]
         achieved = per_chain * chains_per_launch / (ms_per_launch * 1e-3) / 1e12
         mhz = res["clocks"].get("sm_mhz") or 2070.0
-        peak = FP64_FLOPS_PER_CLK * 2070.0e6 / 1e12
+        per_clk = FP64_FLOPS_PER_CLK if form == "fp64" else DF64_FLOPS_PER_CLK
+        peak = per_clk * 2070.0e6 / 1e12
+        src = ("nominal FP64 at 2070 MHz" if form == "fp64" else
+               "double-float flops at the FP32 pipe rate (9.4 FP32 instructions per flop), 2070 MHz")
         return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_src": "nominal FP64 at 2070 MHz",
-                "frac_at_sampled_clock": achieved / (FP64_FLOPS_PER_CLK * mhz * 1e6 / 1e12),
+                "frac": achieved / peak, "traffic": None, "peak_src": src,
+                "frac_at_sampled_clock": achieved / (per_clk * mhz * 1e6 / 1e12),
                 "ms_per_launch": ms_per_launch, "chains_per_launch": chains_per_launch}
     # complex64 half-spectrum buffer traffic: written once by pair_fwd, read and
     # written by pair_col, read once by pair_inv
@@ -321,6 +329,97 @@ def run_kpoints(args, peaks, peak_src):
                          "peak_src": peak_src + " (hbm copy)"}}
 
 
+def run_cufft_comparison(args, w, nbands=128, chunk=32):
+    """The same apply written with cuFFT (torch.fft) and torch element-wise ops,
+    timed on the first `nbands` bands of workload `w` in FP64 and in complex64:
+    a comparison line, not part of the library.  Real pair densities go through
+    R2C/C2R transforms; pairs (i, j >= i) are taken `chunk` at a time."""
+    import torch
+    from paper_1305_7313_gb300 import FockPlan, PREC_FP64
+    from paper_1305_7313_gb300.workloads import cubic_cell
+    n, L = w["N"], w["L"]
+    nb = min(nbands, w["nb"])
+    plan = FockPlan(n, cubic_cell(L), w["ecut"], w["kernel"], w["omega"], PREC_FP64)
+    cell, c, occ = make_inputs(dict(w, nb=w["nb"]), plan.miller)
+    c, occ = np.ascontiguousarray(c[:nb]), occ[:nb]
+    psi_dev = torch.from_numpy(c).cuda()
+    _, ex_fock, _ = plan.apply(psi_dev, occ, want_ex=True)
+    mill = plan.miller
+    plan.close()
+    vol = L ** 3
+    b = 2.0 * np.pi / L
+    m = np.fft.fftfreq(n, 1.0 / n)
+    mh = np.arange(n // 2 + 1)
+    g2 = b * b * (m[:, None, None] ** 2 + m[None, :, None] ** 2 + mh[None, None, :] ** 2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        if w["kernel"] == 0:
+            rc = (3.0 * vol / (4.0 * np.pi)) ** (1.0 / 3.0)
+            v = 8.0 * np.pi * np.sin(0.5 * np.sqrt(g2) * rc) ** 2 / g2
+            v[0, 0, 0] = 2.0 * np.pi * rc * rc
+        else:
+            om = w["omega"]
+            v = -4.0 * np.pi * np.expm1(-g2 / (4.0 * om * om)) / g2
+            v[0, 0, 0] = np.pi / (om * om)
+    wk3 = np.full(n // 2 + 1, 2.0)
+    wk3[0] = 1.0
+    if n % 2 == 0:
+        wk3[-1] = 1.0
+    flat = ((mill[:, 0] % n) * n + (mill[:, 1] % n)) * n + (mill[:, 2] % n)
+    idx = torch.from_numpy(flat.astype(np.int64)).cuda()
+    out = {}
+    for name, rdt, cdt in (("fp64", torch.float64, torch.complex128), ("mixed32", torch.float32, torch.complex64)):
+        vt = torch.from_numpy(v).to("cuda", rdt)
+        wt = torch.from_numpy(wk3).to("cuda", torch.float64)
+        f = torch.from_numpy(occ).to("cuda", rdt)
+        cg = psi_dev.to(cdt)
+
+        def apply():
+            x = torch.zeros(nb, n ** 3, dtype=cdt, device="cuda")
+            x[:, idx] = cg
+            psi = torch.fft.ifftn(x.view(nb, n, n, n), dim=(1, 2, 3)).real * (n ** 3 / vol ** 0.5)
+            wacc = torch.zeros_like(psi)
+            ex = torch.zeros((), dtype=torch.float64, device="cuda")
+            for i in range(nb):
+                for j0 in range(i, nb, chunk):
+                    j1 = min(nb, j0 + chunk)
+                    rho = psi[i] * psi[j0:j1]
+                    fr = torch.fft.rfftn(rho, dim=(1, 2, 3))
+                    e = ((fr.real.double() ** 2 + fr.imag.double() ** 2) * vt.double() * wt).sum(dim=(1, 2, 3))
+                    fj = f[j0:j1].double()
+                    mult = torch.full_like(fj, 2.0)
+                    if j0 == i:
+                        mult[0] = 1.0
+                    ex = ex + (-(vol / 2.0) / float(n) ** 6) * float(occ[i]) * (mult * fj * e).sum()
+                    phi = torch.fft.irfftn(fr * vt, s=(n, n, n), dim=(1, 2, 3))
+                    wacc[j0:j1] -= f[i] * psi[i] * phi
+                    s = (f[j0:j1, None, None, None] * psi[j0:j1] * phi)
+                    if j0 == i:
+                        s = s[1:]
+                    wacc[i] -= s.sum(0)
+            y = torch.fft.fftn(wacc, dim=(1, 2, 3)).reshape(nb, -1)[:, idx] * (vol ** 0.5 / n ** 3)
+            return y, ex
+
+        y, ex = apply()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        reps = 2
+        for _ in range(reps):
+            y, ex = apply()
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / reps
+        pairs = nb * (nb + 1) // 2
+        out[name] = {"value": pairs / (ms * 1e-3), "unit": UNIT, "ms_per_apply": ms,
+                     "rel_dEx_vs_fock_fp64": abs(float(ex) - ex_fock) / abs(ex_fock)}
+        del y, cg
+        torch.cuda.empty_cache()
+    out["sample"] = ("first %d bands of %s (%d pairs): torch.fft (cuFFT) R2C/C2R transforms, torch "
+                     "element-wise products, %d pairs per batch" % (nb, w["name"], nb * (nb + 1) // 2, chunk))
+    return out
+
+
 def cpu_baseline(w, nbands_sample=32):
     """The FP64 oracle on the first `nbands_sample` bands of the workload."""
     import oracle
@@ -373,6 +472,8 @@ def main():
     ap.add_argument("--workload", default="gamma_fp64_L27_N96_nb512")
     ap.add_argument("--mixed-workload", default="gamma_mixed32_erfc_L27_N96_nb512")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--df64-workload", default="gamma_df64_L27_N96_nb512")
+    ap.add_argument("--no-df64", action="store_true", help="skip the double-float form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-bands", type=int, default=32)
@@ -381,6 +482,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-kpoints", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison line")
+    ap.add_argument("--cufft-bands", type=int, default=128)
     ap.add_argument("--tune-bands", type=int, default=64,
                     help="band count of the subset the apply's pair-block parameters are tuned on")
     args = ap.parse_args()
@@ -417,7 +520,7 @@ def main():
     res = time_form(plan, psi, occ, args.steps, args.warmup, rank=rank, world=world)
     ms_step = res["ms"] / args.steps
     value = pairs * args.steps / (res["ms"] * 1e-3)
-    form = "fp64" if w["prec"] == PREC_FP64 else "mixed32"
+    form = {PREC_FP64: "fp64", PREC_MIXED32: "mixed32"}.get(w["prec"], "df64")
     roof = roofline(form, plan, res, args.steps, peaks, peak_src)
 
     # ---- end to end through the public API from pinned host memory
@@ -462,6 +565,29 @@ def main():
         del psim
         torch.cuda.empty_cache()
 
+    # ---- double-float form of the FP64 workload (FP64-class accuracy, FP32 pipe)
+    df = None
+    if not args.no_df64:
+        wd = workload(args.df64_workload)
+        if args.nb:
+            wd["nb"] = args.nb
+        pland = FockPlan(wd["N"], cubic_cell(wd["L"]), wd["ecut"], wd["kernel"], wd["omega"], wd["prec"])
+        _, cd, occd = make_inputs(wd, pland.miller)
+        tunedd = None
+        if not args.no_tune:
+            tunedd = tune_on_subset(pland, cd, occd, min(wd["nb"], args.tune_bands), reps=1)
+        psid = torch.from_numpy(cd).cuda()
+        resd = time_form(pland, psid, occd, args.steps, args.warmup, rank=rank, world=world)
+        pd = wd["nb"] * (wd["nb"] + 1) // 2
+        df = {"workload": wd["name"], "value": pd * args.steps / (resd["ms"] * 1e-3), "unit": UNIT,
+              "ms_per_step": resd["ms"] / args.steps, "dtype": "f32x2 (double-float)",
+              "roofline": roofline("df64", pland, resd, args.steps, peaks, peak_src),
+              "phase_ms_per_step": {k: v / args.steps for k, v in resd["phase_ms"].items()},
+              "gpu_launches": resd["launches"], "clocks": resd["clocks"], "tuned": tunedd}
+        pland.close()
+        del psid
+        torch.cuda.empty_cache()
+
     batched = None
     if not args.no_batched and world == 1:
         batched = run_batched(args, peaks, peak_src)
@@ -470,6 +596,11 @@ def main():
     kpoints = None
     if not args.no_kpoints and world == 1:
         kpoints = run_kpoints(args, peaks, peak_src)
+        torch.cuda.empty_cache()
+
+    cufft = None
+    if not args.no_cufft and world == 1:
+        cufft = run_cufft_comparison(args, w, args.cufft_bands)
         torch.cuda.empty_cache()
 
     if rank != 0:
@@ -481,13 +612,13 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "strong", "vs_baseline": None, "dtype": "f64" if form == "fp64" else "f32",
+        "scaling": "strong", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed32": "f32", "df64": "f32x2 (double-float)"}[form],
         "data": "synthetic",
         "config": {"workload": w["name"], "grid": n, "L_bohr": w["L"], "ecut_ha": w["ecut"],
                    "nbands": w["nb"], "pairs": pairs, "npw": plan.npw,
                    "kernel": "spencer_alavi" if w["kernel"] == 0 else "erfc",
                    "l2": "inputs larger than L2 (psi_G %.0f MB, real-space orbitals and accumulators "
-                         "%.1f GB each)" % (c.nbytes / 1e6, w["nb"] * n**3 * (8 if form == "fp64" else 4) / 1e9),
+                         "%.1f GB each)" % (c.nbytes / 1e6, w["nb"] * n**3 * (4 if form == "mixed32" else 8) / 1e9),
                    "parallelism": "pair-triangle shards + all-reduce" if world > 1 else "single GPU"},
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -497,8 +628,10 @@ def main():
         "phase_ms_per_step": {k: v / args.steps for k, v in res["phase_ms"].items()},
         "tuned": tuned,
         "mixed32": mixed,
+        "df64": df,
         "batched": batched,
         "kpoints": kpoints,
+        "cufft_comparison": cufft,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -68,7 +68,14 @@ typedef enum {
   FOCK_PREC_FP64 = 0,
   /* complex64 transforms and FP32 pair products / V_x psi accumulation; the
    * kernel terms of the smallest |G| (|m|^2 <= 3) and every energy sum in FP64. */
-  FOCK_PREC_MIXED32 = 1
+  FOCK_PREC_MIXED32 = 1,
+  /* Double-float: every real of the pair passes and the O(nb) transforms is
+   * the unevaluated sum of two floats (about 48 significant bits, float's
+   * exponent range), computed with error-free float transformations on the
+   * FP32 pipe; V_x psi accumulators, energies and the I/O stay FP64.  Same
+   * inputs, outputs and tolerance (1e-10 relative) as FOCK_PREC_FP64.  Gamma
+   * point only: batches and k-point plans refuse it (INVALID_ARG). */
+  FOCK_PREC_DF64 = 2
 } fock_precision;
 
 /* Orbitals are Gamma-point real functions: c(-G) = c(G)*.  Required. */

@@ -11,6 +11,7 @@ raises immediately.
 from ._lib import (  # noqa: F401
     ERFC,
     GAMMA_REAL,
+    PREC_DF64,
     PREC_FP64,
     PREC_MIXED32,
     SPENCER_ALAVI,

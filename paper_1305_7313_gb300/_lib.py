@@ -16,6 +16,7 @@ SPENCER_ALAVI = 0
 ERFC = 1
 PREC_FP64 = 0
 PREC_MIXED32 = 1
+PREC_DF64 = 2
 GAMMA_REAL = 1
 
 STATUS = {

@@ -72,6 +72,10 @@ def _jobs():
                          nv + ["-DFOCK_T=" + t, "-DFOCK_N=%d" % n, "-DFOCK_OPS_NAME=kOps_%s_%d" % (tag, n),
                                "-DFOCK_KOPS_NAME=kKOps_%s_%d" % (tag, n),
                                "-c", os.path.join(CSRC, "fock_kernels_inst.cu")]))
+        # double-float form: Gamma-point kernels only
+        jobs.append(("fock_df_%d.o" % n,
+                     nv + ["-DFOCK_T=fockx::df64", "-DFOCK_N=%d" % n, "-DFOCK_OPS_NAME=kOps_df_%d" % n,
+                           "-c", os.path.join(CSRC, "fock_kernels_inst.cu")]))
     return nvcc, jobs
 
 

@@ -30,6 +30,8 @@
 
 #include <cuda_runtime.h>
 
+#include "df64.cuh"
+
 namespace fockx {
 
 constexpr int kMaxStages = 8;
@@ -96,11 +98,11 @@ __host__ __device__ constexpr int cgcd(int a, int b) {
   return a;
 }
 
-__host__ __device__ constexpr int best_tl(int n, const int* r, int nst, int nlines, int maxt) {
+__host__ __device__ constexpr int best_tl(int n, const int* r, int nst, int nlines, int maxt, int emax) {
   int g = 0;
   for (int s = 0; s < nst; ++s) g = cgcd(g, n / r[s]);
   for (int t = g; t >= 1; --t)
-    if (g % t == 0 && n / t <= kEmax && (nlines * t + 31) / 32 * 32 <= maxt) return t;
+    if (g % t == 0 && n / t <= emax && (nlines * t + 31) / 32 * 32 <= maxt) return t;
   return 0;
 }
 
@@ -109,11 +111,11 @@ constexpr int kRadices[8] = {16, 12, 9, 8, 6, 4, 3, 2};
 // Depth-first search over radix multisets (in descending order) whose product
 // is n; keeps the plan with the fewest stages, then the most threads per line.
 __host__ __device__ constexpr void radix_search(int n, int rem, int first, RadixPlan& cur, RadixPlan& best,
-                                                int& best_score, int maxt) {
+                                                int& best_score, int maxt, int emax) {
   if (rem == 1) {
     RadixPlan p = cur;
-    p.tl_plane = best_tl(n, p.r, p.nst, n, maxt);
-    p.tl_colh = best_tl(n, p.r, p.nst, 2 * (n / 2 + 1), maxt);
+    p.tl_plane = best_tl(n, p.r, p.nst, n, maxt, emax);
+    p.tl_colh = best_tl(n, p.r, p.nst, 2 * (n / 2 + 1), maxt, emax);
     if (p.tl_plane == 0 || p.tl_colh == 0) return;
     const int score = p.nst * 4096 - p.tl_plane;
     if (score < best_score) {
@@ -127,7 +129,7 @@ __host__ __device__ constexpr void radix_search(int n, int rem, int first, Radix
     const int r = kRadices[k];
     if (rem % r != 0) continue;
     cur.r[cur.nst++] = r;
-    radix_search(n, rem / r, k, cur, best, best_score, maxt);
+    radix_search(n, rem / r, k, cur, best, best_score, maxt, emax);
     --cur.nst;
   }
 }
@@ -135,20 +137,38 @@ __host__ __device__ constexpr void radix_search(int n, int rem, int first, Radix
 // Fewest stages first, then the most threads per line, with CTAs of at most
 // maxt threads.  Radices 6, 9, 12 and 16 are done in registers as two small
 // DFTs, so a plan such as 96 = 12 x 8 needs two shared-memory stages.
-__host__ __device__ constexpr RadixPlan make_radix_plan(int n, int maxt = kMaxThreads) {
+__host__ __device__ constexpr RadixPlan make_radix_plan(int n, int maxt = kMaxThreads, int emax = kEmax) {
   RadixPlan best{};
   best.nst = 0;
   RadixPlan cur{};
   cur.nst = 0;
   int best_score = 1 << 30;
-  radix_search(n, n, 0, cur, best, best_score, maxt);
+  radix_search(n, n, 0, cur, best, best_score, maxt, emax);
   return best;
 }
+
+// Elements a thread may hold across a stage, per working type: double-float
+// values take twice the instructions and live registers of a float, so their
+// plans use more threads per line (e.g. 96 = 12 x 4 x 2 with 8 threads per
+// line instead of 12 x 8 with 4).
+template <class T> struct FftTraits { static constexpr int emax = kEmax; };
 
 template <class T> struct CplxOf;
 template <> struct CplxOf<float> { using type = float2; };
 template <> struct CplxOf<double> { using type = double2; };
+template <> struct CplxOf<df64> { using type = cdf64; };
+template <> struct FftTraits<df64> { static constexpr int emax = 12; };
 template <class T> using cplx = typename CplxOf<T>::type;
+
+// S * x for S = +1 or -1 (a sign flip, never a multiplication)
+template <int S, class T> __device__ __forceinline__ T sgn(T x) {
+  if constexpr (S > 0) return x;
+  else return -x;
+}
+// x / 2, exact
+__device__ __forceinline__ float half_of(float x) { return 0.5f * x; }
+__device__ __forceinline__ double half_of(double x) { return 0.5 * x; }
+__device__ __forceinline__ df64 half_of(df64 x) { return ldexp_pow2(x, 0.5f); }
 
 template <class T>
 __device__ __forceinline__ cplx<T> cmake(T x, T y) {
@@ -182,10 +202,11 @@ template <int SIGN, class T> struct Dft {
     x[1] = csub(a, x[1]);
   }
   static __device__ __forceinline__ void r3(C* x) {
-    const T h = T(SIGN) * T(0.86602540378443864676372317075293618);  // sin(2 pi / 3)
+    constexpr T h0 = T(0.86602540378443864676372317075293618);  // sin(2 pi / 3)
+    const T h = sgn<SIGN>(h0);
     C s = cadd(x[1], x[2]);
     C d = csub(x[1], x[2]);
-    C m = cmake<T>(x[0].x - T(0.5) * s.x, x[0].y - T(0.5) * s.y);
+    C m = cmake<T>(x[0].x - half_of(s.x), x[0].y - half_of(s.y));
     C u = cmake<T>(-h * d.y, h * d.x);
     x[0] = cadd(x[0], s);
     x[1] = cadd(m, u);
@@ -200,15 +221,15 @@ template <int SIGN, class T> struct Dft {
   }
   static __device__ __forceinline__ void r4(C* x) { r4v(x[0], x[1], x[2], x[3]); }
   static __device__ __forceinline__ void r8(C* x) {
-    const T c = T(0.70710678118654752440084436210484904);  // cos(pi / 4)
+    constexpr T c = T(0.70710678118654752440084436210484904);  // cos(pi / 4)
     C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
     C o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
     r4v(e0, e1, e2, e3);
     r4v(o0, o1, o2, o3);
     // o_q *= exp(SIGN 2 pi i q / 8)
-    C t1 = cmake<T>(c * (o1.x - T(SIGN) * o1.y), c * (o1.y + T(SIGN) * o1.x));
+    C t1 = cmake<T>(c * (o1.x - sgn<SIGN>(o1.y)), c * (o1.y + sgn<SIGN>(o1.x)));
     C t2 = cmul_si<SIGN>(o2);
-    C t3 = cmake<T>(-c * (o3.x + T(SIGN) * o3.y), c * (T(SIGN) * o3.x - o3.y));
+    C t3 = cmake<T>(-(c * (o3.x + sgn<SIGN>(o3.y))), c * (sgn<SIGN>(o3.x) - o3.y));
     x[0] = cadd(e0, o0);
     x[4] = csub(e0, o0);
     x[1] = cadd(e1, t1);
@@ -321,7 +342,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* base, int t, bool active, con
 
 template <class T, int N, int SIGN, int TL, int ES, int S, int P, int MAXT>
 __device__ __forceinline__ void fft_stages(cplx<T>* base, int t, bool active, const cplx<T>* tw) {
-  constexpr RadixPlan pl = make_radix_plan(N, MAXT);
+  constexpr RadixPlan pl = make_radix_plan(N, MAXT, FftTraits<T>::emax);
   if constexpr (S < pl.nst) {
     constexpr int R = pl.r[S];
     fft_stage<T, N, R, P, TL, ES, SIGN>(base, t, active, tw);
@@ -332,7 +353,8 @@ __device__ __forceinline__ void fft_stages(cplx<T>* base, int t, bool active, co
 // FFT of NLINES lines of length N in shared memory: line l starts at buf + l*LS,
 // its elements are ES apart.  Every thread of the CTA must call this (it
 // synchronises); threads with tid >= NLINES*TL idle.
-// MAXT names the radix plan (make_radix_plan(N, MAXT)) that TL was chosen for.
+// MAXT names the radix plan (make_radix_plan(N, MAXT, FftTraits<T>::emax)) that
+// TL was chosen for.
 template <class T, int N, int SIGN, int NLINES, int TL, int LS, int ES, int MAXT = kMaxThreads>
 __device__ __forceinline__ void fft_lines(cplx<T>* buf, const cplx<T>* tw) {
   const int tid = threadIdx.x;

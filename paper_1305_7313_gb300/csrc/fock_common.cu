@@ -8,6 +8,7 @@ namespace fockx {
 #define FOCK_DECLARE(N)                 \
   extern const KernelOps kOps_f64_##N; \
   extern const KernelOps kOps_f32_##N; \
+  extern const KernelOps kOps_df_##N;  \
   extern const KOps kKOps_f64_##N;     \
   extern const KOps kKOps_f32_##N;
 FOCK_GRID_SIZES(FOCK_DECLARE)
@@ -15,7 +16,7 @@ FOCK_GRID_SIZES(FOCK_DECLARE)
 
 const KernelOps* find_kernel_ops(int prec, int n) {
 #define FOCK_FIND(N) \
-  if (n == N) return prec == 0 ? &kOps_f64_##N : &kOps_f32_##N;
+  if (n == N) return prec == 0 ? &kOps_f64_##N : prec == 1 ? &kOps_f32_##N : prec == 2 ? &kOps_df_##N : nullptr;
   FOCK_GRID_SIZES(FOCK_FIND)
 #undef FOCK_FIND
   return nullptr;
@@ -23,7 +24,7 @@ const KernelOps* find_kernel_ops(int prec, int n) {
 
 const KOps* find_kops(int prec, int n) {
 #define FOCK_FINDK(N) \
-  if (n == N) return prec == 0 ? &kKOps_f64_##N : &kKOps_f32_##N;
+  if (n == N) return prec == 0 ? &kKOps_f64_##N : prec == 1 ? &kKOps_f32_##N : nullptr;
   FOCK_GRID_SIZES(FOCK_FINDK)
 #undef FOCK_FINDK
   return nullptr;

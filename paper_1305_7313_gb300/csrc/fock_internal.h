@@ -48,6 +48,7 @@ struct DevPlan {
 
 struct KernelOps {
   int real_bytes;  // sizeof of the working real type
+  int prec;        // 0 FP64, 1 mixed FP32, 2 double-float (fock_precision)
   int n;           // grid size these kernels are compiled for
   size_t smem;     // largest dynamic shared memory of its kernels
   cudaError_t (*configure)(const DevPlan&);

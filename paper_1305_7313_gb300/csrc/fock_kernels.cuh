@@ -1,9 +1,11 @@
 // fock_kernels.cuh — the CUDA kernels of the Gamma-point Fock apply, templated
-// on the working real type T (double: FP64 form; float: mixed form).
+// on the working real type T (double: FP64 form; float: mixed form; df64:
+// double-float form, FP64-class accuracy on the FP32 pipe).
 //
 // Data layout in HBM (all row-major, last index fastest):
 //   psi  [nb][N][N][N]  real T      orbitals in real space, psi(r) of §4
-//   W    [nb][N][N][N]  real T      accumulators of V_x psi_j(r)
+//   W    [nb][N][N][N]  real A      accumulators of V_x psi_j(r) (A = T, or
+//                                   double for df64)
 //   H    [chain][N][N][2][N/2+1]    complex T: per plane i1 and row k2, the
 //        stored half (k3 <= N/2) of the 2D transforms of the two pair densities
 //        of a chain (index 0: pair a, 1: pair b)
@@ -33,7 +35,30 @@ __device__ __forceinline__ int freq_of(int k, int n) { return k < (n + 1) / 2 ? 
 // memory in the pass prologues (memory-level parallelism).
 constexpr int kLoadUnroll = 4;
 
+// Per working type: the precision code of the plan (0 FP64, 1 mixed FP32,
+// 2 double-float) and the type of the accumulators W.
+template <class T> struct RealTraits;
+template <> struct RealTraits<double> { static constexpr int prec = 0; using acc = double; };
+template <> struct RealTraits<float> { static constexpr int prec = 1; using acc = float; };
+template <> struct RealTraits<df64> { static constexpr int prec = 2; using acc = double; };
+template <class T> using acc_t = typename RealTraits<T>::acc;
+
+// Load through L2 only (ld.global.cg) of one complex value.
+template <class C> __device__ __forceinline__ C ldcg_c(const C* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ cdf64 ldcg_c<cdf64>(const cdf64* p) {
+  const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+  cdf64 r;
+  r.x = df64(v.x, v.y);
+  r.y = df64(v.z, v.w);
+  return r;
+}
+
 template <class T> __device__ __forceinline__ void atomic_add_real(T* p, T v) { atomicAdd(p, v); }
+// df64 into an FP64 accumulator: both parts become doubles by integer
+// instructions, one FP64 add joins them (exact to the rounding of that add).
+__device__ __forceinline__ void atomic_add_real(double* p, df64 v) {
+  atomicAdd(p, float_bits_to_double(v.hi) + float_bits_to_double(v.lo));
+}
 
 // Sum of four doubles over the CTA; the result is valid in thread 0.
 __device__ inline void block_sum4(double v[4], double* red) {
@@ -61,7 +86,7 @@ __device__ inline void block_sum4(double v[4], double* red) {
 template <class T, int N, int MAXT = kMaxThreads>
 struct Geo {
   using C = cplx<T>;
-  static constexpr RadixPlan pl = make_radix_plan(N, MAXT);
+  static constexpr RadixPlan pl = make_radix_plan(N, MAXT, FftTraits<T>::emax);
   static_assert(pl.nst > 0, "grid size must be 2^a 3^b and fit the FFT kernels");
   static constexpr int KH = N / 2 + 1;                    // stored half of the last axis
   static constexpr int NC = 2 * KH;                       // stored columns per row (A and B)
@@ -174,6 +199,14 @@ __device__ __forceinline__ void load_twiddles(cplx<T>* tw, const DevPlan& g) {
   for (int t = threadIdx.x; t < g.n; t += blockDim.x) tw[t] = src[t];
 }
 
+// 2D FFT of a plane held with row stride RP: along the last axis, then the
+// middle one.
+template <class T, int N, int SIGN, int TLP, int RP, int MAXT>
+__device__ __forceinline__ void fft_plane(cplx<T>* P, const cplx<T>* tw) {
+  fft_lines<T, N, SIGN, N, TLP, RP, 1, MAXT>(P, tw);
+  fft_lines<T, N, SIGN, N, TLP, 1, RP, MAXT>(P, tw);
+}
+
 // ---------------------------------------------------------------- O(nb) passes
 
 // X[q] = scatter(c_{b0} + i c_{b0+1}) for band pairs q of the batch (X zeroed before).
@@ -218,7 +251,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_COLF) k_col_full(DevPlan g, cpl
 // EPI 0: store to X; EPI 1: psi_b0 = Re z * psi_scale, psi_b0+1 = Im z * psi_scale.
 template <class T, int N, int SIGN, int PRO, int EPI>
 __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
-    k_plane_full(DevPlan g, cplx<T>* __restrict__ X, const T* __restrict__ W, T* __restrict__ psi,
+    k_plane_full(DevPlan g, cplx<T>* __restrict__ X, const acc_t<T>* __restrict__ W, T* __restrict__ psi,
                  int band0, int nb, int nbat) {
   using C = cplx<T>;
   using G = Geo<T, N>;
@@ -238,8 +271,8 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
     if (PRO == 0) {
       z = Xq[e];
     } else {
-      z.x = W[(int64_t)b0 * g.ntot + plane0 + e];
-      z.y = has1 ? W[(int64_t)(b0 + 1) * g.ntot + plane0 + e] : T(0);
+      z.x = T(W[(int64_t)b0 * g.ntot + plane0 + e]);
+      z.y = has1 ? T(W[(int64_t)(b0 + 1) * g.ntot + plane0 + e]) : T(0);
     }
     P[i2 * RP + i3] = z;
   }
@@ -271,7 +304,7 @@ __global__ void k_gather(DevPlan g, const cplx<T>* __restrict__ X, int nb, int b
   const double s = 0.5 * g.out_scale;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < g.npw; k += gridDim.x * blockDim.x) {
     const cplx<T> y = Xq[g.gidx[k]], ym = Xq[g.gidxneg[k]];
-    const double yx = y.x, yy = y.y, mx = ym.x, my = ym.y;
+    const double yx = to_double(y.x), yy = to_double(y.y), mx = to_double(ym.x), my = to_double(ym.y);
     vpsiG[(int64_t)b0 * g.npw + k] = make_double2(s * (yx + mx), s * (yy - my));
     if (has1) vpsiG[(int64_t)(b0 + 1) * g.npw + k] = make_double2(s * (yy + my), s * (mx - yx));
   }
@@ -318,16 +351,14 @@ __device__ __forceinline__ void pair_fwd_task(const DevPlan& g, const T* __restr
     }
   }
   __syncthreads();
-  fft_lines<T, N, -1, N, G::TLP, RP, 1, MAXT>(P, tw);  // along i3
-  fft_lines<T, N, -1, N, G::TLP, 1, RP, MAXT>(P, tw);  // along i2
+  fft_plane<T, N, -1, G::TLP, RP, MAXT>(P, tw);  // along i3, then i2
   C* Hp = Hc + (int64_t)i1 * N * NC;
   for (int e = threadIdx.x; e < N * KH; e += blockDim.x) {
     const int k2 = e / KH, k3 = e - k2 * KH;
     const int m2 = k2 == 0 ? 0 : N - k2, m3 = k3 == 0 ? 0 : N - k3;
     const C z = P[k2 * RP + k3], zm = P[m2 * RP + m3];
-    const T h = T(0.5);
-    Hp[k2 * NC + k3] = cmake<T>(h * (z.x + zm.x), h * (z.y - zm.y));
-    Hp[k2 * NC + KH + k3] = cmake<T>(h * (z.y + zm.y), h * (zm.x - z.x));
+    Hp[k2 * NC + k3] = cmake<T>(half_of(z.x + zm.x), half_of(z.y - zm.y));
+    Hp[k2 * NC + KH + k3] = cmake<T>(half_of(z.y + zm.y), half_of(zm.x - z.x));
   }
 }
 
@@ -340,12 +371,91 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
   pair_fwd_task<T, N, kMaxThreads>(g, psi, ch, H + (int64_t)blockIdx.y * g.hsize, blockIdx.x, smem_raw);
 }
 
-// One task of the column pass: row k2 of chain `ch` (transform buffer Hc).
-// Shared memory: Geo::SMEM_COLH bytes at smem_raw.
+// The column pass in double-float arithmetic: the df64 tables of v / Ntot and
+// dv/domega, per-thread double-float energy sums that are reduced (in FP64)
+// before the inverse transform, so they hold no registers across it.
+template <int N, int MAXT>
+__device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __restrict__ Hc, const Chain& ch,
+                                                 int k2, double* __restrict__ epair, double* __restrict__ dpair,
+                                                 unsigned char* smem_raw) {
+  using C = cdf64;
+  using G = Geo<df64, N, MAXT>;
+  constexpr int KH = G::KH, NC = G::NC;
+  C* S = reinterpret_cast<C*>(smem_raw);
+  C* tw = S + N * NC;
+  double* red = reinterpret_cast<double*>(tw + N);
+  load_twiddles<df64>(tw, g);
+  for (int e0 = threadIdx.x; e0 < N * NC; e0 += kLoadUnroll * blockDim.x) {
+    C v[kLoadUnroll];
+#pragma unroll
+    for (int u = 0; u < kLoadUnroll; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < N * NC) {
+        const int i1 = e / NC, c = e - i1 * NC;
+        v[u] = ldcg_c(Hc + ((int64_t)i1 * N + k2) * NC + c);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadUnroll; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < N * NC) S[e] = v[u];
+    }
+  }
+  __syncthreads();
+  const bool want_d = g.dvtab64 != nullptr;
+  const df64* vt = static_cast<const df64*>(g.vtab);    // v / Ntot
+  const df64* dvt = static_cast<const df64*>(g.dvtab);  // dv/domega
+  fft_lines<df64, N, -1, NC, G::TLC, 1, NC, MAXT>(S, tw);  // along i1
+  {
+    df64 accd[4] = {df64(0.f), df64(0.f), df64(0.f), df64(0.f)};
+    for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
+      const int k1 = e / NC, c = e - k1 * NC;
+      const int s = c >= KH ? 1 : 0;
+      const int k3 = c - s * KH;
+      const int vi = (k1 * N + k2) * KH + k3;
+      const bool twice = !(k3 == 0 || 2 * k3 == N);
+      C z = S[e];
+      const df64 a2 = z.x * z.x + z.y * z.y;
+      const df64 v = vt[vi];
+      df64 te = v * a2;
+      if (twice) te = ldexp_pow2(te, 2.0f);
+      if (s) accd[1] += te;
+      else accd[0] += te;
+      if (want_d) {
+        df64 td = dvt[vi] * a2;
+        if (twice) td = ldexp_pow2(td, 2.0f);
+        if (s) accd[3] += td;
+        else accd[2] += td;
+      }
+      z.x *= v;
+      z.y *= v;
+      S[e] = z;
+    }
+    const double ntot = double(g.ntot);  // the energy table holds v / Ntot
+    double acc[4] = {to_double(accd[0]) * ntot, to_double(accd[1]) * ntot, to_double(accd[2]),
+                     to_double(accd[3])};
+    block_sum4(acc, red);  // synchronises the CTA
+    if (threadIdx.x == 0) {
+      if (ch.pa >= 0) atomicAdd(&epair[ch.pa], acc[0]);
+      if (ch.pb >= 0) atomicAdd(&epair[ch.pb], acc[1]);
+      if (want_d) {
+        if (ch.pa >= 0) atomicAdd(&dpair[ch.pa], acc[2]);
+        if (ch.pb >= 0) atomicAdd(&dpair[ch.pb], acc[3]);
+      }
+    }
+  }
+  fft_lines<df64, N, +1, NC, G::TLC, 1, NC, MAXT>(S, tw);  // inverse along k1
+  for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
+    const int i1 = e / NC, c = e - i1 * NC;
+    Hc[((int64_t)i1 * N + k2) * NC + c] = S[e];
+  }
+}
+
+// The column pass in FP64 or in the mixed form.
 template <class T, int N, int MAXT>
-__device__ __forceinline__ void pair_col_task(const DevPlan& g, cplx<T>* __restrict__ Hc,
-                                              const Chain& ch, int k2, double* __restrict__ epair,
-                                              double* __restrict__ dpair, unsigned char* smem_raw) {
+__device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __restrict__ Hc,
+                                                  const Chain& ch, int k2, double* __restrict__ epair,
+                                                  double* __restrict__ dpair, unsigned char* smem_raw) {
   using C = cplx<T>;
   using G = Geo<T, N, MAXT>;
   constexpr int KH = G::KH, NC = G::NC;
@@ -360,7 +470,7 @@ __device__ __forceinline__ void pair_col_task(const DevPlan& g, cplx<T>* __restr
       const int e = e0 + u * blockDim.x;
       if (e < N * NC) {
         const int i1 = e / NC, c = e - i1 * NC;
-        v[u] = __ldcg(Hc + ((int64_t)i1 * N + k2) * NC + c);
+        v[u] = ldcg_c(Hc + ((int64_t)i1 * N + k2) * NC + c);
       }
     }
 #pragma unroll
@@ -377,7 +487,7 @@ __device__ __forceinline__ void pair_col_task(const DevPlan& g, cplx<T>* __restr
   const int m2 = freq_of(k2, N);
   double acc[4] = {0.0, 0.0, 0.0, 0.0};  // e_a, e_b, d_a, d_b (FP64 terms)
   float acc_f32[4] = {0.f, 0.f, 0.f, 0.f};  // the same from the FP32 terms (mixed form)
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (RealTraits<T>::prec == 0) {
     for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
       const int k1 = e / NC, c = e - k1 * NC;
       const int s = c >= KH ? 1 : 0;
@@ -445,7 +555,7 @@ __device__ __forceinline__ void pair_col_task(const DevPlan& g, cplx<T>* __restr
     const int i1 = e / NC, c = e - i1 * NC;
     Hc[((int64_t)i1 * N + k2) * NC + c] = S[e];
   }
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (RealTraits<T>::prec != 1) {
     block_sum4(acc, red);
   } else {
     float hi[4], lo[4];
@@ -465,6 +575,19 @@ __device__ __forceinline__ void pair_col_task(const DevPlan& g, cplx<T>* __restr
   }
 }
 
+// One task of the column pass: row k2 of chain `ch` (transform buffer Hc).
+// Shared memory: Geo::SMEM_COLH bytes at smem_raw.
+template <class T, int N, int MAXT>
+__device__ __forceinline__ void pair_col_task(const DevPlan& g, cplx<T>* __restrict__ Hc,
+                                              const Chain& ch, int k2, double* __restrict__ epair,
+                                              double* __restrict__ dpair, unsigned char* smem_raw) {
+  if constexpr (RealTraits<T>::prec == 2) {
+    pair_col_task_df<N, MAXT>(g, Hc, ch, k2, epair, dpair, smem_raw);
+  } else {
+    pair_col_task_std<T, N, MAXT>(g, Hc, ch, k2, epair, dpair, smem_raw);
+  }
+}
+
 template <class T, int N>
 __global__ void __launch_bounds__(Geo<T, N>::THR_COLH, Geo<T, N>::MIN_CTAS)
     k_pair_col(DevPlan g, cplx<T>* __restrict__ H, const Chain* __restrict__ chains,
@@ -479,7 +602,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_COLH, Geo<T, N>::MIN_CTAS)
 // Hc), accumulating into W.  Shared memory: Geo::SMEM_PLANE bytes at smem_raw.
 template <class T, int N, int MAXT>
 __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restrict__ psi,
-                                              T* __restrict__ W, const T* __restrict__ occ,
+                                              acc_t<T>* __restrict__ W, const T* __restrict__ occ,
                                               const Chain& ch, const cplx<T>* __restrict__ Hc, int i1,
                                               unsigned char* smem_raw) {
   using C = cplx<T>;
@@ -499,8 +622,8 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
         // k3 > N/2 is the mirror image of the stored half: A(-k) = A(k)*
         const bool lo = k3 < KH;
         const int r = lo ? k2 : (k2 == 0 ? 0 : N - k2), c = lo ? k3 : N - k3;
-        a[u] = __ldcg(Hp + r * NC + c);
-        b[u] = __ldcg(Hp + r * NC + KH + c);
+        a[u] = ldcg_c(Hp + r * NC + c);
+        b[u] = ldcg_c(Hp + r * NC + KH + c);
         if (!lo) {
           a[u].y = -a[u].y;
           b[u].y = -b[u].y;
@@ -517,8 +640,7 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
     }
   }
   __syncthreads();
-  fft_lines<T, N, +1, N, G::TLP, 1, RP, MAXT>(P, tw);  // along k2
-  fft_lines<T, N, +1, N, G::TLP, RP, 1, MAXT>(P, tw);  // along k3
+  fft_plane<T, N, +1, G::TLP, RP, MAXT>(P, tw);  // along k3, then k2
   const int64_t plane0 = (int64_t)i1 * N * N;
   const bool hb = ch.bi >= 0;
   // Up to four updates k, W[tgt_k] -= f[src_k] psi[src_k] phi:
@@ -537,13 +659,13 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
     for (int m = 0; m < k; ++m)
       if (into[k] == k && tgt[k] >= 0 && tgt[m] == tgt[k]) into[k] = m;
   const T* ps[4];
-  T* wt[4];
+  acc_t<T>* wt[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     ps[k] = psi + (int64_t)src[k] * g.ntot + plane0;
     wt[k] = W + (int64_t)(tgt[k] >= 0 ? tgt[k] : 0) * g.ntot + plane0;
   }
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (RealTraits<T>::prec == 1) {
     static_assert(N % 4 == 0, "vector updates need N divisible by 4");
     for (int e4 = threadIdx.x; e4 < N * N / 4; e4 += blockDim.x) {
       const int e = 4 * e4;
@@ -606,7 +728,7 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
 
 template <class T, int N>
 __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
-    k_pair_inv(DevPlan g, const T* __restrict__ psi, T* __restrict__ W, const T* __restrict__ occ,
+    k_pair_inv(DevPlan g, const T* __restrict__ psi, acc_t<T>* __restrict__ W, const T* __restrict__ occ,
                const Chain* __restrict__ chains, const cplx<T>* __restrict__ H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Chain ch = chains[blockIdx.y];
@@ -665,7 +787,7 @@ struct Launch {
   static cudaError_t pair_inv(const DevPlan& g, const void* psi, void* W, const void* occ,
                               const Chain* ch, int nch, const void* H, cudaStream_t s) {
     k_pair_inv<T, N><<<dim3(N, nch), G::THR_PLANE, G::SMEM_PLANE, s>>>(
-        g, static_cast<const T*>(psi), static_cast<T*>(W), static_cast<const T*>(occ), ch,
+        g, static_cast<const T*>(psi), static_cast<acc_t<T>*>(W), static_cast<const T*>(occ), ch,
         static_cast<const C*>(H));
     return cudaGetLastError();
   }
@@ -675,14 +797,15 @@ struct Launch {
     C* X = static_cast<C*>(Xv);
     const int nq = (nbat + 1) / 2;
     k_plane_full<T, N, -1, 1, 0><<<dim3(N, nq), G::THR_PLANE, G::SMEM_PLANE, s>>>(
-        g, X, static_cast<const T*>(W), nullptr, band0, nb, nbat);
+        g, X, static_cast<const acc_t<T>*>(W), nullptr, band0, nb, nbat);
     k_col_full<T, N, -1><<<dim3(N, nq), G::THR_COLF, G::SMEM_COLF, s>>>(g, X);
     k_gather<T><<<dim3((g.npw + 255) / 256, nq), 256, 0, s>>>(g, X, nb, band0, nbat, vpsiG);
     return cudaGetLastError();
   }
 
   static constexpr KernelOps ops() {
-    return KernelOps{(int)sizeof(T), N, G::SMEM_COLH > G::SMEM_PLANE ? G::SMEM_COLH : G::SMEM_PLANE,
+    return KernelOps{(int)sizeof(T), RealTraits<T>::prec, N,
+                     G::SMEM_COLH > G::SMEM_PLANE ? G::SMEM_COLH : G::SMEM_PLANE,
                      configure, to_real, pair_fwd, pair_col, pair_inv, to_sphere};
   }
 };

@@ -155,7 +155,7 @@ fock_status fock_kplan_create(fock_kplan_t* out, const int grid[3], const double
   if (!grid || !cell || !kpts || !wk || nk < 1 || nk > 4096)
     return kfail(nullptr, FOCK_ERR_INVALID_ARG, "NULL argument or nk out of range");
   if (prec != FOCK_PREC_FP64 && prec != FOCK_PREC_MIXED32)
-    return kfail(nullptr, FOCK_ERR_INVALID_ARG, "unknown precision");
+    return kfail(nullptr, FOCK_ERR_INVALID_ARG, "k-point plans run the FP64 and mixed forms only");
   if (kind != FOCK_KERNEL_SPENCER_ALAVI && kind != FOCK_KERNEL_ERFC)
     return kfail(nullptr, FOCK_ERR_INVALID_ARG, "unknown kernel kind");
   if (!(ecut_ha > 0.0) || !std::isfinite(ecut_ha)) return kfail(nullptr, FOCK_ERR_INVALID_ARG, "bad ecut");

@@ -28,6 +28,13 @@ constexpr int kBandBlock = 16;                  // default bands per block of th
 constexpr size_t kChainBufferBytes = 120u << 20;  // default size of the pair-transform buffer
 constexpr int kMsmall2 = 3;                     // |m|^2 of the kernel terms kept in FP64 (mixed)
 
+// d as the double-float pair (hi, lo): hi = float(d), lo = float(d - hi).
+void split_df64(double d, float* out) {
+  const float hi = (float)d;
+  out[0] = hi;
+  out[1] = (float)(d - (double)hi);
+}
+
 thread_local std::string g_create_error;
 
 using fockx::lattice::GEntry;
@@ -342,8 +349,13 @@ fock_status grow_keeping(fock_plan* p, int nb, int keep) {
 fock_status upload_occ(fock_plan* p, const double* occ, int nb, cudaStream_t s) {
   p->occ_host.assign(occ, occ + nb);
   FOCK_CUDA(p, cudaMemcpyAsync(p->ws.occ, occ, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
-  if (p->ops->real_bytes == 8) {
+  if (p->prec == FOCK_PREC_FP64) {
     FOCK_CUDA(p, cudaMemcpyAsync(p->ws.occT, occ, sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+  } else if (p->prec == FOCK_PREC_DF64) {
+    std::vector<float> f(2 * (size_t)nb);
+    for (int k = 0; k < nb; ++k) split_df64(occ[k], &f[2 * k]);
+    FOCK_CUDA(p, cudaMemcpyAsync(p->ws.occT, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice, s));
+    FOCK_CUDA(p, cudaStreamSynchronize(s));  // f is a local buffer
   } else {
     std::vector<float> f(occ, occ + nb);
     FOCK_CUDA(p, cudaMemcpyAsync(p->ws.occT, f.data(), sizeof(float) * nb, cudaMemcpyHostToDevice, s));
@@ -525,7 +537,7 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
   if (!(flags & FOCK_GAMMA_REAL))
     return fail(nullptr, FOCK_ERR_INVALID_ARG, "FOCK_GAMMA_REAL is required");
   if (flags & ~FOCK_GAMMA_REAL) return fail(nullptr, FOCK_ERR_INVALID_ARG, "unknown flag bits");
-  if (prec != FOCK_PREC_FP64 && prec != FOCK_PREC_MIXED32)
+  if (prec != FOCK_PREC_FP64 && prec != FOCK_PREC_MIXED32 && prec != FOCK_PREC_DF64)
     return fail(nullptr, FOCK_ERR_INVALID_ARG, "unknown precision");
   if (kind != FOCK_KERNEL_SPENCER_ALAVI && kind != FOCK_KERNEL_ERFC)
     return fail(nullptr, FOCK_ERR_INVALID_ARG, "unknown kernel kind");
@@ -543,7 +555,7 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
     return fail(nullptr, FOCK_ERR_UNSUPPORTED_SIZE, "the FFT grid must be cubic (N1 = N2 = N3)");
   const int n = grid[0];
   if (n < 2 || !supported_n(n)) return fail(nullptr, FOCK_ERR_UNSUPPORTED_SIZE, "N must be 2^a 3^b");
-  const KernelOps* ops = fockx::find_kernel_ops(prec == FOCK_PREC_FP64 ? 0 : 1, n);
+  const KernelOps* ops = fockx::find_kernel_ops((int)prec, n);
   if (!ops) {
     return fail(nullptr, FOCK_ERR_UNSUPPORTED_SIZE,
                 "no kernels compiled for N = " + std::to_string(n));
@@ -598,7 +610,7 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
         const int64_t i = ((int64_t)k1 * n + k2) * kh + k3;
         kernel_value(p, g2, &v64[i], &dv64[i]);
       }
-  const bool fp64 = ops->real_bytes == 8;
+  const bool fp64 = prec == FOCK_PREC_FP64;
   // twiddles w[t] = exp(-2 pi i t / N)
   std::vector<double> tw64(2 * n);
   for (int t = 0; t < n; ++t) {
@@ -633,6 +645,18 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
       for (int64_t i = 0; i < nhalf; ++i) vs[i] = v64[i] / (double)ntot;
       ok = upload(&p->d_vtab, vs.data(), sizeof(double) * nhalf) &&
            upload(&p->d_tw, tw64.data(), sizeof(double) * tw64.size());
+    } else if (prec == FOCK_PREC_DF64) {
+      // (hi, lo) float pairs: v / Ntot, dv/domega and the twiddles
+      std::vector<float> vs(2 * nhalf), tw2(4 * n);
+      for (int64_t i = 0; i < nhalf; ++i) split_df64(v64[i] / (double)ntot, &vs[2 * i]);
+      for (int t = 0; t < 2 * n; ++t) split_df64(tw64[t], &tw2[2 * t]);
+      ok = upload(&p->d_vtab, vs.data(), sizeof(float) * vs.size()) &&
+           upload(&p->d_tw, tw2.data(), sizeof(float) * tw2.size());
+      if (ok && kind == FOCK_KERNEL_ERFC) {
+        std::vector<float> dvs(2 * nhalf);
+        for (int64_t i = 0; i < nhalf; ++i) split_df64(dv64[i], &dvs[2 * i]);
+        ok = upload(&p->d_dvtab, dvs.data(), sizeof(float) * dvs.size());
+      }
     } else {
       std::vector<float> vs(nhalf), tw32(2 * n);
       for (int64_t i = 0; i < nhalf; ++i) vs[i] = (float)(v64[i] / (double)ntot);
@@ -674,7 +698,7 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
   d.inv_ntot = 1.0 / (double)ntot;
   d.psi_scale = 1.0 / std::sqrt(p->vol);
   d.out_scale = std::sqrt(p->vol) / (double)ntot;
-  d.msmall2 = fp64 ? -1 : kMsmall2;
+  d.msmall2 = prec == FOCK_PREC_MIXED32 ? kMsmall2 : -1;
 
   const size_t chain_bytes = (size_t)d.hsize * 2 * (size_t)ops->real_bytes;
   p->chain_batch = (int)std::max<size_t>(1, kChainBufferBytes / chain_bytes);
@@ -1200,6 +1224,8 @@ fock_status fock_batch_create(fock_batch_t* out, int nsys, const fock_plan_t* pl
     if (!fockx::persist_supports(plans[k]->n))
       return bfail(nullptr, FOCK_ERR_UNSUPPORTED_SIZE, "batched grids must be 24, 32, 48, 64, 72 or 96");
   }
+  if (plans[0]->prec == FOCK_PREC_DF64)
+    return bfail(nullptr, FOCK_ERR_INVALID_ARG, "batches run the FP64 and mixed forms only");
   fock_batch* b = new (std::nothrow) fock_batch();
   if (!b) return bfail(nullptr, FOCK_ERR_OOM, "host allocation failed");
   b->nsys = nsys;

@@ -9,7 +9,7 @@ class FockPlan:
     """A plane-wave cell on an N^3 grid with one Coulomb kernel and precision.
 
     ``kernel``: ``SPENCER_ALAVI`` or ``ERFC`` (then ``omega`` in bohr^-1);
-    ``precision``: ``PREC_FP64`` or ``PREC_MIXED32``.
+    ``precision``: ``PREC_FP64``, ``PREC_MIXED32`` or ``PREC_DF64`` (double-float).
     """
 
     def __init__(self, grid, cell, ecut, kernel=_lib.SPENCER_ALAVI, omega=None,

@@ -12,6 +12,7 @@ SPENCER_ALAVI = 0
 ERFC = 1
 PREC_FP64 = 0
 PREC_MIXED32 = 1
+PREC_DF64 = 2
 
 
 def cubic_cell(length):
@@ -25,7 +26,10 @@ WORKLOADS = {
     # large cell: 96^3 grid, 512 bands, all 131,328 pairs, FP64
     "gamma_fp64_L27_N96_nb512": dict(L=27.0, N=96, ecut=12.0, nb=512, kernel=SPENCER_ALAVI,
                                      omega=None, prec=PREC_FP64, seed=1306),
-    # the same orbitals in complex64 transforms with FP64 energy sums, erfc kernel
+    # the FP64 workload in double-float arithmetic (FP64-class accuracy on the FP32 pipe)
+    "gamma_df64_L27_N96_nb512": dict(L=27.0, N=96, ecut=12.0, nb=512, kernel=SPENCER_ALAVI,
+                                     omega=None, prec=PREC_DF64, seed=1306),
+    # complex64 transforms with FP64 energy sums, erfc kernel
     "gamma_mixed32_erfc_L27_N96_nb512": dict(L=27.0, N=96, ecut=12.0, nb=512, kernel=ERFC,
                                              omega=0.106, prec=PREC_MIXED32, seed=1307),
     # differentiation: 72^3 grid, L = 20, 256 bands, erfc kernel

@@ -1,8 +1,10 @@
 """GPU path (through the C ABI) against the FP64 oracle, element by element.
 
 Tolerances:
-* FP64 form: 1e-10 relative (max |diff| / max |oracle|) on V_x psi and on E_x,
-  the target of the FP64 path.
+* FP64 form and double-float form (FP64-class: ~48-bit significands, unit
+  roundoff 2^-48 ~ 3.6e-15, so a transform chain of O(log Ntot) steps stays
+  near 1e-13): 1e-10 relative (max |diff| / max |oracle|) on V_x psi and on
+  E_x, the target of the FP64 path.
 * mixed form (complex64 transforms): a transform of length Ntot in FP32 carries
   a relative error of a few u * log2(Ntot) with u = 2^-24 = 6e-8 and
   log2(Ntot) ~ 17-20, i.e. ~1e-6 RMS; the pair potential goes through two of
@@ -23,6 +25,7 @@ from tests._common import cubic, rel_inf, require_gpu
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-10
+FP64_FORMS = pytest.mark.parametrize("prec", [_lib.PREC_FP64, _lib.PREC_DF64], ids=["fp64", "df64"])
 TOL32_V = 2e-5
 TOL32_E = 5e-6
 
@@ -46,21 +49,23 @@ def oracle_of(case):
                              case["kind"], case["omega"])
 
 
-def test_small_fp64_matches_oracle():
+@FP64_FORMS
+def test_small_fp64_matches_oracle(prec):
     # 24^3 grid, L = 10, Ecut = 10 Ha, 8 bands, f = 2, Spencer-Alavi
-    case = setup_case(24, 10.0, 10.0, 8, 1305)
+    case = setup_case(24, 10.0, 10.0, 8, 1305, prec=prec)
     vpsi, ex, _ = case["plan"].apply(case["psi"], case["occ"])
     vref, eref, _ = oracle_of(case)
     assert rel_inf(vpsi.cpu().numpy(), vref) <= TOL64
     assert abs(ex - eref) <= TOL64 * abs(eref)
 
 
-def test_fp64_many_batches_ragged_tails_uneven_occupations():
+@FP64_FORMS
+def test_fp64_many_batches_ragged_tails_uneven_occupations(prec):
     # 48^3 grid, 37 bands (odd: a lone last pair and a lone last band), chains in
     # batches of 5 so both the pair loop and the band transforms have ragged tails
     occ = np.linspace(2.0, 0.0, 37)
     occ[5] = -0.5
-    case = setup_case(48, 13.5, 12.0, 37, 77, occ=occ)
+    case = setup_case(48, 13.5, 12.0, 37, 77, occ=occ, prec=prec)
     case["plan"].set_batch(5)
     vpsi, ex, _ = case["plan"].apply(case["psi"], case["occ"])
     vref, eref, _ = oracle_of(case)
@@ -68,10 +73,11 @@ def test_fp64_many_batches_ragged_tails_uneven_occupations():
     assert abs(ex - eref) <= TOL64 * abs(eref)
 
 
-def test_fp64_erfc_energy_derivative_and_general_cell():
+@FP64_FORMS
+def test_fp64_erfc_energy_derivative_and_general_cell(prec):
     cell = np.array([[9.0, 0.4, 0.0], [0.3, 9.5, 0.2], [0.0, -0.3, 8.5]])
     case = setup_case(32, None, 8.0, 6, 5, kind=_lib.ERFC, omega=0.3, cell=cell,
-                      occ=[2.0, 2.0, 1.5, 1.0, 0.5, 0.25])
+                      occ=[2.0, 2.0, 1.5, 1.0, 0.5, 0.25], prec=prec)
     vpsi, ex, dex = case["plan"].apply(case["psi"], case["occ"], want_dex=True)
     vref, eref, dref = oracle_of(case)
     assert rel_inf(vpsi.cpu().numpy(), vref) <= TOL64
@@ -79,18 +85,20 @@ def test_fp64_erfc_energy_derivative_and_general_cell():
     assert abs(dex - dref) <= TOL64 * abs(dref)
 
 
-def test_single_band_and_two_bands():
+@FP64_FORMS
+def test_single_band_and_two_bands(prec):
     for nb in (1, 2, 3):
-        case = setup_case(24, 10.0, 10.0, nb, 40 + nb)
+        case = setup_case(24, 10.0, 10.0, nb, 40 + nb, prec=prec)
         vpsi, ex, _ = case["plan"].apply(case["psi"], case["occ"])
         vref, eref, _ = oracle_of(case)
         assert rel_inf(vpsi.cpu().numpy(), vref) <= TOL64
         assert abs(ex - eref) <= TOL64 * abs(eref)
 
 
-def test_shards_sum_to_the_full_apply():
+@FP64_FORMS
+def test_shards_sum_to_the_full_apply(prec):
     # the band-group split of the paper's EXX loop: partial results add up
-    case = setup_case(24, 10.0, 10.0, 11, 9)
+    case = setup_case(24, 10.0, 10.0, 11, 9, prec=prec)
     vfull, efull, _ = case["plan"].apply(case["psi"], case["occ"])
     vsum = 0.0
     esum = 0.0
@@ -102,8 +110,9 @@ def test_shards_sum_to_the_full_apply():
     assert abs(esum - efull) <= 1e-13 * abs(efull)
 
 
-def test_pair_energies_match_the_oracle():
-    case = setup_case(24, 10.0, 10.0, 6, 21, kind=_lib.ERFC, omega=0.4)
+@FP64_FORMS
+def test_pair_energies_match_the_oracle(prec):
+    case = setup_case(24, 10.0, 10.0, 6, 21, kind=_lib.ERFC, omega=0.4, prec=prec)
     pairs = [(0, 0), (0, 5), (3, 2), (4, 4), (1, 3)]
     e, d = case["plan"].pair_energies(case["psi"], pairs, want_d=True)
     psi = oracle.orbitals_to_real(case["c"], case["mill"], (24,) * 3, case["cell"], real=True)
@@ -141,3 +150,22 @@ def test_invalid_calls_fail_cleanly():
     vpsi, ex, _ = plan.apply(case["psi"], case["occ"])
     vref, eref, _ = oracle_of(case)
     assert abs(ex - eref) <= TOL64 * abs(eref)
+
+
+@pytest.mark.parametrize("N", [8, 12, 16, 36, 64, 72])
+def test_double_float_form_on_every_other_compiled_size(N):
+    # the grid sizes the tests above do not reach (24, 32, 48 are covered):
+    # cells with L = 0.3 N bohr and Ecut = 6 Ha, a few bands, FP64 tolerance
+    nb = 5 if N <= 36 else 3
+    case = setup_case(N, 0.3 * N, 6.0, nb, 500 + N, prec=_lib.PREC_DF64, occ=np.linspace(2.0, 1.0, nb))
+    vpsi, ex, _ = case["plan"].apply(case["psi"], case["occ"])
+    vref, eref, _ = oracle_of(case)
+    assert rel_inf(vpsi.cpu().numpy(), vref) <= TOL64
+    assert abs(ex - eref) <= TOL64 * abs(eref)
+
+
+def test_double_float_form_refused_where_not_built():
+    torch = require_gpu()
+    with pytest.raises(_lib.FockError):
+        _lib.fock_kplan_create((16, 16, 16), cubic(7.0), 6.0, [[0.0, 0.0, 0.0]], [1.0], _lib.ERFC, (0.5,),
+                               _lib.PREC_DF64)
