@@ -41,6 +41,12 @@ struct DevPlan {
   double psi_scale;    // 1 / sqrt(Omega)
   double out_scale;    // sqrt(Omega) / Ntot
   int msmall2;         // |m|^2 at or below which kernel terms are done in FP64 (mixed form)
+  // Columns of the stored half that pair densities reach (Gamma point): row k2
+  // keeps k3 < ncol[k2]; the column pass takes them NC = 2 (N/2 + 1) lines per
+  // CTA from colmap (ncta_col * NC entries, (k2 << 16) | (s << 15) | k3, -1: none)
+  const int* ncol;
+  const int* colmap;
+  int ncta_col;
   // Brillouin-zone sampling: full-grid tables [nq][N][N][N] of v(G + q)
   const void* vtabq;      // v / Ntot in the working precision
   const double* vtabq64;  // v in FP64
@@ -109,7 +115,7 @@ struct Segment {
   int dep;     // segment that must be complete first (-1: none)
   int dep2;    // second such segment (-1: none)
   int task0;   // first ticket
-  int ntasks;  // N * nch
+  int ntasks;  // (N, or ncta_col for the column pass) * nch
   int pad;
 };
 

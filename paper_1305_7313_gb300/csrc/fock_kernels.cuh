@@ -15,7 +15,8 @@
 //   pair_fwd  (plane i1):  z = psi_ai psi_aj + i psi_bi psi_bj, 2D FFT over
 //             (i2, i3), split z = A + iB by Hermitian symmetry (A, B are the
 //             transforms of real planes), store the k3 <= N/2 half of A and B.
-//   pair_col  (row k2):    FFT along i1 of every stored column, energy partials
+//   pair_col  (NC columns): FFT along i1 of the stored columns a pair density
+//             reaches (DevPlan::colmap: NC = 2 (N/2+1) lines per CTA), energy partials
 //             sum w(k3) v |A|^2 and sum w(k3) v |B|^2 (w = 1 on the k3 = 0, N/2
 //             planes, 2 elsewhere: the k3 > N/2 half is the mirror image), times
 //             v/Ntot, inverse FFT along k1.
@@ -82,6 +83,42 @@ __device__ inline void block_sum4(double v[4], double* red) {
   }
 }
 
+// CTA sum of four double-float values in double-float arithmetic (warp
+// shuffles of both parts, then warp 0 over the per-warp sums): no FP64
+// instruction.  The result is valid in thread 0.  red: 2 * 4 * 32 floats.
+__device__ inline void block_sum4_df(df64 v[4], float* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_down_sync(0xffffffffu, v[k].hi, o);
+      const float l2 = __shfl_down_sync(0xffffffffu, v[k].lo, o);
+      v[k] += df64(h2, l2);
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      red[(warp * 4 + k) * 2] = v[k].hi;
+      red[(warp * 4 + k) * 2 + 1] = v[k].lo;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = lane < nw ? df64(red[(lane * 4 + k) * 2], red[(lane * 4 + k) * 2 + 1]) : df64(0.f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, v[k].hi, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, v[k].lo, o);
+        v[k] += df64(h2, l2);
+      }
+    }
+  }
+}
+
 // Compile-time geometry of the passes for grid size N.
 template <class T, int N, int MAXT = kMaxThreads>
 struct Geo {
@@ -103,7 +140,8 @@ struct Geo {
   // two in FP32 up to N = 96, one in FP64)
   static constexpr int MIN_CTAS = (sizeof(T) == 4) ? 2 : 1;
   static constexpr size_t SMEM_PLANE = sizeof(C) * (size_t)(N * RP + N);
-  static constexpr size_t SMEM_COLH = sizeof(C) * (size_t)(N * NC + N) + 32 * 4 * sizeof(double);
+  static constexpr size_t SMEM_COLH =
+      sizeof(C) * (size_t)(N * NC + N) + 32 * 4 * sizeof(double) + NC * sizeof(int);
   static constexpr size_t SMEM_COLF = sizeof(C) * (size_t)(N * N + N);
 };
 
@@ -162,21 +200,15 @@ __device__ inline void block_sum4_ff(const float v[4], float hi[4], float lo[4],
   }
 }
 
-// The kernel terms of the smallest |m| (|m|^2 <= msmall2) of one row k2 of the
-// mixed-form column pass, in FP64: at most 3 (m1) x 2 (m3 = 0, 1 in the stored
-// half) x 2 (A, B) points, one per thread t < 12.  Adds its energy terms to the
-// pair slots itself.  Kept out of line so the FP64 instructions are not
-// predicated into every warp of the kernel.
+// One kernel term of the smallest |m| (|m|^2 <= msmall2: 27 points per pair)
+// of the mixed-form column pass, in FP64: element e of the CTA's lines, at
+// (k1, k2, k3) of pair s.  Adds its energy terms to the pair slot itself.
+// Kept out of line so the FP64 instructions are not predicated into every
+// warp of the kernel.
 template <class T, int N>
-__device__ __noinline__ void small_g_terms_fp64(const DevPlan& g, cplx<T>* S, int k2, int t,
-                                                const Chain& ch, double* epair, double* dpair) {
-  constexpr int KH = N / 2 + 1, NC = 2 * KH;
-  const int m2 = freq_of(k2, N);
-  const int s = t & 1, m3 = (t >> 1) & 1, m1 = (t >> 2) - 1;
-  if (m1 * m1 + m2 * m2 + m3 * m3 > g.msmall2) return;
-  if (s == 1 && ch.bi < 0) return;
-  const int k1 = (m1 + N) % N, k3 = m3;
-  const int e = k1 * NC + s * KH + k3;
+__device__ __noinline__ void small_g_term_fp64(const DevPlan& g, cplx<T>* S, int e, int k1, int k2, int k3,
+                                               int s, const Chain& ch, double* epair, double* dpair) {
+  constexpr int KH = N / 2 + 1;
   const int64_t vi = ((int64_t)k1 * N + k2) * KH + k3;
   const double wgt = (k3 == 0 || 2 * k3 == N) ? 1.0 : 2.0;
   cplx<T> z = S[e];
@@ -355,6 +387,7 @@ __device__ __forceinline__ void pair_fwd_task(const DevPlan& g, const T* __restr
   C* Hp = Hc + (int64_t)i1 * N * NC;
   for (int e = threadIdx.x; e < N * KH; e += blockDim.x) {
     const int k2 = e / KH, k3 = e - k2 * KH;
+    if (k3 >= __ldg(g.ncol + k2)) continue;  // a column no pair density reaches
     const int m2 = k2 == 0 ? 0 : N - k2, m3 = k3 == 0 ? 0 : N - k3;
     const C z = P[k2 * RP + k3], zm = P[m2 * RP + m3];
     Hp[k2 * NC + k3] = cmake<T>(half_of(z.x + zm.x), half_of(z.y - zm.y));
@@ -371,28 +404,33 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
   pair_fwd_task<T, N, kMaxThreads>(g, psi, ch, H + (int64_t)blockIdx.y * g.hsize, blockIdx.x, smem_raw);
 }
 
-// The column pass in double-float arithmetic: the df64 tables of v / Ntot and
-// dv/domega, per-thread double-float energy sums that are reduced (in FP64)
-// before the inverse transform, so they hold no registers across it.
-template <int N, int MAXT>
-__device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __restrict__ Hc, const Chain& ch,
-                                                 int k2, double* __restrict__ epair, double* __restrict__ dpair,
-                                                 unsigned char* smem_raw) {
-  using C = cdf64;
-  using G = Geo<df64, N, MAXT>;
-  constexpr int KH = G::KH, NC = G::NC;
-  C* S = reinterpret_cast<C*>(smem_raw);
-  C* tw = S + N * NC;
-  double* red = reinterpret_cast<double*>(tw + N);
-  load_twiddles<df64>(tw, g);
+// Line code of the column pass: (k2 << 16) | (s << 15) | k3, or -1 (no line).
+__device__ __forceinline__ int line_k2(int code) { return code >> 16; }
+__device__ __forceinline__ int line_s(int code) { return (code >> 15) & 1; }
+__device__ __forceinline__ int line_k3(int code) { return code & 0x7fff; }
+
+// Stage the CTA's line codes in shared memory, then its lines of the transform
+// buffer (all i1) into S[i1][l]; lines without a code are zero.
+template <class C, int N, int NC>
+__device__ __forceinline__ void col_load(const DevPlan& g, const C* __restrict__ Hc, int cta, int* codes,
+                                         C* S) {
+  constexpr int KH = NC / 2;
+  for (int l = threadIdx.x; l < NC; l += blockDim.x) codes[l] = __ldg(g.colmap + cta * NC + l);
+  __syncthreads();
   for (int e0 = threadIdx.x; e0 < N * NC; e0 += kLoadUnroll * blockDim.x) {
     C v[kLoadUnroll];
 #pragma unroll
     for (int u = 0; u < kLoadUnroll; ++u) {
       const int e = e0 + u * blockDim.x;
       if (e < N * NC) {
-        const int i1 = e / NC, c = e - i1 * NC;
-        v[u] = ldcg_c(Hc + ((int64_t)i1 * N + k2) * NC + c);
+        const int i1 = e / NC, l = e - i1 * NC;
+        const int code = codes[l];
+        if (code >= 0) {
+          v[u] = ldcg_c(Hc + ((int64_t)i1 * N + line_k2(code)) * NC + line_s(code) * KH + line_k3(code));
+        } else {
+          v[u].x = 0;
+          v[u].y = 0;
+        }
       }
     }
 #pragma unroll
@@ -402,6 +440,34 @@ __device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __rest
     }
   }
   __syncthreads();
+}
+
+template <class C, int N, int NC>
+__device__ __forceinline__ void col_store(C* __restrict__ Hc, const int* codes, const C* S) {
+  constexpr int KH = NC / 2;
+  for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
+    const int i1 = e / NC, l = e - i1 * NC;
+    const int code = codes[l];
+    if (code >= 0) Hc[((int64_t)i1 * N + line_k2(code)) * NC + line_s(code) * KH + line_k3(code)] = S[e];
+  }
+}
+
+// The column pass in double-float arithmetic: the df64 tables of v / Ntot and
+// dv/domega, per-thread double-float energy sums that are reduced (in FP64)
+// before the inverse transform, so they hold no registers across it.
+template <int N, int MAXT>
+__device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __restrict__ Hc, const Chain& ch,
+                                                 int cta, double* __restrict__ epair, double* __restrict__ dpair,
+                                                 unsigned char* smem_raw) {
+  using C = cdf64;
+  using G = Geo<df64, N, MAXT>;
+  constexpr int KH = G::KH, NC = G::NC;
+  C* S = reinterpret_cast<C*>(smem_raw);
+  C* tw = S + N * NC;
+  double* red = reinterpret_cast<double*>(tw + N);
+  int* codes = reinterpret_cast<int*>(red + 32 * 4);
+  load_twiddles<df64>(tw, g);
+  col_load<C, N, NC>(g, Hc, cta, codes, S);
   const bool want_d = g.dvtab64 != nullptr;
   const df64* vt = static_cast<const df64*>(g.vtab);    // v / Ntot
   const df64* dvt = static_cast<const df64*>(g.dvtab);  // dv/domega
@@ -409,9 +475,10 @@ __device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __rest
   {
     df64 accd[4] = {df64(0.f), df64(0.f), df64(0.f), df64(0.f)};
     for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
-      const int k1 = e / NC, c = e - k1 * NC;
-      const int s = c >= KH ? 1 : 0;
-      const int k3 = c - s * KH;
+      const int k1 = e / NC, l = e - k1 * NC;
+      const int code = codes[l];
+      if (code < 0) continue;
+      const int k2 = line_k2(code), s = line_s(code), k3 = line_k3(code);
       const int vi = (k1 * N + k2) * KH + k3;
       const bool twice = !(k3 == 0 || 2 * k3 == N);
       C z = S[e];
@@ -431,11 +498,11 @@ __device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __rest
       z.y *= v;
       S[e] = z;
     }
-    const double ntot = double(g.ntot);  // the energy table holds v / Ntot
-    double acc[4] = {to_double(accd[0]) * ntot, to_double(accd[1]) * ntot, to_double(accd[2]),
-                     to_double(accd[3])};
-    block_sum4(acc, red);  // synchronises the CTA
+    block_sum4_df(accd, reinterpret_cast<float*>(red));  // synchronises the CTA
     if (threadIdx.x == 0) {
+      const double ntot = double(g.ntot);  // the energy table holds v / Ntot
+      const double acc[4] = {to_double(accd[0]) * ntot, to_double(accd[1]) * ntot, to_double(accd[2]),
+                             to_double(accd[3])};
       if (ch.pa >= 0) atomicAdd(&epair[ch.pa], acc[0]);
       if (ch.pb >= 0) atomicAdd(&epair[ch.pb], acc[1]);
       if (want_d) {
@@ -445,16 +512,13 @@ __device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __rest
     }
   }
   fft_lines<df64, N, +1, NC, G::TLC, 1, NC, MAXT>(S, tw);  // inverse along k1
-  for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
-    const int i1 = e / NC, c = e - i1 * NC;
-    Hc[((int64_t)i1 * N + k2) * NC + c] = S[e];
-  }
+  col_store<C, N, NC>(Hc, codes, S);
 }
 
 // The column pass in FP64 or in the mixed form.
 template <class T, int N, int MAXT>
 __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __restrict__ Hc,
-                                                  const Chain& ch, int k2, double* __restrict__ epair,
+                                                  const Chain& ch, int cta, double* __restrict__ epair,
                                                   double* __restrict__ dpair, unsigned char* smem_raw) {
   using C = cplx<T>;
   using G = Geo<T, N, MAXT>;
@@ -462,36 +526,21 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
   C* S = reinterpret_cast<C*>(smem_raw);
   C* tw = S + N * NC;
   double* red = reinterpret_cast<double*>(tw + N);
+  int* codes = reinterpret_cast<int*>(red + 32 * 4);
   load_twiddles<T>(tw, g);
-  for (int e0 = threadIdx.x; e0 < N * NC; e0 += kLoadUnroll * blockDim.x) {
-    C v[kLoadUnroll];
-#pragma unroll
-    for (int u = 0; u < kLoadUnroll; ++u) {
-      const int e = e0 + u * blockDim.x;
-      if (e < N * NC) {
-        const int i1 = e / NC, c = e - i1 * NC;
-        v[u] = ldcg_c(Hc + ((int64_t)i1 * N + k2) * NC + c);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kLoadUnroll; ++u) {
-      const int e = e0 + u * blockDim.x;
-      if (e < N * NC) S[e] = v[u];
-    }
-  }
-  __syncthreads();
+  col_load<C, N, NC>(g, Hc, cta, codes, S);
   fft_lines<T, N, -1, NC, G::TLC, 1, NC, MAXT>(S, tw);  // along i1
 
   // kernel multiply and energy partials
   const bool want_d = g.dvtab64 != nullptr;
-  const int m2 = freq_of(k2, N);
   double acc[4] = {0.0, 0.0, 0.0, 0.0};  // e_a, e_b, d_a, d_b (FP64 terms)
   float acc_f32[4] = {0.f, 0.f, 0.f, 0.f};  // the same from the FP32 terms (mixed form)
   if constexpr (RealTraits<T>::prec == 0) {
     for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
-      const int k1 = e / NC, c = e - k1 * NC;
-      const int s = c >= KH ? 1 : 0;
-      const int k3 = c - s * KH;
+      const int k1 = e / NC, l = e - k1 * NC;
+      const int code = codes[l];
+      if (code < 0) continue;
+      const int k2 = line_k2(code), s = line_s(code), k3 = line_k3(code);
       const int64_t vi = ((int64_t)k1 * N + k2) * KH + k3;
       const double wgt = (k3 == 0 || 2 * k3 == N) ? 1.0 : 2.0;
       C z = S[e];
@@ -512,18 +561,19 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
       S[e] = z;
     }
   } else {
-    if (m2 * m2 <= g.msmall2 && threadIdx.x < 32) {  // warp 0 of the few rows with small |m2|
-      if (threadIdx.x < 12) small_g_terms_fp64<T, N>(g, S, k2, threadIdx.x, ch, epair, dpair);
-    }
     const T* vt = static_cast<const T*>(g.vtab);    // v / Ntot
     const T* dvt = static_cast<const T*>(g.dvtab);  // dv/domega
     T accf[4] = {T(0), T(0), T(0), T(0)};
     for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
-      const int k1 = e / NC, c = e - k1 * NC;
-      const int s = c >= KH ? 1 : 0;
-      const int k3 = c - s * KH;
-      const int m1 = freq_of(k1, N), m3 = freq_of(k3, N);
-      if (m1 * m1 + m2 * m2 + m3 * m3 <= g.msmall2) continue;
+      const int k1 = e / NC, l = e - k1 * NC;
+      const int code = codes[l];
+      if (code < 0) continue;
+      const int k2 = line_k2(code), s = line_s(code), k3 = line_k3(code);
+      const int m1 = freq_of(k1, N), m2 = freq_of(k2, N), m3 = freq_of(k3, N);
+      if (m1 * m1 + m2 * m2 + m3 * m3 <= g.msmall2) {
+        if (s == 0 || ch.bi >= 0) small_g_term_fp64<T, N>(g, S, e, k1, k2, k3, s, ch, epair, dpair);
+        continue;
+      }
       const int vi = (k1 * N + k2) * KH + k3;
       const T wgt = (k3 == 0 || 2 * k3 == N) ? T(1) : T(2);
       C z = S[e];
@@ -551,10 +601,7 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
   }
   __syncthreads();
   fft_lines<T, N, +1, NC, G::TLC, 1, NC, MAXT>(S, tw);  // inverse along k1
-  for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
-    const int i1 = e / NC, c = e - i1 * NC;
-    Hc[((int64_t)i1 * N + k2) * NC + c] = S[e];
-  }
+  col_store<C, N, NC>(Hc, codes, S);
   if constexpr (RealTraits<T>::prec != 1) {
     block_sum4(acc, red);
   } else {
@@ -575,16 +622,16 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
   }
 }
 
-// One task of the column pass: row k2 of chain `ch` (transform buffer Hc).
-// Shared memory: Geo::SMEM_COLH bytes at smem_raw.
+// One task of the column pass: the NC lines `cta` of the column map for chain
+// `ch` (transform buffer Hc).  Shared memory: Geo::SMEM_COLH bytes at smem_raw.
 template <class T, int N, int MAXT>
 __device__ __forceinline__ void pair_col_task(const DevPlan& g, cplx<T>* __restrict__ Hc,
-                                              const Chain& ch, int k2, double* __restrict__ epair,
+                                              const Chain& ch, int cta, double* __restrict__ epair,
                                               double* __restrict__ dpair, unsigned char* smem_raw) {
   if constexpr (RealTraits<T>::prec == 2) {
-    pair_col_task_df<N, MAXT>(g, Hc, ch, k2, epair, dpair, smem_raw);
+    pair_col_task_df<N, MAXT>(g, Hc, ch, cta, epair, dpair, smem_raw);
   } else {
-    pair_col_task_std<T, N, MAXT>(g, Hc, ch, k2, epair, dpair, smem_raw);
+    pair_col_task_std<T, N, MAXT>(g, Hc, ch, cta, epair, dpair, smem_raw);
   }
 }
 
@@ -622,11 +669,16 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
         // k3 > N/2 is the mirror image of the stored half: A(-k) = A(k)*
         const bool lo = k3 < KH;
         const int r = lo ? k2 : (k2 == 0 ? 0 : N - k2), c = lo ? k3 : N - k3;
-        a[u] = ldcg_c(Hp + r * NC + c);
-        b[u] = ldcg_c(Hp + r * NC + KH + c);
-        if (!lo) {
-          a[u].y = -a[u].y;
-          b[u].y = -b[u].y;
+        if (c < __ldg(g.ncol + r)) {
+          a[u] = ldcg_c(Hp + r * NC + c);
+          b[u] = ldcg_c(Hp + r * NC + KH + c);
+          if (!lo) {
+            a[u].y = -a[u].y;
+            b[u].y = -b[u].y;
+          }
+        } else {  // a column no pair density reaches: zero
+          a[u] = cmake<T>(T(0), T(0));
+          b[u] = a[u];
         }
       }
     }
@@ -779,7 +831,7 @@ struct Launch {
 
   static cudaError_t pair_col(const DevPlan& g, void* H, const Chain* ch, int nch, double* ep,
                               double* dp, cudaStream_t s) {
-    k_pair_col<T, N><<<dim3(N, nch), G::THR_COLH, G::SMEM_COLH, s>>>(g, static_cast<C*>(H), ch,
+    k_pair_col<T, N><<<dim3(g.ncta_col, nch), G::THR_COLH, G::SMEM_COLH, s>>>(g, static_cast<C*>(H), ch,
                                                                        ep, dp);
     return cudaGetLastError();
   }

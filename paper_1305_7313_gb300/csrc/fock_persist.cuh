@@ -3,7 +3,7 @@
 // The work of a batch of systems (uneven grids and band counts) is cut into
 // segments: a segment is one pass kind (forward plane pass, column pass,
 // inverse plane pass) over a run of consecutive chains of one system, i.e.
-// N * nch tasks of one CTA each (a plane or a row of one chain).  A resident
+// N * nch (planes) or ncta_col * nch (column-map CTAs) tasks of one CTA each.  A resident
 // grid of CTAs takes tasks in ticket order from a global counter.  Segments are
 // listed in an order in which every dependency points backwards:
 //
@@ -87,7 +87,9 @@ __device__ __noinline__ void persist_task(const SysDesc* __restrict__ sys, int s
 template <class T, int N>
 __device__ __forceinline__ void run_task(const SysDesc* sys, const Segment& sg, int local, cplx<T>* hslot,
                                          int64_t hsize) {
-  const int c = local / N, idx = local - c * N;
+  // tasks per chain: N planes, or the column-map CTAs of the column pass
+  const int per = sg.kind == 1 ? sys[sg.sys].g.ncta_col : N;
+  const int c = local / per, idx = local - c * per;
   cplx<T>* Hc = hslot + (int64_t)c * hsize;
   if (sg.kind == 0) persist_task<T, N, 0>(sys, sg.sys, sg.chain0 + c, idx, Hc);
   else if (sg.kind == 1) persist_task<T, N, 1>(sys, sg.sys, sg.chain0 + c, idx, Hc);

@@ -85,6 +85,8 @@ struct fock_plan {
   void* d_dvtab = nullptr;
   double* d_vtab64 = nullptr;
   double* d_dvtab64 = nullptr;
+  int* d_ncol = nullptr;
+  int* d_colmap = nullptr;
   double* d_result = nullptr;
   double* h_result = nullptr;  // pinned
   int64_t table_bytes = 0;
@@ -610,6 +612,39 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
         const int64_t i = ((int64_t)k1 * n + k2) * kh + k3;
         kernel_value(p, g2, &v64[i], &dv64[i]);
       }
+  // Columns (k2, k3 <= N/2) of the half spectrum a pair density can reach.
+  // The product of two sphere orbitals has components only at |G| <= 2 Gmax,
+  // so the columns that the ball |G|^2 <= 8 Ecut hits (indices modulo N, so a
+  // grid that aliases the pair densities keeps what the aliases reach) are
+  // kept; the others hold rounding noise only and are never stored,
+  // transformed or read.  Row k2 keeps the prefix k3 < ncol[k2].
+  std::vector<int> ncol(n, 0);
+  {
+    const double r2 = 8.0 * ecut_ha * (1.0 + 1e-9);
+    int mb[3];
+    for (int a = 0; a < 3; ++a) {
+      const double len = std::sqrt(cell[3 * a] * cell[3 * a] + cell[3 * a + 1] * cell[3 * a + 1] +
+                                   cell[3 * a + 2] * cell[3 * a + 2]);
+      mb[a] = (int)std::floor(std::sqrt(r2) * len / (2.0 * kPi)) + 1;
+    }
+    std::vector<unsigned char> mark((size_t)n * n, 0);
+    for (int m1 = -mb[0]; m1 <= mb[0]; ++m1)
+      for (int m2 = -mb[1]; m2 <= mb[1]; ++m2)
+        for (int m3 = -mb[2]; m3 <= mb[2]; ++m3)
+          if (g2_of(p->recip, m1, m2, m3) <= r2)
+            mark[(size_t)(((m2 % n) + n) % n) * n + (((m3 % n) + n) % n)] = 1;
+    for (int k2 = 0; k2 < n; ++k2)
+      for (int k3 = 0; k3 < kh; ++k3)
+        if (mark[(size_t)k2 * n + k3]) ncol[k2] = k3 + 1;
+  }
+  std::vector<int> colmap;
+  for (int k2 = 0; k2 < n; ++k2)
+    for (int s = 0; s < 2; ++s)
+      for (int k3 = 0; k3 < ncol[k2]; ++k3) colmap.push_back((k2 << 16) | (s << 15) | k3);
+  const int nlines = 2 * kh;
+  const int ncta_col = std::max(1, (int)((colmap.size() + nlines - 1) / nlines));
+  colmap.resize((size_t)ncta_col * nlines, -1);
+
   const bool fp64 = prec == FOCK_PREC_FP64;
   // twiddles w[t] = exp(-2 pi i t / N)
   std::vector<double> tw64(2 * n);
@@ -639,6 +674,9 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
             upload((void**)&p->d_gidxneg, gneg.data(), sizeof(int) * gneg.size()) &&
             upload((void**)&p->d_vtab64, v64.data(), sizeof(double) * nhalf);
   if (ok && kind == FOCK_KERNEL_ERFC) ok = upload((void**)&p->d_dvtab64, dv64.data(), sizeof(double) * nhalf);
+  if (ok)
+    ok = upload((void**)&p->d_ncol, ncol.data(), sizeof(int) * ncol.size()) &&
+         upload((void**)&p->d_colmap, colmap.data(), sizeof(int) * colmap.size());
   if (ok) {
     if (fp64) {
       std::vector<double> vs(nhalf);
@@ -699,6 +737,9 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
   d.psi_scale = 1.0 / std::sqrt(p->vol);
   d.out_scale = std::sqrt(p->vol) / (double)ntot;
   d.msmall2 = prec == FOCK_PREC_MIXED32 ? kMsmall2 : -1;
+  d.ncol = p->d_ncol;
+  d.colmap = p->d_colmap;
+  d.ncta_col = ncta_col;
 
   const size_t chain_bytes = (size_t)d.hsize * 2 * (size_t)ops->real_bytes;
   p->chain_batch = (int)std::max<size_t>(1, kChainBufferBytes / chain_bytes);
@@ -1026,6 +1067,8 @@ fock_status fock_destroy(fock_plan_t plan) {
   cudaFree(plan->d_vtab64);
   cudaFree(plan->d_dvtab);
   cudaFree(plan->d_dvtab64);
+  cudaFree(plan->d_ncol);
+  cudaFree(plan->d_colmap);
   cudaFree(plan->d_result);
   if (plan->h_result) cudaFreeHost(plan->h_result);
   delete plan;
@@ -1309,7 +1352,7 @@ fock_status fock_batch_create(fock_batch_t* out, int nsys, const fock_plan_t* pl
     sg.slot = t % D;
     sg.dep = dep;
     sg.dep2 = dep2;
-    sg.ntasks = b->plans[sg.sys]->n * sg.nch;
+    sg.ntasks = (sg.kind == 1 ? b->plans[sg.sys]->dp.ncta_col : b->plans[sg.sys]->n) * sg.nch;
     b->segs.push_back(sg);
     return (int)b->segs.size() - 1;
   };
