@@ -146,7 +146,9 @@ fock_status fock_plan_reserve(fock_plan_t plan, int nb_max);
 
 /* Number of band-pair chains (two pairs per complex transform) each launch of
  * the pair passes processes; sets the size of the plan's transform buffer
- * (chain_batch x N^2 (N+2) complex elements).  The default targets 120 MiB.
+ * (chain_batch x N^2 (N+2) complex elements).  The default is the largest
+ * multiple of SMs / gcd(N, SMs) chains (whole waves of the plane passes) whose
+ * buffer fits 320 MiB, or as many chains as fit when one such group does not.
  * Takes effect at the next call.  Errors: INVALID_ARG. */
 fock_status fock_plan_set_batch(fock_plan_t plan, int chain_batch);
 

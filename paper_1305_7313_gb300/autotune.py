@@ -79,7 +79,7 @@ def _time_ms(fn, reps):
     return statistics.median(out)
 
 
-def tune_apply(plan, psi, occ, chain_batches=(4, 8, 17, 32), band_blocks=(8, 16, 32), reps=2,
+def tune_apply(plan, psi, occ, chain_batches=(8, 17, 19, 32, 38), band_blocks=(8, 16, 32), reps=2,
                use_cache=True):
     """Fastest (chain_batch, band_block) for ``plan.apply(psi, occ)``; sets it on the plan.
 

@@ -25,7 +25,7 @@ using fockx::KernelOps;
 namespace {
 
 constexpr int kBandBlock = 16;                  // default bands per block of the pair schedule
-constexpr size_t kChainBufferBytes = 120u << 20;  // default size of the pair-transform buffer
+constexpr size_t kChainBufferBytes = 320u << 20;  // budget of the default pair-transform buffer
 constexpr int kMsmall2 = 3;                     // |m|^2 of the kernel terms kept in FP64 (mixed)
 
 // d as the double-float pair (hi, lo): hi = float(d), lo = float(d - hi).
@@ -741,14 +741,27 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
   d.colmap = p->d_colmap;
   d.ncta_col = ncta_col;
 
-  const size_t chain_bytes = (size_t)d.hsize * 2 * (size_t)ops->real_bytes;
-  p->chain_batch = (int)std::max<size_t>(1, kChainBufferBytes / chain_bytes);
-
-  int optin = 0;
+  int optin = 0, sms = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
   if (e != cudaSuccess) {
     fock_destroy(p);
     return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
+  }
+  // Default chains per launch: a multiple of c0 = SMs / gcd(N, SMs), so the N
+  // CTAs per chain of the plane passes fill whole waves (19 on a 152-SM GPU for
+  // every compiled N), as many multiples as the buffer budget holds.
+  const size_t chain_bytes = (size_t)d.hsize * 2 * (size_t)ops->real_bytes;
+  {
+    int a = n, b = std::max(1, sms);
+    while (b != 0) {
+      const int t = a % b;
+      a = b;
+      b = t;
+    }
+    const size_t c0 = (size_t)std::max(1, sms) / (size_t)a;
+    const size_t fit = kChainBufferBytes / chain_bytes;
+    p->chain_batch = (int)(fit >= c0 ? c0 * (fit / c0) : std::max<size_t>(1, fit));
   }
   if (ops->smem > (size_t)optin) {
     fock_destroy(p);
