@@ -166,7 +166,22 @@ def time_form(plan, psi, occ, steps, warmup, want_dex=False, rank=0, world=1):
     return dict(ms=ms, phase_ms=phase_ms, launches=launches, stats=plan.stats(), clocks=clk.summary())
 
 
-def roofline(form, plan, res, steps, peaks, peak_src):
+# DRAM bytes (read + write) per chain of the dominant kernel, from one ncu
+# capture of the 96^3 pair passes at 38 chains per launch and band block 8
+# (profiles/pair_passes_*_96.md); scaled to a launch by its chains, reported
+# only for that band block (the orbital re-reads depend on it).
+MEASURED_TRAFFIC_PER_CHAIN = {("fp64", 96, "pair_inv"): 57.6e6, ("df64", 96, "pair_inv"): 57.6e6,
+                              ("mixed32", 96, "pair_inv"): 16.4e6}
+
+
+def measured_traffic(form, n, kernel, band_block, chains_per_launch):
+    per = MEASURED_TRAFFIC_PER_CHAIN.get((form, n, kernel))
+    if per is None or band_block != 8:
+        return None
+    return per * chains_per_launch
+
+
+def roofline(form, plan, res, steps, peaks, peak_src, band_block=16):
     """Roofline of the dominant pair kernel (the phase with the largest device time)."""
     n = plan.grid[0]
     ntot = float(n) ** 3
@@ -190,18 +205,39 @@ def roofline(form, plan, res, steps, peaks, peak_src):
         src = ("nominal FP64 at 2070 MHz" if form == "fp64" else
                "double-float flops at the FP32 pipe rate (9.4 FP32 instructions per flop), 2070 MHz")
         return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_src": src,
+                "frac": achieved / peak,
+                "traffic": measured_traffic(form, n, dom, band_block, chains_per_launch),
+                "traffic_unit": "DRAM bytes per launch (ncu)", "peak_src": src,
                 "frac_at_sampled_clock": achieved / (per_clk * mhz * 1e6 / 1e12),
                 "ms_per_launch": ms_per_launch, "chains_per_launch": chains_per_launch}
-    # complex64 half-spectrum buffer traffic: written once by pair_fwd, read and
-    # written by pair_col, read once by pair_inv
-    hbytes = n * n * nc * 8.0
-    per_chain = {"pair_fwd": hbytes, "pair_col": 2 * hbytes, "pair_inv": hbytes}[dom]
+    # Algorithmic bytes per chain (two pairs): the kept columns of the complex64
+    # half spectrum (written by pair_fwd, read and written by pair_col, read by
+    # pair_inv) plus the orbital and accumulator planes, each reused by the
+    # chains of a band block: pair_fwd reads four orbital planes, pair_inv reads
+    # four and read-modify-writes four accumulator planes.
+    kept, total = plan.columns()
+    hbytes = n * n * nc * 8.0 * kept / total
+    plane = ntot * 4.0 / max(1, band_block)
+    per_chain = {"pair_fwd": hbytes + 4 * plane, "pair_col": 2 * hbytes, "pair_inv": hbytes + 12 * plane}[dom]
     achieved = per_chain * chains_per_launch / (ms_per_launch * 1e-3) / 1e9
     peak = float(peaks["hbm_gbs"])
     return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "peak_src": peak_src + " (hbm copy)",
+            "frac": achieved / peak,
+            "traffic": measured_traffic(form, n, dom, band_block, chains_per_launch),
+            "traffic_unit": "DRAM bytes per launch (ncu)", "algorithmic_bytes_per_launch": per_chain * chains_per_launch,
+            "peak_src": peak_src + " (hbm copy)",
+            "bytes_per_chain": per_chain, "kept_columns": kept / total, "band_block": band_block,
             "ms_per_launch": ms_per_launch, "chains_per_launch": chains_per_launch}
+
+
+def fixed_blocks(plan, args):
+    """--chain-batch / --band-block given: set them and report them as the choice."""
+    if args.chain_batch:
+        plan.set_batch(args.chain_batch)
+    if args.band_block:
+        plan.set_band_block(args.band_block)
+    return {"chain_batch": args.chain_batch, "band_block": args.band_block or 16, "tuned_on_bands": 0,
+            "candidates": 0}
 
 
 def tune_on_subset(plan, c, occ, nbands, reps=2):
@@ -482,6 +518,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-kpoints", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--chain-batch", type=int, default=0,
+                    help="with --no-tune: chains per pair-pass launch of the Gamma-point forms")
+    ap.add_argument("--band-block", type=int, default=0,
+                    help="with --no-tune: band block of the Gamma-point pair schedule")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison line")
     ap.add_argument("--cufft-bands", type=int, default=128)
     ap.add_argument("--tune-bands", type=int, default=64,
@@ -515,13 +555,15 @@ def main():
     tuned = None
     if not args.no_tune:
         tuned = tune_on_subset(plan, c, occ, min(w["nb"], max(8, args.tune_bands // 2)), reps=1)
+    elif args.chain_batch or args.band_block:
+        tuned = fixed_blocks(plan, args)
     psi = torch.from_numpy(c).cuda()
     pairs = w["nb"] * (w["nb"] + 1) // 2
     res = time_form(plan, psi, occ, args.steps, args.warmup, rank=rank, world=world)
     ms_step = res["ms"] / args.steps
     value = pairs * args.steps / (res["ms"] * 1e-3)
     form = {PREC_FP64: "fp64", PREC_MIXED32: "mixed32"}.get(w["prec"], "df64")
-    roof = roofline(form, plan, res, args.steps, peaks, peak_src)
+    roof = roofline(form, plan, res, args.steps, peaks, peak_src, tuned["band_block"] if tuned else 16)
 
     # ---- end to end through the public API from pinned host memory
     e2e = None
@@ -553,12 +595,15 @@ def main():
         tunedm = None
         if not args.no_tune:
             tunedm = tune_on_subset(planm, cm, occm, min(wm["nb"], args.tune_bands))
+        elif args.chain_batch or args.band_block:
+            tunedm = fixed_blocks(planm, args)
         psim = torch.from_numpy(cm).cuda()
         resm = time_form(planm, psim, occm, args.steps, args.warmup, rank=rank, world=world)
         pm = wm["nb"] * (wm["nb"] + 1) // 2
         mixed = {"workload": wm["name"], "value": pm * args.steps / (resm["ms"] * 1e-3), "unit": UNIT,
                  "ms_per_step": resm["ms"] / args.steps, "dtype": "f32",
-                 "roofline": roofline("mixed32", planm, resm, args.steps, peaks, peak_src),
+                 "roofline": roofline("mixed32", planm, resm, args.steps, peaks, peak_src,
+                                      tunedm["band_block"] if tunedm else 16),
                  "phase_ms_per_step": {k: v / args.steps for k, v in resm["phase_ms"].items()},
                  "gpu_launches": resm["launches"], "clocks": resm["clocks"], "tuned": tunedm}
         planm.close()
@@ -576,12 +621,15 @@ def main():
         tunedd = None
         if not args.no_tune:
             tunedd = tune_on_subset(pland, cd, occd, min(wd["nb"], args.tune_bands), reps=1)
+        elif args.chain_batch or args.band_block:
+            tunedd = fixed_blocks(pland, args)
         psid = torch.from_numpy(cd).cuda()
         resd = time_form(pland, psid, occd, args.steps, args.warmup, rank=rank, world=world)
         pd = wd["nb"] * (wd["nb"] + 1) // 2
         df = {"workload": wd["name"], "value": pd * args.steps / (resd["ms"] * 1e-3), "unit": UNIT,
               "ms_per_step": resd["ms"] / args.steps, "dtype": "f32x2 (double-float)",
-              "roofline": roofline("df64", pland, resd, args.steps, peaks, peak_src),
+              "roofline": roofline("df64", pland, resd, args.steps, peaks, peak_src,
+                                   tunedd["band_block"] if tunedd else 16),
               "phase_ms_per_step": {k: v / args.steps for k, v in resd["phase_ms"].items()},
               "gpu_launches": resd["launches"], "clocks": resd["clocks"], "tuned": tunedd}
         pland.close()

@@ -189,6 +189,11 @@ fock_status fock_plan_set_band_block(fock_plan_t plan, int band_block);
 /* Bytes of device memory the plan holds (tables + workspace).  bytes: host. */
 fock_status fock_plan_device_bytes(fock_plan_t plan, int64_t* bytes);
 
+/* Columns of the stored half spectrum (N x 2(N/2+1) per plane, both pairs of a
+ * chain) that the pair-density ball |G| <= 2 Gmax reaches and the column pass
+ * transforms (`kept`), out of `total`.  Host outputs; either may be NULL. */
+fock_status fock_plan_columns(fock_plan_t plan, int64_t* kept, int64_t* total);
+
 /*
  * fock_apply — V_x psi and E_x for nb orbitals (§4, V_x equation and E_x).
  *   psi_G   device complex128 [nb][npw] (interleaved re, im), canonical order.

@@ -80,6 +80,7 @@ _SIGNATURES = {
     "fock_plan_reserve": [_vp, ctypes.c_int],
     "fock_plan_set_batch": [_vp, ctypes.c_int],
     "fock_plan_device_bytes": [_vp, _c_i64_p],
+    "fock_plan_columns": [_vp, _c_i64_p, _c_i64_p],
     "fock_plan_set_timing": [_vp, ctypes.c_int],
     "fock_plan_stats": [_vp, ctypes.POINTER(FockStats)],
     "fock_apply": [_vp, _vp, ctypes.c_int, _c_dbl_p, _vp, _c_dbl_p, _c_dbl_p, _vp],
@@ -259,6 +260,14 @@ def fock_plan_device_bytes(plan):
     n = ctypes.c_int64()
     _check(load().fock_plan_device_bytes(plan, ctypes.byref(n)), plan)
     return n.value
+
+
+def fock_plan_columns(plan):
+    """(kept, total) columns of the stored half spectrum the column pass transforms."""
+    k = ctypes.c_int64()
+    t = ctypes.c_int64()
+    _check(load().fock_plan_columns(plan, ctypes.byref(k), ctypes.byref(t)), plan)
+    return k.value, t.value
 
 
 def fock_apply(plan, psi_G, occ, vpsi_G, want_ex=True, want_dex=False, stream=None):

@@ -87,6 +87,7 @@ struct fock_plan {
   double* d_dvtab64 = nullptr;
   int* d_ncol = nullptr;
   int* d_colmap = nullptr;
+  int64_t kept_columns = 0;  // lines of the column map (both pairs)
   double* d_result = nullptr;
   double* h_result = nullptr;  // pinned
   int64_t table_bytes = 0;
@@ -642,6 +643,7 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
     for (int s = 0; s < 2; ++s)
       for (int k3 = 0; k3 < ncol[k2]; ++k3) colmap.push_back((k2 << 16) | (s << 15) | k3);
   const int nlines = 2 * kh;
+  p->kept_columns = (int64_t)colmap.size();
   const int ncta_col = std::max(1, (int)((colmap.size() + nlines - 1) / nlines));
   colmap.resize((size_t)ncta_col * nlines, -1);
 
@@ -882,6 +884,13 @@ fock_status fock_plan_reserve(fock_plan_t plan, int nb_max) {
   fock_status st = check_device(plan);
   if (st != FOCK_OK) return st;
   return ensure_workspace(plan, nb_max, nb_max * (nb_max + 1) / 2);
+}
+
+fock_status fock_plan_columns(fock_plan_t plan, int64_t* kept, int64_t* total) {
+  if (!plan) return fail(nullptr, FOCK_ERR_INVALID_ARG, "plan is NULL");
+  if (kept) *kept = plan->kept_columns;
+  if (total) *total = (int64_t)plan->n * 2 * (plan->n / 2 + 1);
+  return FOCK_OK;
 }
 
 fock_status fock_plan_device_bytes(fock_plan_t plan, int64_t* bytes) {

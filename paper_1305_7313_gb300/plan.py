@@ -56,6 +56,10 @@ class FockPlan:
     def device_bytes(self):
         return _lib.fock_plan_device_bytes(self.handle)
 
+    def columns(self):
+        """(kept, total) half-spectrum columns the column pass transforms."""
+        return _lib.fock_plan_columns(self.handle)
+
     def apply(self, psi_G, occ, vpsi_G=None, want_ex=True, want_dex=False, stream=None):
         """(V_x psi, E_x, dE_x/domega) for device orbitals ``psi_G`` [nb, npw] complex128."""
         import torch
