@@ -430,12 +430,35 @@ __device__ __forceinline__ int line_k3(int code) { return code & 0x7fff; }
 
 // Stage the CTA's line codes in shared memory, then its lines of the transform
 // buffer (all i1) into S[i1][l]; lines without a code are zero.
-template <class C, int N, int NC>
+// Asynchronous global-to-shared copies (cp.async) for the column-pass loads of
+// the stand-alone kernels: every element of a thread is in flight at once, no
+// register holds it.  Inside the persistent kernel the loads stay ld.global.cg
+// (the buffer was written earlier by the same launch, so L1 must not serve it).
+constexpr bool kColAsync = true;
+
+template <class C, int N, int NC, bool ASYNC>
 __device__ __forceinline__ void col_load(const DevPlan& g, const C* __restrict__ Hc, int cta, int* codes,
                                          C* S) {
   constexpr int KH = NC / 2;
   for (int l = threadIdx.x; l < NC; l += blockDim.x) codes[l] = __ldg(g.colmap + cta * NC + l);
   __syncthreads();
+  if constexpr (ASYNC) {
+    static_assert(sizeof(C) == 8 || sizeof(C) == 16, "cp.async copies 8 or 16 bytes");
+    for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
+      const int i1 = e / NC, l = e - i1 * NC;
+      const int code = codes[l];
+      // a line without a code copies zero bytes: the destination is zero-filled
+      const C* src = code >= 0 ? Hc + ((int64_t)i1 * N + line_k2(code)) * NC + line_s(code) * KH + line_k3(code)
+                               : Hc;
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(S + e);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst), "l"(src), "n"((int)sizeof(C)),
+                   "r"(code >= 0 ? (int)sizeof(C) : 0)
+                   : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    return;
+  }
   for (int e0 = threadIdx.x; e0 < N * NC; e0 += kLoadUnroll * blockDim.x) {
     C v[kLoadUnroll];
 #pragma unroll
@@ -486,7 +509,7 @@ __device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __rest
   double* red = reinterpret_cast<double*>(tw + N);
   int* codes = reinterpret_cast<int*>(red + 32 * 4);
   load_twiddles<df64>(tw, g);
-  col_load<C, N, NC>(g, Hc, cta, codes, S);
+  col_load<C, N, NC, kColAsync && MAXT == kMaxThreads>(g, Hc, cta, codes, S);
   const bool want_d = g.dvtab64 != nullptr;
   const df64* vt = static_cast<const df64*>(g.vtab);    // v / Ntot
   const df64* dvt = static_cast<const df64*>(g.dvtab);  // dv/domega
@@ -547,7 +570,7 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
   double* red = reinterpret_cast<double*>(tw + N);
   int* codes = reinterpret_cast<int*>(red + 32 * 4);
   load_twiddles<T>(tw, g);
-  col_load<C, N, NC>(g, Hc, cta, codes, S);
+  col_load<C, N, NC, kColAsync && MAXT == kMaxThreads>(g, Hc, cta, codes, S);
   fft_lines<T, N, -1, NC, G::TLC, 1, NC, MAXT>(S, tw);  // along i1
 
   // kernel multiply and energy partials

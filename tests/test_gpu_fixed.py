@@ -11,7 +11,7 @@ from tests._common import cubic, rel_inf, require_gpu
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec,tol", [(_lib.PREC_FP64, 1e-10), (_lib.PREC_MIXED32, 2e-5)])
+@pytest.mark.parametrize("prec,tol", [(_lib.PREC_FP64, 1e-10), (_lib.PREC_DF64, 1e-10), (_lib.PREC_MIXED32, 2e-5)])
 def test_fixed_operator_on_trial_orbitals(prec, tol):
     torch = require_gpu()
     N, L, ecut = 32, 9.0, 12.0

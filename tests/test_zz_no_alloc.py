@@ -22,6 +22,7 @@ TOL32 = 5e-6
 
 @pytest.mark.parametrize("N,L,ecut,nb,kind,omega,prec,tol", [
     (24, 10.0, 10.0, 8, _lib.SPENCER_ALAVI, None, _lib.PREC_FP64, TOL64),
+    (24, 10.0, 10.0, 8, _lib.SPENCER_ALAVI, None, _lib.PREC_DF64, TOL64),
     (48, 13.5, 12.0, 9, _lib.ERFC, 0.106, _lib.PREC_MIXED32, TOL32),
 ])
 def test_static_scratch_matches_the_allocating_entry_point(N, L, ecut, nb, kind, omega, prec, tol):
