@@ -20,8 +20,9 @@
 //             sum w(k3) v |A|^2 and sum w(k3) v |B|^2 (w = 1 on the k3 = 0, N/2
 //             planes, 2 elsewhere: the k3 > N/2 half is the mirror image), times
 //             v/Ntot, inverse FFT along k1.
-//   pair_inv  (plane i1):  rebuild z = A + iB over the whole plane from the
-//             stored half, inverse 2D FFT -> phi_a + i phi_b, then
+//   pair_inv  (plane i1):  inverse FFT along k2 of the stored half plane (A and B
+//             columns), rebuild each row z = A + iB over all k3 (the k3 > N/2
+//             half from the conjugates), inverse FFT along k3 -> phi_a + i phi_b, then
 //             W_aj -= f_ai psi_ai phi_a, W_ai -= f_aj psi_aj phi_a (i != j), same for b.
 #pragma once
 
@@ -153,6 +154,10 @@ struct Geo {
   static constexpr size_t SMEM_COLH =
       sizeof(C) * (size_t)(N * NC + N) + 32 * 4 * sizeof(double) + NC * sizeof(int);
   static constexpr size_t SMEM_COLF = sizeof(C) * (size_t)(N * N + N);
+  // inverse plane pass: the stored half plane with an odd row stride NC + 1,
+  // the twiddles and the column map's row lengths
+  static constexpr int NCP = NC + 1;
+  static constexpr size_t SMEM_INV = sizeof(C) * (size_t)(N * NCP + N) + N * sizeof(int);
 };
 
 // Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
@@ -696,45 +701,83 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
                                               unsigned char* smem_raw) {
   using C = cplx<T>;
   using G = Geo<T, N, MAXT>;
-  constexpr int RP = G::RP, KH = G::KH, NC = G::NC;
-  C* P = reinterpret_cast<C*>(smem_raw);
-  C* tw = P + N * RP;
+  constexpr int KH = G::KH, NC = G::NC, NCP = G::NCP;
+  C* Q = reinterpret_cast<C*>(smem_raw);
+  C* tw = Q + N * NCP;
+  int* ncol = reinterpret_cast<int*>(tw + N);
   load_twiddles<T>(tw, g);
+  for (int r = threadIdx.x; r < N; r += blockDim.x) ncol[r] = __ldg(g.ncol + r);
+  __syncthreads();
   const C* Hp = Hc + (int64_t)i1 * N * NC;
-  for (int e0 = threadIdx.x; e0 < N * N; e0 += kLoadUnroll * blockDim.x) {
-    C a[kLoadUnroll], b[kLoadUnroll];
+  // 1. the stored half plane, row k2 = [A(k2, 0..N/2) | B(k2, 0..N/2)], into
+  //    Q[k2][0..NC); columns no pair density reaches (never written) are zero
+  if constexpr (kColAsync && MAXT == kMaxThreads) {
+    for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
+      const int k2 = e / NC, c = e - k2 * NC;
+      const int keep = (c < KH ? c : c - KH) < ncol[k2];
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(Q + k2 * NCP + c);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst), "l"(Hp + e), "n"((int)sizeof(C)),
+                   "r"(keep ? (int)sizeof(C) : 0)
+                   : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else {
+    for (int e0 = threadIdx.x; e0 < N * NC; e0 += kLoadUnroll * blockDim.x) {
+      C v[kLoadUnroll];
 #pragma unroll
-    for (int u = 0; u < kLoadUnroll; ++u) {
-      const int e = e0 + u * blockDim.x;
-      if (e < N * N) {
-        const int k2 = e / N, k3 = e - k2 * N;
-        // k3 > N/2 is the mirror image of the stored half: A(-k) = A(k)*
-        const bool lo = k3 < KH;
-        const int r = lo ? k2 : (k2 == 0 ? 0 : N - k2), c = lo ? k3 : N - k3;
-        if (c < __ldg(g.ncol + r)) {
-          a[u] = ldcg_c(Hp + r * NC + c);
-          b[u] = ldcg_c(Hp + r * NC + KH + c);
-          if (!lo) {
-            a[u].y = -a[u].y;
-            b[u].y = -b[u].y;
-          }
-        } else {  // a column no pair density reaches: zero
-          a[u] = cmake<T>(T(0), T(0));
-          b[u] = a[u];
+      for (int u = 0; u < kLoadUnroll; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < N * NC) {
+          const int k2 = e / NC, c = e - k2 * NC;
+          v[u] = ldcg_c(Hp + e);
+          if (!((c < KH ? c : c - KH) < ncol[k2])) v[u] = cmake<T>(T(0), T(0));
         }
       }
-    }
 #pragma unroll
-    for (int u = 0; u < kLoadUnroll; ++u) {
-      const int e = e0 + u * blockDim.x;
-      if (e < N * N) {
-        const int k2 = e / N, k3 = e - k2 * N;
-        P[k2 * RP + k3] = cmake<T>(a[u].x - b[u].y, a[u].y + b[u].x);
+      for (int u = 0; u < kLoadUnroll; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < N * NC) {
+          const int k2 = e / NC, c = e - k2 * NC;
+          Q[k2 * NCP + c] = v[u];
+        }
       }
     }
   }
   __syncthreads();
-  fft_plane<T, N, +1, G::TLP, RP, MAXT>(P, tw);  // along k3, then k2
+  // 2. inverse transform along k2 of the NC stored columns
+  fft_lines<T, N, +1, NC, G::TLC, 1, NCP, MAXT>(Q, tw);
+  // 3. rows: z(k3) = A^(k3) + i B^(k3) for k3 <= N/2 and, from the Hermitian
+  //    symmetry of the transforms of the real planes, z(N - k3) =
+  //    conj(A^(k3)) + i conj(B^(k3)); one warp per row (reads, then writes)
+  {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    static_assert(N / 2 + 1 <= 64, "two stored columns per lane");
+    for (int i2 = threadIdx.x >> 5; i2 < N; i2 += nw) {
+      C* row = Q + i2 * NCP;
+      C av[2], bv[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int k = lane + 32 * t;
+        if (k < KH) {
+          av[t] = row[k];
+          bv[t] = row[KH + k];
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int k = lane + 32 * t;
+        if (k < KH) {
+          row[k] = cmake<T>(av[t].x - bv[t].y, av[t].y + bv[t].x);
+          if (k > 0 && 2 * k < N) row[N - k] = cmake<T>(av[t].x + bv[t].y, bv[t].x - av[t].y);
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // 4. inverse transform along k3 of the N rows: Q[i2][i3] = phi_a + i phi_b
+  fft_lines<T, N, +1, N, G::TLP, NCP, 1, MAXT>(Q, tw);
   const int64_t plane0 = (int64_t)i1 * N * N;
   const bool hb = ch.bi >= 0;
   // Up to four updates k, W[tgt_k] -= f[src_k] psi[src_k] phi:
@@ -766,8 +809,8 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
       const int i2 = e / N, i3 = e - i2 * N;
       float4 phia, phib;
       {
-        const C z0 = P[i2 * RP + i3], z1 = P[i2 * RP + i3 + 1], z2 = P[i2 * RP + i3 + 2],
-                z3 = P[i2 * RP + i3 + 3];
+        const C z0 = Q[i2 * NCP + i3], z1 = Q[i2 * NCP + i3 + 1], z2 = Q[i2 * NCP + i3 + 2],
+                z3 = Q[i2 * NCP + i3 + 3];
         phia = make_float4(z0.x, z1.x, z2.x, z3.x);
         phib = make_float4(z0.y, z1.y, z2.y, z3.y);
       }
@@ -803,7 +846,7 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
   } else {
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
       const int i2 = e / N, i3 = e - i2 * N;
-      const C z = P[i2 * RP + i3];
+      const C z = Q[i2 * NCP + i3];
       T c[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) c[k] = tgt[k] < 0 ? T(0) : -f[k] * ps[k][e] * (k < 2 ? z.x : z.y);
@@ -821,7 +864,7 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
 }
 
 template <class T, int N>
-__global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
+__global__ void __launch_bounds__(Geo<T, N>::THR_COLH, Geo<T, N>::MIN_CTAS)
     k_pair_inv(DevPlan g, const T* __restrict__ psi, acc_t<T>* __restrict__ W, const T* __restrict__ occ,
                const Chain* __restrict__ chains, const cplx<T>* __restrict__ H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -832,6 +875,8 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
 
 // ------------------------------------------------------------------ launchers
 
+constexpr size_t smem_max(size_t a, size_t b) { return a > b ? a : b; }
+
 template <class T, int N>
 struct Launch {
   using C = cplx<T>;
@@ -840,13 +885,15 @@ struct Launch {
   static cudaError_t configure(const DevPlan&) {
     const void* fns[] = {(const void*)k_col_full<T, N, +1>, (const void*)k_col_full<T, N, -1>,
                          (const void*)k_plane_full<T, N, +1, 0, 1>,
-                         (const void*)k_plane_full<T, N, -1, 1, 0>, (const void*)k_pair_fwd<T, N>,
-                         (const void*)k_pair_inv<T, N>};
+                         (const void*)k_plane_full<T, N, -1, 1, 0>, (const void*)k_pair_fwd<T, N>};
     for (const void* f : fns) {
       cudaError_t err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)G::SMEM_PLANE);
       if (err != cudaSuccess) return err;
     }
+    cudaError_t err = cudaFuncSetAttribute((const void*)k_pair_inv<T, N>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_INV);
+    if (err != cudaSuccess) return err;
     return cudaFuncSetAttribute((const void*)k_pair_col<T, N>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_COLH);
   }
@@ -880,7 +927,7 @@ struct Launch {
 
   static cudaError_t pair_inv(const DevPlan& g, const void* psi, void* W, const void* occ,
                               const Chain* ch, int nch, const void* H, cudaStream_t s) {
-    k_pair_inv<T, N><<<dim3(N, nch), G::THR_PLANE, G::SMEM_PLANE, s>>>(
+    k_pair_inv<T, N><<<dim3(N, nch), G::THR_COLH, G::SMEM_INV, s>>>(
         g, static_cast<const T*>(psi), static_cast<acc_t<T>*>(W), static_cast<const T*>(occ), ch,
         static_cast<const C*>(H));
     return cudaGetLastError();
@@ -899,7 +946,7 @@ struct Launch {
 
   static constexpr KernelOps ops() {
     return KernelOps{(int)sizeof(T), RealTraits<T>::prec, N,
-                     G::SMEM_COLH > G::SMEM_PLANE ? G::SMEM_COLH : G::SMEM_PLANE,
+                     smem_max(smem_max(G::SMEM_COLH, G::SMEM_PLANE), G::SMEM_INV),
                      configure, to_real, pair_fwd, pair_col, pair_inv, to_sphere};
   }
 };

@@ -33,9 +33,10 @@ template <class T>
 struct PersistGeo {
   // largest dynamic shared memory over the grid sizes the persistent kernel runs
   static constexpr size_t smem_of(size_t a, size_t b) { return a > b ? a : b; }
-  static constexpr size_t SMEM =
+  static constexpr size_t SMEM = smem_of(
       smem_of(smem_of(Geo<T, 96, kPersistMaxT>::SMEM_PLANE, Geo<T, 96, kPersistMaxT>::SMEM_COLH),
-              smem_of(Geo<T, 72, kPersistMaxT>::SMEM_PLANE, Geo<T, 72, kPersistMaxT>::SMEM_COLH));
+              smem_of(Geo<T, 72, kPersistMaxT>::SMEM_PLANE, Geo<T, 72, kPersistMaxT>::SMEM_COLH)),
+      smem_of(Geo<T, 96, kPersistMaxT>::SMEM_INV, Geo<T, 72, kPersistMaxT>::SMEM_INV));
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 2 : 1;  // shared memory allows 2 in FP32
 };
 
