@@ -170,8 +170,8 @@ def time_form(plan, psi, occ, steps, warmup, want_dex=False, rank=0, world=1):
 # capture of the 96^3 pair passes at 38 chains per launch and band block 8
 # (profiles/pair_passes_*_96.md); scaled to a launch by its chains, reported
 # only for that band block (the orbital re-reads depend on it).
-MEASURED_TRAFFIC_PER_CHAIN = {("fp64", 96, "pair_inv"): 57.6e6, ("df64", 96, "pair_inv"): 57.6e6,
-                              ("mixed32", 96, "pair_inv"): 16.4e6}
+MEASURED_TRAFFIC_PER_CHAIN = {("fp64", 96, "pair_inv"): 57.6e6, ("df64", 96, "pair_inv"): 57.5e6,
+                              ("mixed32", 96, "pair_inv"): 15.4e6}
 
 
 def measured_traffic(form, n, kernel, band_block, chains_per_launch):
@@ -179,6 +179,12 @@ def measured_traffic(form, n, kernel, band_block, chains_per_launch):
     if per is None or band_block != 8:
         return None
     return per * chains_per_launch
+
+
+def pair_loop_rate(pairs, res, steps):
+    """Pairs per second of the pair passes alone (forward, column, inverse; device time)."""
+    ms = sum(res["phase_ms"].get(k, 0.0) for k in ("pair_fwd", "pair_col", "pair_inv")) / steps
+    return pairs / (ms * 1e-3) if ms > 0 else None
 
 
 def roofline(form, plan, res, steps, peaks, peak_src, band_block=16):
@@ -605,6 +611,7 @@ def main():
                  "roofline": roofline("mixed32", planm, resm, args.steps, peaks, peak_src,
                                       tunedm["band_block"] if tunedm else 16),
                  "phase_ms_per_step": {k: v / args.steps for k, v in resm["phase_ms"].items()},
+                 "pair_loop_pairs_per_s": pair_loop_rate(pm, resm, args.steps),
                  "gpu_launches": resm["launches"], "clocks": resm["clocks"], "tuned": tunedm}
         planm.close()
         del psim
@@ -631,6 +638,7 @@ def main():
               "roofline": roofline("df64", pland, resd, args.steps, peaks, peak_src,
                                    tunedd["band_block"] if tunedd else 16),
               "phase_ms_per_step": {k: v / args.steps for k, v in resd["phase_ms"].items()},
+              "pair_loop_pairs_per_s": pair_loop_rate(pd, resd, args.steps),
               "gpu_launches": resd["launches"], "clocks": resd["clocks"], "tuned": tunedd}
         pland.close()
         del psid
@@ -674,6 +682,7 @@ def main():
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
         "phase_ms_per_step": {k: v / args.steps for k, v in res["phase_ms"].items()},
+        "pair_loop_pairs_per_s": pair_loop_rate(pairs, res, args.steps),
         "tuned": tuned,
         "mixed32": mixed,
         "df64": df,
