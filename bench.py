@@ -133,7 +133,7 @@ def time_form(plan, psi, occ, steps, warmup, want_dex=False, rank=0, world=1):
         else:
             import torch.distributed as dist
             plan.apply_shard(psi, occ, rank, world, vpsi, True, want_dex)
-            dist.all_reduce(vpsi)
+            dist.all_reduce(torch.view_as_real(vpsi))
 
     for _ in range(warmup):
         step()
