@@ -189,6 +189,18 @@ fock_status fock_plan_set_band_block(fock_plan_t plan, int band_block);
 /* Bytes of device memory the plan holds (tables + workspace).  bytes: host. */
 fock_status fock_plan_device_bytes(fock_plan_t plan, int64_t* bytes);
 
+/* Deterministic accumulation (enable != 0; FP64 and double-float plans): the
+ * V_x psi accumulators are summed exactly in 64-bit fixed point (integer
+ * atomics; the scale 2^s is set per call from a bound on the sums of absolute
+ * values, |W_t(r)| <= ||v||_2 ||psi_t||_2 sum_s |f_s| max|psi_s|^2 / sqrt(Ntot),
+ * that leaves them two bits of headroom) and the per-pair energies are summed in a
+ * fixed order, so fock_apply, fock_apply_shard and fock_apply_fixed give
+ * bitwise identical results run to run and for every chain batch.  The
+ * rounding of each contribution to the fixed-point grid adds at most
+ * nb * 2^-(s+1) per accumulator.  Default off.  Errors: INVALID_ARG (mixed
+ * plans). */
+fock_status fock_plan_set_deterministic(fock_plan_t plan, int enable);
+
 /* Columns of the stored half spectrum (N x 2(N/2+1) per plane, both pairs of a
  * chain) that the pair-density ball |G| <= 2 Gmax reaches and the column pass
  * transforms (`kept`), out of `total`.  Host outputs; either may be NULL. */

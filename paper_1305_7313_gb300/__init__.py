@@ -39,6 +39,7 @@ from ._lib import (  # noqa: F401
     fock_schedule,
     fock_plan_create,
     fock_plan_columns,
+    fock_plan_set_deterministic,
     fock_plan_device_bytes,
     fock_plan_gvectors,
     fock_plan_npw,

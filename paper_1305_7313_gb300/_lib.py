@@ -81,6 +81,7 @@ _SIGNATURES = {
     "fock_plan_set_batch": [_vp, ctypes.c_int],
     "fock_plan_device_bytes": [_vp, _c_i64_p],
     "fock_plan_columns": [_vp, _c_i64_p, _c_i64_p],
+    "fock_plan_set_deterministic": [_vp, ctypes.c_int],
     "fock_plan_set_timing": [_vp, ctypes.c_int],
     "fock_plan_stats": [_vp, ctypes.POINTER(FockStats)],
     "fock_apply": [_vp, _vp, ctypes.c_int, _c_dbl_p, _vp, _c_dbl_p, _c_dbl_p, _vp],
@@ -260,6 +261,11 @@ def fock_plan_device_bytes(plan):
     n = ctypes.c_int64()
     _check(load().fock_plan_device_bytes(plan, ctypes.byref(n)), plan)
     return n.value
+
+
+def fock_plan_set_deterministic(plan, enable=True):
+    """Exact fixed-point accumulation and fixed-order energy sums (FP64 and double-float plans)."""
+    _check(load().fock_plan_set_deterministic(plan, 1 if enable else 0), plan)
 
 
 def fock_plan_columns(plan):

@@ -47,6 +47,10 @@ struct DevPlan {
   const int* ncol;
   const int* colmap;
   int ncta_col;
+  // deterministic accumulation: W holds 64-bit fixed point scaled by det_scale[0]
+  // (= 2^s), the column pass stores per-CTA energy partials at [pair * ncta_col + cta]
+  int det;
+  const double* det_scale;
   // Brillouin-zone sampling: full-grid tables [nq][N][N][N] of v(G + q)
   const void* vtabq;      // v / Ntot in the working precision
   const double* vtabq64;  // v in FP64
@@ -142,6 +146,18 @@ struct PlanView {
 };
 bool plan_view(struct ::fock_plan* plan, PlanView* out);
 void plan_set_error(struct ::fock_plan* plan, const char* msg);
+
+// Deterministic accumulation.  Per band b of psi (real-space, type code prec):
+// stats[2b] = max |psi_b|, stats[2b+1] = sum psi_b^2; then the fixed-point scale
+// [2^s, 2^-s] into scale from the bound of the header (vnorm = ||v||_2 over the
+// grid, occupations of the nsrc source bands); W (int64 fixed point) to double
+// in place; per-pair sums of the per-CTA energy partials in a fixed order.
+cudaError_t launch_orbital_stats(int prec, const void* psi, int nbands, int64_t ntot, double* stats,
+                                 cudaStream_t s);
+cudaError_t launch_det_scale(const double* stats, int nbands, const double* occ, int nsrc, double vnorm,
+                             int64_t ntot, double* scale, cudaStream_t s);
+cudaError_t launch_det_to_double(void* w, int64_t n, const double* scale, cudaStream_t s);
+cudaError_t launch_det_pair_sums(const double* part, int npairs, int ncta, double* out, cudaStream_t s);
 
 // E = scale * sum_p f_i f_j (1 or 2) e_p over the pairs; out[0] = E, out[1] = dE.
 cudaError_t launch_energy_reduce(const int2* pairs, int npairs, const double* occ,

@@ -428,6 +428,41 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
   pair_fwd_task<T, N, kMaxThreads>(g, psi, ch, H + (int64_t)blockIdx.y * g.hsize, blockIdx.x, smem_raw);
 }
 
+// Publish a CTA's energy partials (thread 0): atomically into the pair slots,
+// or, in deterministic mode, into slot [pair * ncta_col + cta] for a sum in a
+// fixed order afterwards.
+__device__ __forceinline__ void put_energies(const DevPlan& g, const Chain& ch, int cta, const double acc[4],
+                                             bool want_d, double* epair, double* dpair) {
+  if (g.det) {
+    const int64_t nc = g.ncta_col;
+    if (ch.pa >= 0) epair[ch.pa * nc + cta] = acc[0];
+    if (ch.pb >= 0) epair[ch.pb * nc + cta] = acc[1];
+    if (want_d) {
+      if (ch.pa >= 0) dpair[ch.pa * nc + cta] = acc[2];
+      if (ch.pb >= 0) dpair[ch.pb * nc + cta] = acc[3];
+    }
+    return;
+  }
+  if (ch.pa >= 0) atomicAdd(&epair[ch.pa], acc[0]);
+  if (ch.pb >= 0) atomicAdd(&epair[ch.pb], acc[1]);
+  if (want_d) {
+    if (ch.pa >= 0) atomicAdd(&dpair[ch.pa], acc[2]);
+    if (ch.pb >= 0) atomicAdd(&dpair[ch.pb], acc[3]);
+  }
+}
+
+// Deterministic accumulation: one contribution as 64-bit fixed point (scale
+// 2^s), added with an integer atomic (exact, so the order does not matter).
+__device__ __forceinline__ void det_add(double* p, double v, double scale) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)__double2ll_rn(v * scale));
+}
+__device__ __forceinline__ void det_add(double* p, df64 v, double scale) {
+  const float sf = (float)scale;  // a power of two, exact in float
+  const long long q = __float2ll_rn(v.hi * sf) + __float2ll_rn(v.lo * sf);
+  atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)q);
+}
+__device__ __forceinline__ void det_add(float*, float, double) {}  // not offered for the mixed form
+
 // Line code of the column pass: (k2 << 16) | (s << 15) | k3, or -1 (no line).
 __device__ __forceinline__ int line_k2(int code) { return code >> 16; }
 __device__ __forceinline__ int line_s(int code) { return (code >> 15) & 1; }
@@ -550,12 +585,7 @@ __device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __rest
       const double ntot = double(g.ntot);  // the energy table holds v / Ntot
       const double acc[4] = {to_double(accd[0]) * ntot, to_double(accd[1]) * ntot, to_double(accd[2]),
                              to_double(accd[3])};
-      if (ch.pa >= 0) atomicAdd(&epair[ch.pa], acc[0]);
-      if (ch.pb >= 0) atomicAdd(&epair[ch.pb], acc[1]);
-      if (want_d) {
-        if (ch.pa >= 0) atomicAdd(&dpair[ch.pa], acc[2]);
-        if (ch.pb >= 0) atomicAdd(&dpair[ch.pb], acc[3]);
-      }
+      put_energies(g, ch, cta, acc, want_d, epair, dpair);
     }
   }
   fft_lines<df64, N, +1, NC, G::TLC, 1, NC, MAXT>(S, tw);  // inverse along k1
@@ -659,14 +689,7 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
       for (int k = 0; k < 4; ++k) acc[k] = ((double)hi[k] + (double)lo[k]) * (k < 2 ? ntot : 1.0);
     }
   }
-  if (threadIdx.x == 0) {
-    if (ch.pa >= 0) atomicAdd(&epair[ch.pa], acc[0]);
-    if (ch.pb >= 0) atomicAdd(&epair[ch.pb], acc[1]);
-    if (want_d) {
-      if (ch.pa >= 0) atomicAdd(&dpair[ch.pa], acc[2]);
-      if (ch.pb >= 0) atomicAdd(&dpair[ch.pb], acc[3]);
-    }
-  }
+  if (threadIdx.x == 0) put_energies(g, ch, cta, acc, want_d, epair, dpair);
 }
 
 // One task of the column pass: the NC lines `cta` of the column map for chain
@@ -844,6 +867,8 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
       }
     }
   } else {
+    const bool det = g.det != 0;
+    const double dscale = det ? g.det_scale[0] : 0.0;
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
       const int i2 = e / N, i3 = e - i2 * N;
       const C z = Q[i2 * NCP + i3];
@@ -857,7 +882,8 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
 #pragma unroll
         for (int k = r + 1; k < 4; ++k)
           if (into[k] == r) a += c[k];
-        atomic_add_real(wt[r] + e, a);
+        if (det) det_add(wt[r] + e, a, dscale);
+        else atomic_add_real(wt[r] + e, a);
       }
     }
   }

@@ -87,6 +87,15 @@ struct fock_plan {
   double* d_dvtab64 = nullptr;
   int* d_ncol = nullptr;
   int* d_colmap = nullptr;
+  // deterministic accumulation (fock_plan_set_deterministic)
+  bool det = false;
+  double vnorm = 0.0;          // ||v||_2 over the whole grid
+  double* d_stats = nullptr;   // [2 * det_nb_cap] per-band max |psi| and sum psi^2
+  double* d_scale = nullptr;   // [2] fixed-point scale 2^s and 2^-s
+  double* d_epart = nullptr;   // [det_npair_cap * ncta_col] per-CTA energy partials
+  double* d_dpart = nullptr;
+  int det_nb_cap = 0;
+  int det_npair_cap = 0;
   int64_t kept_columns = 0;  // lines of the column map (both pairs)
   double* d_result = nullptr;
   double* h_result = nullptr;  // pinned
@@ -393,6 +402,39 @@ fock_status validate_apply(fock_plan* p, const void* psiG, int nb, const void* o
   return check_device(p);
 }
 
+// Deterministic mode: buffers for nbands real-space bands and npairs pairs.
+fock_status det_buffers(fock_plan* p, int nbands, int npairs) {
+  if (nbands > p->det_nb_cap) {
+    cudaFree(p->d_stats);
+    p->d_stats = nullptr;
+    p->det_nb_cap = 0;
+    FOCK_CUDA(p, dev_alloc(&p->d_stats, sizeof(double) * 2 * nbands));
+    p->det_nb_cap = nbands;
+  }
+  if (!p->d_scale) FOCK_CUDA(p, dev_alloc(&p->d_scale, sizeof(double) * 2));
+  if (npairs > p->det_npair_cap) {
+    cudaFree(p->d_epart);
+    cudaFree(p->d_dpart);
+    p->d_epart = p->d_dpart = nullptr;
+    p->det_npair_cap = 0;
+    const size_t n = (size_t)npairs * (size_t)p->dp.ncta_col;
+    FOCK_CUDA(p, dev_alloc(&p->d_epart, sizeof(double) * n));
+    FOCK_CUDA(p, dev_alloc(&p->d_dpart, sizeof(double) * n));
+    p->det_npair_cap = npairs;
+  }
+  return FOCK_OK;
+}
+
+// Deterministic mode: the fixed-point scale of this call from the real-space
+// bands [0, nbands) (sources: the first nsrc, occupations in ws.occ).
+fock_status det_prepare(fock_plan* p, int nbands, int nsrc, DevPlan* dp, cudaStream_t s) {
+  FOCK_CUDA(p, fockx::launch_orbital_stats(p->ops->prec, p->ws.psi, nbands, p->dp.ntot, p->d_stats, s));
+  FOCK_CUDA(p, fockx::launch_det_scale(p->d_stats, nbands, p->ws.occ, nsrc, p->vnorm, p->dp.ntot, p->d_scale, s));
+  dp->det = 1;
+  dp->det_scale = p->d_scale;
+  return FOCK_OK;
+}
+
 fock_status apply_impl(fock_plan* p, const void* psiG, int nb, const double* occ, int shard,
                        int nshards, void* vpsiG, double* ex, double* dex, fock_stream_t stream) {
   fock_status st = validate_apply(p, psiG, nb, vpsiG);
@@ -434,6 +476,16 @@ fock_status apply_impl(fock_plan* p, const void* psiG, int nb, const double* occ
 
   DevPlan dp = p->dp;
   if (!dex) dp.dvtab64 = nullptr;  // skip the dE/domega partials nobody asked for
+  double* ep = p->ws.epair;
+  double* dpp = p->ws.dpair;
+  if (p->det) {
+    st = det_buffers(p, nb, npairs);
+    if (st != FOCK_OK) return st;
+    st = det_prepare(p, nb, nb, &dp, s);
+    if (st != FOCK_OK) return st;
+    ep = p->d_epart;
+    dpp = p->d_dpart;
+  }
   const int nch = (int)p->chains.size();
   int c0 = 0, c1 = 0;
   shard_range(nch, shard, nshards, &c0, &c1);
@@ -449,12 +501,20 @@ fock_status apply_impl(fock_plan* p, const void* psiG, int nb, const double* occ
     }
     {
       PhaseScope ps(p, FOCK_PHASE_PAIR_COL, 1, s);
-      FOCK_CUDA(p, p->ops->pair_col(dp, p->ws.h, ch, cnt, p->ws.epair, p->ws.dpair, s));
+      FOCK_CUDA(p, p->ops->pair_col(dp, p->ws.h, ch, cnt, ep, dpp, s));
     }
     {
       PhaseScope ps(p, FOCK_PHASE_PAIR_INV, 1, s);
       FOCK_CUDA(p, p->ops->pair_inv(dp, p->ws.psi, p->ws.w, p->ws.occT, ch, cnt, p->ws.h, s));
     }
+  }
+  const int p0 = std::min(npairs, 2 * c0), p1 = std::min(npairs, 2 * c1);
+  if (p->det) {
+    FOCK_CUDA(p, fockx::launch_det_to_double(p->ws.w, (int64_t)nb * p->dp.ntot, p->d_scale, s));
+    const int nc = p->dp.ncta_col;
+    FOCK_CUDA(p, fockx::launch_det_pair_sums(p->d_epart + (size_t)p0 * nc, p1 - p0, nc, p->ws.epair + p0, s));
+    if (dp.dvtab64)
+      FOCK_CUDA(p, fockx::launch_det_pair_sums(p->d_dpart + (size_t)p0 * nc, p1 - p0, nc, p->ws.dpair + p0, s));
   }
 
   const int nbat = bands_per_grid_batch(p);
@@ -465,7 +525,6 @@ fock_status apply_impl(fock_plan* p, const void* psiG, int nb, const double* occ
                                    static_cast<double2*>(vpsiG), s));
   }
 
-  const int p0 = std::min(npairs, 2 * c0), p1 = std::min(npairs, 2 * c1);
   const double scale = -0.5 * p->vol / ((double)p->dp.ntot * (double)p->dp.ntot);
   {
     PhaseScope ps(p, FOCK_PHASE_ENERGY, 1, s);
@@ -613,6 +672,16 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
         const int64_t i = ((int64_t)k1 * n + k2) * kh + k3;
         kernel_value(p, g2, &v64[i], &dv64[i]);
       }
+  {
+    double s2 = 0.0;  // ||v||_2^2 over the full grid from the stored half
+    for (int k1 = 0; k1 < n; ++k1)
+      for (int k2 = 0; k2 < n; ++k2)
+        for (int k3 = 0; k3 < kh; ++k3) {
+          const double v = v64[((int64_t)k1 * n + k2) * kh + k3];
+          s2 += (k3 == 0 || 2 * k3 == n ? 1.0 : 2.0) * v * v;
+        }
+    p->vnorm = std::sqrt(s2);
+  }
   // Columns (k2, k3 <= N/2) of the half spectrum a pair density can reach.
   // The product of two sphere orbitals has components only at |G| <= 2 Gmax,
   // so the columns that the ball |G|^2 <= 8 Ecut hits (indices modulo N, so a
@@ -742,6 +811,8 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
   d.ncol = p->d_ncol;
   d.colmap = p->d_colmap;
   d.ncta_col = ncta_col;
+  d.det = 0;  // set per call on a copy when the plan is deterministic
+  d.det_scale = nullptr;
 
   int optin = 0, sms = 0;
   cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
@@ -886,6 +957,14 @@ fock_status fock_plan_reserve(fock_plan_t plan, int nb_max) {
   return ensure_workspace(plan, nb_max, nb_max * (nb_max + 1) / 2);
 }
 
+fock_status fock_plan_set_deterministic(fock_plan_t plan, int enable) {
+  if (!plan) return fail(nullptr, FOCK_ERR_INVALID_ARG, "plan is NULL");
+  if (enable && plan->prec == FOCK_PREC_MIXED32)
+    return fail(plan, FOCK_ERR_INVALID_ARG, "deterministic accumulation is offered for FP64 and double-float plans");
+  plan->det = enable != 0;
+  return FOCK_OK;
+}
+
 fock_status fock_plan_columns(fock_plan_t plan, int64_t* kept, int64_t* total) {
   if (!plan) return fail(nullptr, FOCK_ERR_INVALID_ARG, "plan is NULL");
   if (kept) *kept = plan->kept_columns;
@@ -990,6 +1069,12 @@ fock_status fock_apply_fixed(fock_plan_t plan, const void* phi_G, int nt, void* 
   }
   DevPlan dp = p->dp;
   dp.dvtab64 = nullptr;
+  if (p->det) {
+    st = det_buffers(p, nb + nt, 1);
+    if (st != FOCK_OK) return st;
+    st = det_prepare(p, nb + nt, nb, &dp, s);
+    if (st != FOCK_OK) return st;
+  }
   const int nch = (int)p->chains.size();
   p->stats.chain_batch = p->chain_batch;
   p->stats.chains = nch;
@@ -1010,6 +1095,7 @@ fock_status fock_apply_fixed(fock_plan_t plan, const void* phi_G, int nt, void* 
       FOCK_CUDA(p, p->ops->pair_inv(dp, p->ws.psi, p->ws.w, p->ws.occT, ch, cnt, p->ws.h, s));
     }
   }
+  if (p->det) FOCK_CUDA(p, fockx::launch_det_to_double(w_trial, (int64_t)nt * p->dp.ntot, p->d_scale, s));
   for (int b0 = 0; b0 < nt; b0 += nbat) {
     PhaseScope ps(p, FOCK_PHASE_TO_SPHERE, 3, s);
     FOCK_CUDA(p, p->ops->to_sphere(p->dp, w_trial, nt, b0, std::min(nbat, nt - b0), p->ws.h,
@@ -1091,6 +1177,10 @@ fock_status fock_destroy(fock_plan_t plan) {
   cudaFree(plan->d_dvtab64);
   cudaFree(plan->d_ncol);
   cudaFree(plan->d_colmap);
+  cudaFree(plan->d_stats);
+  cudaFree(plan->d_scale);
+  cudaFree(plan->d_epart);
+  cudaFree(plan->d_dpart);
   cudaFree(plan->d_result);
   if (plan->h_result) cudaFreeHost(plan->h_result);
   delete plan;

@@ -56,6 +56,10 @@ class FockPlan:
     def device_bytes(self):
         return _lib.fock_plan_device_bytes(self.handle)
 
+    def set_deterministic(self, enable=True):
+        """Bitwise reproducible results: exact fixed-point V_x psi sums, fixed-order energies."""
+        _lib.fock_plan_set_deterministic(self.handle, enable)
+
     def columns(self):
         """(kept, total) half-spectrum columns the column pass transforms."""
         return _lib.fock_plan_columns(self.handle)
