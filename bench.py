@@ -462,6 +462,50 @@ def run_cufft_comparison(args, w, nbands=128, chunk=32):
     return out
 
 
+def run_autograd(args):
+    """E_x(psi, omega) forward + backward through the torch.autograd.Function:
+    72^3 grid, L = 20 bohr, Ecut = 12 Ha, 256 bands, erfc kernel (omega = 0.106),
+    complex64 orbitals, mixed form; gradients w.r.t. psi and omega."""
+    import torch
+    from paper_1305_7313_gb300 import FockPlan, synth
+    from paper_1305_7313_gb300.autograd import exchange_energy
+    w = workload("grad_erfc_L20_N72_nb256")
+    if args.nb:
+        w["nb"] = min(w["nb"], args.nb)
+    n = w["N"]
+    from paper_1305_7313_gb300.workloads import cubic_cell
+    cell = cubic_cell(w["L"])
+    with FockPlan(n, cell, w["ecut"], w["kernel"], w["omega"], w["prec"]) as probe:
+        mill = probe.miller
+    c = synth.orbitals(mill, cell, w["nb"], w["seed"])
+    occ = np.full(w["nb"], 2.0)
+    psi = torch.from_numpy(c).to("cuda", torch.complex64).requires_grad_(True)
+    omega = torch.tensor(w["omega"], dtype=torch.float64, requires_grad=True)
+
+    def step():
+        psi.grad = None
+        omega.grad = None
+        e = exchange_energy(psi, occ, n, cell, w["ecut"], w["kernel"], omega, w["prec"])
+        e.backward()
+        return e
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        e = step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    pairs = w["nb"] * (w["nb"] + 1) // 2
+    return {"workload": w["name"], "value": pairs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "pairs": pairs, "dtype": "f32 (complex64 orbitals and gradients, FP64 energy sums)",
+            "e_x": float(e.detach()), "de_domega": float(omega.grad), "grad_psi_norm": float(psi.grad.abs().max())}
+
+
 def cpu_baseline(w, nbands_sample=32):
     """The FP64 oracle on the first `nbands_sample` bands of the workload."""
     import oracle
@@ -523,6 +567,7 @@ def main():
                     help="override the band count of the workloads (small profiling cases)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-kpoints", action="store_true")
+    ap.add_argument("--no-autograd", action="store_true", help="skip the E_x(psi, omega) autograd leg")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--chain-batch", type=int, default=0,
                     help="with --no-tune: chains per pair-pass launch of the Gamma-point forms")
@@ -654,6 +699,11 @@ def main():
         kpoints = run_kpoints(args, peaks, peak_src)
         torch.cuda.empty_cache()
 
+    autograd = None
+    if not args.no_autograd and world == 1:
+        autograd = run_autograd(args)
+        torch.cuda.empty_cache()
+
     cufft = None
     if not args.no_cufft and world == 1:
         cufft = run_cufft_comparison(args, w, args.cufft_bands)
@@ -688,6 +738,7 @@ def main():
         "df64": df,
         "batched": batched,
         "kpoints": kpoints,
+        "autograd": autograd,
         "cufft_comparison": cufft,
     }
     print(json.dumps(line), flush=True)

@@ -22,6 +22,15 @@
 
 namespace fockx {
 
+// One complex value global -> shared without a register (cp.async).
+template <class C>
+__device__ __forceinline__ void cp_async_c(C* dst, const C* src) {
+  static_assert(sizeof(C) == 8 || sizeof(C) == 16, "cp.async copies 8 or 16 bytes");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"((int)sizeof(C)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // X[q] = scatter(c_{band0 + q}) on the sphere of one k point (X zeroed before).
 template <class T>
 __global__ void k_scatter_k(int npw, const int* __restrict__ gidx, int64_t ntot,
@@ -140,22 +149,12 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_COLF, Geo<T, N>::MIN_CTAS)
   const Chain ch = chains[blockIdx.y];
   C* Hc = H + (int64_t)blockIdx.y * g.ntot;
   load_twiddles<T>(tw, g);
-  for (int e0 = threadIdx.x; e0 < N * N; e0 += kLoadUnroll * blockDim.x) {
-    C v[kLoadUnroll];
-#pragma unroll
-    for (int r = 0; r < kLoadUnroll; ++r) {
-      const int e = e0 + r * blockDim.x;
-      if (e < N * N) {
-        const int i1 = e / N, i3 = e - i1 * N;
-        v[r] = Hc[((int64_t)i1 * N + k2) * N + i3];
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < kLoadUnroll; ++r) {
-      const int e = e0 + r * blockDim.x;
-      if (e < N * N) S[e] = v[r];
-    }
+  // the row k2 of every plane i1, copied asynchronously (all in flight at once)
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int i1 = e / N, i3 = e - i1 * N;
+    cp_async_c(S + e, Hc + ((int64_t)i1 * N + k2) * N + i3);
   }
+  cp_async_wait_all();
   __syncthreads();
   fft_lines<T, N, -1, N, G::TLP, 1, N>(S, tw);  // along i1
   const int64_t qoff = (int64_t)ch.pad1 * g.ntot;
@@ -214,22 +213,12 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
   load_twiddles<T>(tw, g);
   const int64_t plane0 = (int64_t)i1 * N * N;
   const C* Hp = H + (int64_t)blockIdx.y * g.ntot + plane0;
-  for (int e0 = threadIdx.x; e0 < N * N; e0 += kLoadUnroll * blockDim.x) {
-    C v[kLoadUnroll];
-#pragma unroll
-    for (int r = 0; r < kLoadUnroll; ++r) {
-      const int e = e0 + r * blockDim.x;
-      if (e < N * N) v[r] = Hp[e];
-    }
-#pragma unroll
-    for (int r = 0; r < kLoadUnroll; ++r) {
-      const int e = e0 + r * blockDim.x;
-      if (e < N * N) {
-        const int k2 = e / N, k3 = e - k2 * N;
-        P[k2 * RP + k3] = v[r];
-      }
-    }
+  // the plane, copied asynchronously into the padded layout
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int k2 = e / N, k3 = e - k2 * N;
+    cp_async_c(P + k2 * RP + k3, Hp + e);
   }
+  cp_async_wait_all();
   __syncthreads();
   fft_lines<T, N, +1, N, G::TLP, 1, RP>(P, tw);  // along k2
   fft_lines<T, N, +1, N, G::TLP, RP, 1>(P, tw);  // along k3
