@@ -317,7 +317,7 @@ def run_batched(args, peaks, peak_src):
             "graph branches of size-specialised launches",
             "systems": [{"N": sy["N"], "L": sy["L"], "nb": sy["nb"]} for sy in systems],
             "value": pairs * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
-            "pairs": pairs, "dtype": "f32", "graph": True, "persistent_launches_per_step": 1,
+            "pairs": pairs, "dtype": "f32", "graph": True, "persistent_launches_per_step": 1 if persistent else 0,
             "gpu_launches_per_step": info["launches"], "persistent_grid": info["grid"],
             "segments": info["segments"], "tasks": info["tasks"],
             "roofline": {"bound": "hbm", "kernel": nbytes_kernel, "achieved": achieved,
