@@ -340,6 +340,33 @@ __device__ __forceinline__ void fft_stage(cplx<T>* base, int t, bool active, con
   __syncthreads();
 }
 
+// The first stage (P = 1, no twiddles) with its inputs taken from a loader
+// (element m of line `line`: load(line, m)) instead of shared memory: the
+// caller's data never pass through shared memory before the transform.
+template <class T, int N, int R, int TL, int ES, int SIGN, class Load>
+__device__ __forceinline__ void fft_stage_first(cplx<T>* base, int t, bool active, int line, const Load& load) {
+  using C = cplx<T>;
+  constexpr int NB = N / R;
+  constexpr int PER = NB / TL;
+  if (active) {
+    C x[PER][R];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int b = t + TL * k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[k][r] = load(line, b + r * NB);
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int b = t + TL * k;
+      Dft<SIGN, T>::template run<R>(x[k]);
+#pragma unroll
+      for (int q = 0; q < R; ++q) base[(b * R + q) * ES] = x[k][q];
+    }
+  }
+  __syncthreads();
+}
+
 template <class T, int N, int SIGN, int TL, int ES, int S, int P, int MAXT>
 __device__ __forceinline__ void fft_stages(cplx<T>* base, int t, bool active, const cplx<T>* tw) {
   constexpr RadixPlan pl = make_radix_plan(N, MAXT, FftTraits<T>::emax);
@@ -348,6 +375,20 @@ __device__ __forceinline__ void fft_stages(cplx<T>* base, int t, bool active, co
     fft_stage<T, N, R, P, TL, ES, SIGN>(base, t, active, tw);
     fft_stages<T, N, SIGN, TL, ES, S + 1, P * R, MAXT>(base, t, active, tw);
   }
+}
+
+// FFT of NLINES lines of length N whose input comes from load(line, m) and
+// whose output lands in shared memory (line l at buf + l*LS, stride ES).
+template <class T, int N, int SIGN, int NLINES, int TL, int LS, int ES, int MAXT, class Load>
+__device__ __forceinline__ void fft_lines_from(cplx<T>* buf, const cplx<T>* tw, const Load& load) {
+  constexpr RadixPlan pl = make_radix_plan(N, MAXT, FftTraits<T>::emax);
+  constexpr int R0 = pl.r[0];
+  const int tid = threadIdx.x;
+  const int line = tid % NLINES;
+  const int t = tid / NLINES;
+  const bool active = t < TL;
+  fft_stage_first<T, N, R0, TL, ES, SIGN>(buf + line * LS, t, active, line, load);
+  fft_stages<T, N, SIGN, TL, ES, 1, R0, MAXT>(buf + line * LS, t, active, tw);
 }
 
 // FFT of NLINES lines of length N in shared memory: line l starts at buf + l*LS,

@@ -36,16 +36,6 @@ __device__ __forceinline__ int freq_of(int k, int n) { return k < (n + 1) / 2 ? 
 // Rounds of global loads each thread issues before storing them to shared
 // memory in the pass prologues (memory-level parallelism).
 constexpr int kLoadUnroll = 4;
-constexpr int kFwdUnroll = 2;  // the forward pass loads four 16-byte vectors per round
-
-// VW consecutive reals in one 16-byte load.
-template <class T> struct alignas(16) Vec16 {
-  static constexpr int W = 16 / (int)sizeof(T);
-  T v[W];
-};
-template <class T> __device__ __forceinline__ Vec16<T> ld16(const T* p) {
-  return *reinterpret_cast<const Vec16<T>*>(p);
-}
 
 // Per working type: the precision code of the plan (0 FP64, 1 mixed FP32,
 // 2 double-float) and the type of the accumulators W.
@@ -377,37 +367,15 @@ __device__ __forceinline__ void pair_fwd_task(const DevPlan& g, const T* __restr
   const T* paj = psi + (int64_t)ch.aj * g.ntot + plane0;
   const T* pbi = psi + (int64_t)(hb ? ch.bi : 0) * g.ntot + plane0;
   const T* pbj = psi + (int64_t)(hb ? ch.bj : 0) * g.ntot + plane0;
-  // 16-byte loads (VW consecutive reals of a row), kFwdUnroll rounds of the
-  // four orbital planes in flight before their shared-memory stores
-  constexpr int VW = Vec16<T>::W;
-  static_assert(N % VW == 0, "plane rows must hold whole 16-byte vectors");
-  for (int e0 = threadIdx.x * VW; e0 < N * N; e0 += kFwdUnroll * blockDim.x * VW) {
-    Vec16<T> a[kFwdUnroll], b[kFwdUnroll], c[kFwdUnroll], d[kFwdUnroll];
-#pragma unroll
-    for (int u = 0; u < kFwdUnroll; ++u) {
-      const int e = e0 + u * blockDim.x * VW;
-      if (e < N * N) {
-        a[u] = ld16(pai + e);
-        b[u] = ld16(paj + e);
-        if (hb) {
-          c[u] = ld16(pbi + e);
-          d[u] = ld16(pbj + e);
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kFwdUnroll; ++u) {
-      const int e = e0 + u * blockDim.x * VW;
-      if (e < N * N) {
-        const int i2 = e / N, i3 = e - i2 * N;
-#pragma unroll
-        for (int j = 0; j < VW; ++j)
-          P[i2 * RP + i3 + j] = cmake<T>(a[u].v[j] * b[u].v[j], hb ? c[u].v[j] * d[u].v[j] : T(0));
-      }
-    }
-  }
-  __syncthreads();
-  fft_plane<T, N, -1, G::TLP, RP, MAXT>(P, tw);  // along i3, then i2
+  // Columns first: the first stage along i2 reads the pair product straight
+  // from the orbital planes (a warp's lines are consecutive columns i3, so the
+  // loads coalesce) and leaves its outputs in shared memory; then the rows.
+  const auto product = [&](int i3, int i2) {
+    const int e = i2 * N + i3;
+    return cmake<T>(pai[e] * paj[e], hb ? pbi[e] * pbj[e] : T(0));
+  };
+  fft_lines_from<T, N, -1, N, G::TLP, 1, RP, MAXT>(P, tw, product);  // along i2
+  fft_lines<T, N, -1, N, G::TLP, RP, 1, MAXT>(P, tw);                // along i3
   C* Hp = Hc + (int64_t)i1 * N * NC;
   for (int e = threadIdx.x; e < N * KH; e += blockDim.x) {
     const int k2 = e / KH, k3 = e - k2 * KH;
