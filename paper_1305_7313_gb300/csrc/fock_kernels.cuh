@@ -448,7 +448,7 @@ constexpr bool kColAsync = true;
 // 96^3: column pass -2..-6% in every form, inverse pass -13% (mixed) and -3%
 // (FP64) but +9% in double-float, whose inverse pass keeps the cp.async staging.
 constexpr bool kFirstStageDirect = true;
-template <class T> constexpr bool inv_first_stage_direct() {
+template <class T> __host__ __device__ constexpr bool inv_first_stage_direct() {
   return kFirstStageDirect && RealTraits<T>::prec != 2;
 }
 
