@@ -104,28 +104,15 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
   const int64_t plane0 = (int64_t)i1 * N * N;
   const C* ua = u + (int64_t)ch.ai * g.ntot + plane0;
   const C* ub = u + (int64_t)ch.aj * g.ntot + plane0;
-  for (int e0 = threadIdx.x; e0 < N * N; e0 += kLoadUnroll * blockDim.x) {
-    C z[kLoadUnroll];
-#pragma unroll
-    for (int r = 0; r < kLoadUnroll; ++r) {
-      const int e = e0 + r * blockDim.x;
-      if (e < N * N) {
-        const C a = ua[e], b = ub[e];
-        z[r] = cmake<T>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);  // conj(a) b
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < kLoadUnroll; ++r) {
-      const int e = e0 + r * blockDim.x;
-      if (e < N * N) {
-        const int i2 = e / N, i3 = e - i2 * N;
-        P[i2 * RP + i3] = z[r];
-      }
-    }
-  }
-  __syncthreads();
-  fft_lines<T, N, -1, N, G::TLP, RP, 1>(P, tw);  // along i3
-  fft_lines<T, N, -1, N, G::TLP, 1, RP>(P, tw);  // along i2
+  // columns first, the first stage reading conj(u_a) u_b straight from global
+  // memory (consecutive columns per warp: coalesced), then the rows
+  const auto product = [&](int i3, int i2) {
+    const int e = i2 * N + i3;
+    const C a = ua[e], b = ub[e];
+    return cmake<T>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);  // conj(a) b
+  };
+  fft_lines_from<T, N, -1, N, G::TLP, 1, RP, kMaxThreads>(P, tw, product);  // along i2
+  fft_lines<T, N, -1, N, G::TLP, RP, 1>(P, tw);                            // along i3
   C* Hp = H + (int64_t)blockIdx.y * g.ntot + plane0;
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
     const int i2 = e / N, i3 = e - i2 * N;
@@ -149,14 +136,10 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_COLF, Geo<T, N>::MIN_CTAS)
   const Chain ch = chains[blockIdx.y];
   C* Hc = H + (int64_t)blockIdx.y * g.ntot;
   load_twiddles<T>(tw, g);
-  // the row k2 of every plane i1, copied asynchronously (all in flight at once)
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int i1 = e / N, i3 = e - i1 * N;
-    cp_async_c(S + e, Hc + ((int64_t)i1 * N + k2) * N + i3);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  fft_lines<T, N, -1, N, G::TLP, 1, N>(S, tw);  // along i1
+  // the row k2 of every plane i1, read by the first stage of the transform
+  // along i1 straight from global memory
+  const auto val = [&](int i3, int i1) { return Hc[((int64_t)i1 * N + k2) * N + i3]; };
+  fft_lines_from<T, N, -1, N, G::TLP, 1, N, kMaxThreads>(S, tw, val);  // along i1
   const int64_t qoff = (int64_t)ch.pad1 * g.ntot;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   if constexpr (sizeof(T) == 8) {
@@ -213,15 +196,11 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
   load_twiddles<T>(tw, g);
   const int64_t plane0 = (int64_t)i1 * N * N;
   const C* Hp = H + (int64_t)blockIdx.y * g.ntot + plane0;
-  // the plane, copied asynchronously into the padded layout
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int k2 = e / N, k3 = e - k2 * N;
-    cp_async_c(P + k2 * RP + k3, Hp + e);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  fft_lines<T, N, +1, N, G::TLP, 1, RP>(P, tw);  // along k2
-  fft_lines<T, N, +1, N, G::TLP, RP, 1>(P, tw);  // along k3
+  // the plane, read by the first stage of the transform along k2 straight from
+  // global memory (consecutive columns k3 per warp), then the rows
+  const auto val = [&](int k3, int k2) { return Hp[k2 * N + k3]; };
+  fft_lines_from<T, N, +1, N, G::TLP, 1, RP, kMaxThreads>(P, tw, val);  // along k2
+  fft_lines<T, N, +1, N, G::TLP, RP, 1>(P, tw);                        // along k3
   const int a = ch.ai, b = ch.aj;
   const bool both = a != b;
   const T fa = occw[a], fb = occw[b];
