@@ -171,7 +171,7 @@ def time_form(plan, psi, occ, steps, warmup, want_dex=False, rank=0, world=1):
 # (profiles/pair_passes_*_96.md); scaled to a launch by its chains, reported
 # only for that band block (the orbital re-reads depend on it).
 MEASURED_TRAFFIC_PER_CHAIN = {("fp64", 96, "pair_inv"): 57.6e6, ("df64", 96, "pair_inv"): 57.5e6,
-                              ("mixed32", 96, "pair_inv"): 15.4e6}
+                              ("mixed32", 96, "pair_inv"): 15.35e6}
 
 
 def measured_traffic(form, n, kernel, band_block, chains_per_launch):
