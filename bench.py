@@ -166,25 +166,22 @@ def time_form(plan, psi, occ, steps, warmup, want_dex=False, rank=0, world=1):
     return dict(ms=ms, phase_ms=phase_ms, launches=launches, stats=plan.stats(), clocks=clk.summary())
 
 
-# DRAM bytes (read + write) per chain of the dominant kernel, from one ncu
-# capture of the 96^3 pair passes at 38 chains per launch and band block 8
+# DRAM bytes (read + write) per chain of the dominant kernel, from ncu captures
+# of the 96^3 pair passes at 38 chains per launch and band blocks 8 and 32
 # (profiles/pair_passes_*_96.md); scaled to a launch by its chains, reported
-# only for that band block (the orbital re-reads depend on it).
-MEASURED_TRAFFIC_PER_CHAIN = {("fp64", 96, "pair_inv"): 57.6e6, ("df64", 96, "pair_inv"): 57.5e6,
-                              ("mixed32", 96, "pair_inv"): 15.35e6}
+# only for a captured band block (the orbital re-reads depend on it).
+MEASURED_TRAFFIC_PER_CHAIN = {
+    ("fp64", 96, "pair_inv", 8): 57.6e6, ("fp64", 96, "pair_inv", 32): 53.3e6,
+    ("df64", 96, "pair_inv", 8): 57.5e6, ("df64", 96, "pair_inv", 32): 53.3e6,
+    ("mixed32", 96, "pair_inv", 8): 15.35e6, ("mixed32", 96, "pair_inv", 32): 26.3e6,
+}
 
 
 def measured_traffic(form, n, kernel, band_block, chains_per_launch):
-    per = MEASURED_TRAFFIC_PER_CHAIN.get((form, n, kernel))
-    if per is None or band_block != 8:
+    per = MEASURED_TRAFFIC_PER_CHAIN.get((form, n, kernel, band_block))
+    if per is None:
         return None
     return per * chains_per_launch
-
-
-def pair_loop_rate(pairs, res, steps):
-    """Pairs per second of the pair passes alone (forward, column, inverse; device time)."""
-    ms = sum(res["phase_ms"].get(k, 0.0) for k in ("pair_fwd", "pair_col", "pair_inv")) / steps
-    return pairs / (ms * 1e-3) if ms > 0 else None
 
 
 def roofline(form, plan, res, steps, peaks, peak_src, band_block=16):
