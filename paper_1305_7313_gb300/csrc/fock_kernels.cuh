@@ -236,14 +236,6 @@ __device__ __forceinline__ void load_twiddles(cplx<T>* tw, const DevPlan& g) {
   for (int t = threadIdx.x; t < g.n; t += blockDim.x) tw[t] = src[t];
 }
 
-// 2D FFT of a plane held with row stride RP: along the last axis, then the
-// middle one.
-template <class T, int N, int SIGN, int TLP, int RP, int MAXT>
-__device__ __forceinline__ void fft_plane(cplx<T>* P, const cplx<T>* tw) {
-  fft_lines<T, N, SIGN, N, TLP, RP, 1, MAXT>(P, tw);
-  fft_lines<T, N, SIGN, N, TLP, 1, RP, MAXT>(P, tw);
-}
-
 // ---------------------------------------------------------------- O(nb) passes
 
 // X[q] = scatter(c_{b0} + i c_{b0+1}) for band pairs q of the batch (X zeroed before).
