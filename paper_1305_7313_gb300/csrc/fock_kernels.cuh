@@ -13,8 +13,13 @@
 //
 // Hot path per chain of two pairs (a = (ai, aj), b = (bi, bj)):
 //   pair_fwd  (plane i1):  z = psi_ai psi_aj + i psi_bi psi_bj, 2D FFT over
-//             (i2, i3), split z = A + iB by Hermitian symmetry (A, B are the
-//             transforms of real planes), store the k3 <= N/2 half of A and B.
+//             (i2, i3) (columns first; the first stage forms z from the orbital
+//             planes in global memory), split z = A + iB by Hermitian symmetry
+//             (A, B are the transforms of real planes), store the kept columns
+//             of the k3 <= N/2 half of A and B.
+//   Every pass reads the first stage of its first transform straight from
+//   global memory (fft_lines_from), so no input is staged in shared memory
+//   (the double-float inverse pass stages its plane with cp.async instead).
 //   pair_col  (NC columns): FFT along i1 of the stored columns a pair density
 //             reaches (DevPlan::colmap: NC = 2 (N/2+1) lines per CTA), energy partials
 //             sum w(k3) v |A|^2 and sum w(k3) v |B|^2 (w = 1 on the k3 = 0, N/2
