@@ -177,6 +177,12 @@ MEASURED_TRAFFIC_PER_CHAIN = {
 }
 
 
+def pair_loop_rate(pairs, res, steps):
+    """Pairs per second of the pair passes alone (forward, column, inverse; device time)."""
+    ms = sum(res["phase_ms"].get(k, 0.0) for k in ("pair_fwd", "pair_col", "pair_inv")) / steps
+    return pairs / (ms * 1e-3) if ms > 0 else None
+
+
 def measured_traffic(form, n, kernel, band_block, chains_per_launch):
     per = MEASURED_TRAFFIC_PER_CHAIN.get((form, n, kernel, band_block))
     if per is None:

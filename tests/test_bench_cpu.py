@@ -25,3 +25,22 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and "3 unique pairs" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_every_function_the_benchmark_calls_is_defined_or_imported():
+    # the GPU legs of bench.py cannot run here; at least their calls must resolve
+    import ast
+    import builtins
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    known = set(dir(builtins))
+    for n in ast.walk(tree):
+        if isinstance(n, (ast.FunctionDef, ast.ClassDef)):
+            known.add(n.name)
+        elif isinstance(n, ast.Import):
+            known.update((a.asname or a.name).split(".")[0] for a in n.names)
+        elif isinstance(n, ast.ImportFrom):
+            known.update(a.asname or a.name for a in n.names)
+        elif isinstance(n, ast.Assign):
+            known.update(t.id for t in n.targets if isinstance(t, ast.Name))
+    called = {n.func.id for n in ast.walk(tree) if isinstance(n, ast.Call) and isinstance(n.func, ast.Name)}
+    assert called <= known, sorted(called - known)
