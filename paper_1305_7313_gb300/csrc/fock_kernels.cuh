@@ -556,29 +556,34 @@ __device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __rest
   }
   {
     df64 accd[4] = {df64(0.f), df64(0.f), df64(0.f), df64(0.f)};
-    for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
-      const int k1 = e / NC, l = e - k1 * NC;
-      const int code = codes[l];
-      if (code < 0) continue;
+    // one line per thread (decoded once), walking k1
+    const int l = threadIdx.x % NC, kstep = blockDim.x / NC;
+    const int code = threadIdx.x < kstep * NC ? codes[l] : -1;
+    if (code >= 0) {
       const int k2 = line_k2(code), s = line_s(code), k3 = line_k3(code);
-      const int vi = (k1 * N + k2) * KH + k3;
-      const bool twice = !(k3 == 0 || 2 * k3 == N);
-      C z = S[e];
-      const df64 a2 = z.x * z.x + z.y * z.y;
-      const df64 v = vt[vi];
-      df64 te = v * a2;
-      if (twice) te = ldexp_pow2(te, 2.0f);
-      if (s) accd[1] += te;
-      else accd[0] += te;
-      if (want_d) {
-        df64 td = dvt[vi] * a2;
-        if (twice) td = ldexp_pow2(td, 2.0f);
-        if (s) accd[3] += td;
-        else accd[2] += td;
+      const float wgt = (k3 == 0 || 2 * k3 == N) ? 1.0f : 2.0f;
+      df64 e_sum(0.f), d_sum(0.f);
+      for (int k1 = threadIdx.x / NC; k1 < N; k1 += kstep) {
+        const int e = k1 * NC + l;
+        const int vi = (k1 * N + k2) * KH + k3;
+        C z = S[e];
+        const df64 a2 = z.x * z.x + z.y * z.y;
+        const df64 v = vt[vi];
+        e_sum += v * a2;
+        if (want_d) d_sum += dvt[vi] * a2;
+        z.x *= v;
+        z.y *= v;
+        S[e] = z;
       }
-      z.x *= v;
-      z.y *= v;
-      S[e] = z;
+      e_sum = ldexp_pow2(e_sum, wgt);
+      d_sum = ldexp_pow2(d_sum, wgt);
+      if (s) {
+        accd[1] = e_sum;
+        accd[3] = d_sum;
+      } else {
+        accd[0] = e_sum;
+        accd[2] = d_sum;
+      }
     }
     block_sum4_df(accd, reinterpret_cast<float*>(red));  // synchronises the CTA
     if (threadIdx.x == 0) {
@@ -618,62 +623,73 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
   const bool want_d = g.dvtab64 != nullptr;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};  // e_a, e_b, d_a, d_b (FP64 terms)
   float acc_f32[4] = {0.f, 0.f, 0.f, 0.f};  // the same from the FP32 terms (mixed form)
+  // one line per thread (decoded once), walking k1
+  const int l = threadIdx.x % NC, kstep = blockDim.x / NC;
+  const int code = threadIdx.x < kstep * NC ? codes[l] : -1;
   if constexpr (RealTraits<T>::prec == 0) {
-    for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
-      const int k1 = e / NC, l = e - k1 * NC;
-      const int code = codes[l];
-      if (code < 0) continue;
+    if (code >= 0) {
       const int k2 = line_k2(code), s = line_s(code), k3 = line_k3(code);
-      const int64_t vi = ((int64_t)k1 * N + k2) * KH + k3;
       const double wgt = (k3 == 0 || 2 * k3 == N) ? 1.0 : 2.0;
-      C z = S[e];
-      const double a2 = z.x * z.x + z.y * z.y;
-      const double v = g.vtab64[vi];
-      const double te = wgt * v * a2;
-      const double td = want_d ? wgt * g.dvtab64[vi] * a2 : 0.0;
-      if (s) {
-        acc[1] += te;
-        acc[3] += td;
-      } else {
-        acc[0] += te;
-        acc[2] += td;
+      const double* v64 = g.vtab64 + k2 * KH + k3;
+      const double* dv64 = g.dvtab64 ? g.dvtab64 + k2 * KH + k3 : nullptr;
+      const double* vs64 = static_cast<const double*>(g.vtab) + k2 * KH + k3;  // v / Ntot
+      double e_sum = 0.0, d_sum = 0.0;
+      for (int k1 = threadIdx.x / NC; k1 < N; k1 += kstep) {
+        const int e = k1 * NC + l;
+        const int vo = k1 * N * KH;
+        C z = S[e];
+        const double a2 = z.x * z.x + z.y * z.y;
+        e_sum += v64[vo] * a2;
+        if (want_d) d_sum += dv64[vo] * a2;
+        const double vs = vs64[vo];
+        z.x *= vs;
+        z.y *= vs;
+        S[e] = z;
       }
-      const double vs = v * g.inv_ntot;
-      z.x *= vs;
-      z.y *= vs;
-      S[e] = z;
+      if (s) {  // explicit selects: a runtime index would put acc in local memory
+        acc[1] = wgt * e_sum;
+        acc[3] = wgt * d_sum;
+      } else {
+        acc[0] = wgt * e_sum;
+        acc[2] = wgt * d_sum;
+      }
     }
   } else {
     const T* vt = static_cast<const T*>(g.vtab);    // v / Ntot
     const T* dvt = static_cast<const T*>(g.dvtab);  // dv/domega
     T accf[4] = {T(0), T(0), T(0), T(0)};
-    for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
-      const int k1 = e / NC, l = e - k1 * NC;
-      const int code = codes[l];
-      if (code < 0) continue;
+    if (code >= 0) {
       const int k2 = line_k2(code), s = line_s(code), k3 = line_k3(code);
-      const int m1 = freq_of(k1, N), m2 = freq_of(k2, N), m3 = freq_of(k3, N);
-      if (m1 * m1 + m2 * m2 + m3 * m3 <= g.msmall2) {
-        if (s == 0 || ch.bi >= 0) small_g_term_fp64<T, N>(g, S, e, k1, k2, k3, s, ch, epair, dpair);
-        continue;
-      }
-      const int vi = (k1 * N + k2) * KH + k3;
+      const int m2 = freq_of(k2, N), m3 = freq_of(k3, N);
+      const int r23 = m2 * m2 + m3 * m3;
       const T wgt = (k3 == 0 || 2 * k3 == N) ? T(1) : T(2);
-      C z = S[e];
-      const T a2 = z.x * z.x + z.y * z.y;
-      const T v = vt[vi];
-      const T te = wgt * v * a2;
-      const T td = want_d ? wgt * dvt[vi] * a2 : T(0);
-      if (s) {
-        accf[1] += te;
-        accf[3] += td;
-      } else {
-        accf[0] += te;
-        accf[2] += td;
+      const T* vl = vt + k2 * KH + k3;
+      const T* dvl = dvt + k2 * KH + k3;
+      T e_sum = T(0), d_sum = T(0);
+      for (int k1 = threadIdx.x / NC; k1 < N; k1 += kstep) {
+        const int e = k1 * NC + l;
+        const int m1 = freq_of(k1, N);
+        if (m1 * m1 + r23 <= g.msmall2) {
+          if (s == 0 || ch.bi >= 0) small_g_term_fp64<T, N>(g, S, e, k1, k2, k3, s, ch, epair, dpair);
+          continue;
+        }
+        const int vo = k1 * N * KH;
+        C z = S[e];
+        const T a2 = z.x * z.x + z.y * z.y;
+        const T v = vl[vo];
+        e_sum += v * a2;
+        if (want_d) d_sum += dvl[vo] * a2;
+        z.x *= v;
+        z.y *= v;
+        S[e] = z;
       }
-      z.x *= v;
-      z.y *= v;
-      S[e] = z;
+      if (s) {
+        accf[1] = wgt * e_sum;
+        accf[3] = wgt * d_sum;
+      } else {
+        accf[0] = wgt * e_sum;
+        accf[2] = wgt * d_sum;
+      }
     }
     // per-thread FP32 sums of at most N (N+2) / blockDim non-negative terms;
     // the table holds v / Ntot, undone in FP64 after the CTA reduction
