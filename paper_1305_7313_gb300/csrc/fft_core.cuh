@@ -151,13 +151,22 @@ __host__ __device__ constexpr RadixPlan make_radix_plan(int n, int maxt = kMaxTh
 // values take twice the instructions and live registers of a float, so their
 // plans use more threads per line (e.g. 96 = 12 x 4 x 2 with 8 threads per
 // line instead of 12 x 8 with 4).
-template <class T> struct FftTraits { static constexpr int emax = kEmax; };
+// emax: elements a thread may hold across a stage.  fused: the type has a
+// hardware fused multiply-add, so twiddle products are folded into the
+// butterfly sums (Dft::run_tw) instead of being rounded on their own.
+template <class T> struct FftTraits {
+  static constexpr int emax = kEmax;
+  static constexpr bool fused = true;
+};
 
 template <class T> struct CplxOf;
 template <> struct CplxOf<float> { using type = float2; };
 template <> struct CplxOf<double> { using type = double2; };
 template <> struct CplxOf<df64> { using type = cdf64; };
-template <> struct FftTraits<df64> { static constexpr int emax = 12; };
+template <> struct FftTraits<df64> {
+  static constexpr int emax = 12;
+  static constexpr bool fused = false;
+};
 template <class T> using cplx = typename CplxOf<T>::type;
 
 // S * x for S = +1 or -1 (a sign flip, never a multiplication)
@@ -169,6 +178,10 @@ template <int S, class T> __device__ __forceinline__ T sgn(T x) {
 __device__ __forceinline__ float half_of(float x) { return 0.5f * x; }
 __device__ __forceinline__ double half_of(double x) { return 0.5 * x; }
 __device__ __forceinline__ df64 half_of(df64 x) { return ldexp_pow2(x, 0.5f); }
+
+// a * b + c with one rounding
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 template <class T>
 __device__ __forceinline__ cplx<T> cmake(T x, T y) {
@@ -201,11 +214,11 @@ template <int SIGN, class T> struct Dft {
     x[0] = cadd(a, x[1]);
     x[1] = csub(a, x[1]);
   }
-  static __device__ __forceinline__ void r3(C* x) {
+  static __device__ __forceinline__ void r3(C* x) { r3_sd(x, cadd(x[1], x[2]), csub(x[1], x[2])); }
+  // the length-3 DFT from x0, s = x1 + x2 and d = x1 - x2
+  static __device__ __forceinline__ void r3_sd(C* x, C s, C d) {
     constexpr T h0 = T(0.86602540378443864676372317075293618);  // sin(2 pi / 3)
     const T h = sgn<SIGN>(h0);
-    C s = cadd(x[1], x[2]);
-    C d = csub(x[1], x[2]);
     C m = cmake<T>(x[0].x - half_of(s.x), x[0].y - half_of(s.y));
     C u = cmake<T>(-h * d.y, h * d.x);
     x[0] = cadd(x[0], s);
@@ -256,38 +269,141 @@ template <int SIGN, class T> struct Dft {
       return cmake<T>(c * x.x - s * x.y, c * x.y + s * x.x);
     }
   }
-  // R = R1 R2 in registers: R2 DFTs of length R1 over x[R2 n1 + n2], twiddle
-  // w_R^(n2 k1), R1 DFTs of length R2; output k = k1 + R1 k2.
-  template <int R1, int R2, int N2 = 0>
-  static __device__ __forceinline__ void inner(C* x, C* a) {
+  // ---- twiddled inputs, for types with a fused multiply-add (FftTraits::fused).
+  // DFT of (x_0, w_1 x_1, ..., w_{R-1} x_{R-1}): each twiddle product is folded
+  // into the first sum it feeds (a + w x as two fused multiply-adds per
+  // component), and the matching difference is taken as 2 a - (a + w x), which
+  // saves the separate rounding of w x and a quarter of the instructions of the
+  // twiddled sums.
+  // a + w x
+  static __device__ __forceinline__ C cfma(C a, C w, C x) {
+    return cmake<T>(fmadd(w.x, x.x, fmadd(-w.y, x.y, a.x)), fmadd(w.x, x.y, fmadd(w.y, x.x, a.y)));
+  }
+  // 2 a - b
+  static __device__ __forceinline__ C ctwice_sub(C a, C b) {
+    return cmake<T>(fmadd(T(2), a.x, -b.x), fmadd(T(2), a.y, -b.y));
+  }
+  // a - 2 b
+  static __device__ __forceinline__ C csub_twice(C a, C b) {
+    return cmake<T>(fmadd(T(-2), b.x, a.x), fmadd(T(-2), b.y, a.y));
+  }
+  static __device__ __forceinline__ void r2_tw(C& x0, C& x1, C w1) {
+    const C a = cfma(x0, w1, x1);
+    x1 = ctwice_sub(x0, a);
+    x0 = a;
+  }
+  static __device__ __forceinline__ void r3_tw(C* x, C w1, C w2) {
+    const C x1w = cmul(x[1], w1);
+    const C s = cfma(x1w, w2, x[2]);  // w1 x1 + w2 x2
+    r3_sd(x, s, ctwice_sub(x1w, s));
+  }
+  static __device__ __forceinline__ void r4v_tw(C& x0, C& x1, C& x2, C& x3, C w1, C w2, C w3) {
+    const C a = cfma(x0, w2, x2);      // x0 + w2 x2
+    const C b = ctwice_sub(x0, a);     // x0 - w2 x2
+    const C x3w = cmul(x3, w3);
+    const C c = cfma(x3w, w1, x1);     // w1 x1 + w3 x3
+    const C d = cmul_si<SIGN>(csub_twice(c, x3w));  // S i (w1 x1 - w3 x3)
+    x0 = cadd(a, c);
+    x2 = csub(a, c);
+    x1 = cadd(b, d);
+    x3 = csub(b, d);
+  }
+  static __device__ __forceinline__ void r8_tw(C* x, const C* w) {
+    constexpr T c = T(0.70710678118654752440084436210484904);  // cos(pi / 4)
+    C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+    C o0 = cmul(x[1], w[1]), o1 = x[3], o2 = x[5], o3 = x[7];
+    r4v_tw(e0, e1, e2, e3, w[2], w[4], w[6]);
+    r4v_tw(o0, o1, o2, o3, w[3], w[5], w[7]);
+    // x_q = e_q +- exp(SIGN 2 pi i q / 8) o_q, the pi/4 rotations as c * p
+    const C p = cmake<T>(o1.x - sgn<SIGN>(o1.y), o1.y + sgn<SIGN>(o1.x));
+    const C q = cmake<T>(o3.x + sgn<SIGN>(o3.y), sgn<SIGN>(o3.x) - o3.y);
+    const C t2 = cmul_si<SIGN>(o2);
+    x[0] = cadd(e0, o0);
+    x[4] = csub(e0, o0);
+    x[1] = cmake<T>(fmadd(c, p.x, e1.x), fmadd(c, p.y, e1.y));
+    x[5] = cmake<T>(fmadd(-c, p.x, e1.x), fmadd(-c, p.y, e1.y));
+    x[2] = cadd(e2, t2);
+    x[6] = csub(e2, t2);
+    x[3] = cmake<T>(fmadd(-c, q.x, e3.x), fmadd(c, q.y, e3.y));
+    x[7] = cmake<T>(fmadd(c, q.x, e3.x), fmadd(-c, q.y, e3.y));
+  }
+  // W0: x_0 carries a twiddle w_0 too
+  template <int R, bool W0> static __device__ __forceinline__ void run_tw(C* x, const C* w) {
+    if constexpr (W0) x[0] = cmul(x[0], w[0]);
+    if constexpr (R == 2) r2_tw(x[0], x[1], w[1]);
+    else if constexpr (R == 3) r3_tw(x, w[1], w[2]);
+    else if constexpr (R == 4) r4v_tw(x[0], x[1], x[2], x[3], w[1], w[2], w[3]);
+    else if constexpr (R == 8) r8_tw(x, w);
+    else if constexpr (R == 6) composite<2, 3, true>(x, w);
+    else if constexpr (R == 9) composite<3, 3, true>(x, w);
+    else if constexpr (R == 12) composite<4, 3, true>(x, w);
+    else composite<4, 4, true>(x, w);  // R == 16
+  }
+
+  // w_R^m is a quarter turn (a sign change or a swap, no arithmetic)
+  static __host__ __device__ constexpr bool quarter_turn(int m, int R) { return (4 * (((m % R) + R) % R)) % R == 0; }
+  // every twiddle w_R^(n2 k1), 0 < n2 < R2, needs arithmetic
+  template <int R2, int R> static __host__ __device__ constexpr bool all_general(int k1) {
+    for (int n2 = 1; n2 < R2; ++n2)
+      if (quarter_turn(n2 * k1, R)) return false;
+    return true;
+  }
+
+  // R = R1 R2 in registers: R2 DFTs of length R1 over x[R2 n1 + n2] (TW: with
+  // the stage twiddles w[R2 n1 + n2] on their inputs), twiddle w_R^(n2 k1),
+  // R1 DFTs of length R2; output k = k1 + R1 k2.
+  template <int R1, int R2, bool TW, int N2 = 0>
+  static __device__ __forceinline__ void inner(C* x, const C* w, C* a) {
     if constexpr (N2 < R2) {
       C t[R1];
 #pragma unroll
       for (int n1 = 0; n1 < R1; ++n1) t[n1] = x[R2 * n1 + N2];
-      run<R1>(t);
-      twiddle_row<R1, R2, N2, 0>(t, a);
-      inner<R1, R2, N2 + 1>(x, a);
-    }
-  }
-  template <int R1, int R2, int N2, int K1>
-  static __device__ __forceinline__ void twiddle_row(const C* t, C* a) {
-    if constexpr (K1 < R1) {
-      a[N2 * R1 + K1] = twiddle<N2 * K1, R1 * R2>(t[K1]);
-      twiddle_row<R1, R2, N2, K1 + 1>(t, a);
-    }
-  }
-  template <int R1, int R2> static __device__ __forceinline__ void composite(C* x) {
-    C a[R1 * R2];
-    inner<R1, R2>(x, a);
+      if constexpr (TW) {
+        C wt[R1];
 #pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) {
+        for (int n1 = 0; n1 < R1; ++n1) wt[n1] = w[R2 * n1 + N2];
+        run_tw<R1, (N2 > 0)>(t, wt);
+      } else {
+        run<R1>(t);
+      }
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) a[N2 * R1 + k1] = t[k1];
+      inner<R1, R2, TW, N2 + 1>(x, w, a);
+    }
+  }
+  template <int R1, int R2, int K1 = 0>
+  static __device__ __forceinline__ void outer(const C* a, C* x) {
+    if constexpr (K1 < R1) {
       C t[R2];
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) t[n2] = a[n2 * R1 + k1];
-      run<R2>(t);
+      for (int n2 = 0; n2 < R2; ++n2) t[n2] = a[n2 * R1 + K1];
+      if constexpr (FftTraits<T>::fused && K1 > 0 && all_general<R2, R1 * R2>(K1)) {
+        C wc[R2];
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) x[k1 + R1 * k2] = t[k2];
+        for (int n2 = 0; n2 < R2; ++n2)
+          wc[n2] = cmake<T>(T(ct_trig(n2 * K1, R1 * R2, false)), T(SIGN * ct_trig(n2 * K1, R1 * R2, true)));
+        run_tw<R2, false>(t, wc);
+      } else {
+        twiddle_col<R1, R2, K1, 1>(t);
+        run<R2>(t);
+      }
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) x[K1 + R1 * k2] = t[k2];
+      outer<R1, R2, K1 + 1>(a, x);
     }
+  }
+  template <int R1, int R2, int K1, int N2>
+  static __device__ __forceinline__ void twiddle_col(C* t) {
+    if constexpr (N2 < R2) {
+      t[N2] = twiddle<N2 * K1, R1 * R2>(t[N2]);
+      twiddle_col<R1, R2, K1, N2 + 1>(t);
+    }
+  }
+  template <int R1, int R2, bool TW = false>
+  static __device__ __forceinline__ void composite(C* x, const C* w = nullptr) {
+    C a[R1 * R2];
+    inner<R1, R2, TW>(x, w, a);
+    outer<R1, R2>(a, x);
   }
   template <int R> static __device__ __forceinline__ void run(C* x) {
     if constexpr (R == 2) r2(x);
@@ -323,15 +439,26 @@ __device__ __forceinline__ void fft_stage(cplx<T>* base, int t, bool active, con
     for (int k = 0; k < PER; ++k) {
       const int b = t + TL * k;
       const int kk = b % P;
-      if (P > 1) {
+      if constexpr (P > 1 && FftTraits<T>::fused) {
+        C w[R];
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          C w = tw[r * kk * TWS];
-          if (SIGN > 0) w.y = -w.y;
-          x[k][r] = cmul(x[k][r], w);
+          w[r] = tw[r * kk * TWS];
+          if (SIGN > 0) w[r].y = -w[r].y;
         }
+        w[0] = w[1];  // not read: x_0 carries no twiddle
+        Dft<SIGN, T>::template run_tw<R, false>(x[k], w);
+      } else {
+        if constexpr (P > 1) {
+#pragma unroll
+          for (int r = 1; r < R; ++r) {
+            C w = tw[r * kk * TWS];
+            if (SIGN > 0) w.y = -w.y;
+            x[k][r] = cmul(x[k][r], w);
+          }
+        }
+        Dft<SIGN, T>::template run<R>(x[k]);
       }
-      Dft<SIGN, T>::template run<R>(x[k]);
       const int j = (b - kk) * R + kk;
 #pragma unroll
       for (int q = 0; q < R; ++q) base[(j + q * P) * ES] = x[k][q];
