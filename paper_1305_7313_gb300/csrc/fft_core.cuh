@@ -163,6 +163,10 @@ template <class T> struct CplxOf;
 template <> struct CplxOf<float> { using type = float2; };
 template <> struct CplxOf<double> { using type = double2; };
 template <> struct CplxOf<df64> { using type = cdf64; };
+template <> struct FftTraits<double> {
+  static constexpr int emax = 12;
+  static constexpr bool fused = true;
+};
 template <> struct FftTraits<df64> {
   static constexpr int emax = 12;
   static constexpr bool fused = false;

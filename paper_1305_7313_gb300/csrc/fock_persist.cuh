@@ -27,16 +27,17 @@
 
 namespace fockx {
 
-constexpr int kPersistMaxT = 416;  // CTA size: enough for the 96^3 column pass
+// CTA size: enough for the 96^3 column pass (4 threads per line in FP32, 8 in FP64)
+template <class T> constexpr int kPersistMaxT = sizeof(T) == 8 ? 800 : 416;
 
 template <class T>
 struct PersistGeo {
   // largest dynamic shared memory over the grid sizes the persistent kernel runs
   static constexpr size_t smem_of(size_t a, size_t b) { return a > b ? a : b; }
   static constexpr size_t SMEM = smem_of(
-      smem_of(smem_of(Geo<T, 96, kPersistMaxT>::SMEM_PLANE, Geo<T, 96, kPersistMaxT>::SMEM_COLH),
-              smem_of(Geo<T, 72, kPersistMaxT>::SMEM_PLANE, Geo<T, 72, kPersistMaxT>::SMEM_COLH)),
-      smem_of(Geo<T, 96, kPersistMaxT>::SMEM_INV, Geo<T, 72, kPersistMaxT>::SMEM_INV));
+      smem_of(smem_of(Geo<T, 96, kPersistMaxT<T>>::SMEM_PLANE, Geo<T, 96, kPersistMaxT<T>>::SMEM_COLH),
+              smem_of(Geo<T, 72, kPersistMaxT<T>>::SMEM_PLANE, Geo<T, 72, kPersistMaxT<T>>::SMEM_COLH)),
+      smem_of(Geo<T, 96, kPersistMaxT<T>>::SMEM_INV, Geo<T, 72, kPersistMaxT<T>>::SMEM_INV));
   static constexpr int MIN_CTAS = sizeof(T) == 4 ? 2 : 1;  // shared memory allows 2 in FP32
 };
 
@@ -76,11 +77,11 @@ __device__ __noinline__ void persist_task(const SysDesc* __restrict__ sys, int s
   const SysDesc& sd = sys[sysi];
   const Chain ch = sd.chains[chain];
   if constexpr (KIND == 0) {
-    pair_fwd_task<T, N, kPersistMaxT>(sd.g, static_cast<const T*>(sd.psi), ch, Hc, idx, smem);
+    pair_fwd_task<T, N, kPersistMaxT<T>>(sd.g, static_cast<const T*>(sd.psi), ch, Hc, idx, smem);
   } else if constexpr (KIND == 1) {
-    pair_col_task<T, N, kPersistMaxT>(sd.g, Hc, ch, idx, sd.epair, sd.dpair, smem);
+    pair_col_task<T, N, kPersistMaxT<T>>(sd.g, Hc, ch, idx, sd.epair, sd.dpair, smem);
   } else {
-    pair_inv_task<T, N, kPersistMaxT>(sd.g, static_cast<const T*>(sd.psi), static_cast<T*>(sd.W),
+    pair_inv_task<T, N, kPersistMaxT<T>>(sd.g, static_cast<const T*>(sd.psi), static_cast<T*>(sd.W),
                                       static_cast<const T*>(sd.occT), ch, Hc, idx, smem);
   }
 }
@@ -100,7 +101,7 @@ __device__ __forceinline__ void run_task(const SysDesc* sys, const Segment& sg, 
 // counters[0]: next ticket; counters[1]: error word (segment + 1 of the wait that
 // gave up); counters[2 + s]: finished tasks of segment s.
 template <class T>
-__global__ void __launch_bounds__(kPersistMaxT, PersistGeo<T>::MIN_CTAS)
+__global__ void __launch_bounds__(kPersistMaxT<T>, PersistGeo<T>::MIN_CTAS)
     k_pair_persistent(const SysDesc* __restrict__ sys, const Segment* __restrict__ seg, int nseg,
                       int ntasks, unsigned* counters, unsigned char* hring, size_t slot_bytes,
                       unsigned long long limit_ns) {
@@ -158,13 +159,13 @@ struct PersistLaunch {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PersistGeo<T>::SMEM);
   }
   static cudaError_t occupancy(int* ctas_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_pair_persistent<T>, kPersistMaxT,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_pair_persistent<T>, kPersistMaxT<T>,
                                                          PersistGeo<T>::SMEM);
   }
   static cudaError_t launch(int grid, const SysDesc* sys, const Segment* seg, int nseg, int ntasks,
                             unsigned* counters, unsigned char* hring, size_t slot_bytes,
                             unsigned long long limit_ns, cudaStream_t s) {
-    k_pair_persistent<T><<<grid, kPersistMaxT, PersistGeo<T>::SMEM, s>>>(sys, seg, nseg, ntasks, counters,
+    k_pair_persistent<T><<<grid, kPersistMaxT<T>, PersistGeo<T>::SMEM, s>>>(sys, seg, nseg, ntasks, counters,
                                                                       hring, slot_bytes, limit_ns);
     return cudaGetLastError();
   }
