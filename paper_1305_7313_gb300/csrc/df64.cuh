@@ -59,6 +59,8 @@ __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
   return df64(h, e - (h - p));
 }
 
+// equal values (a normalised pair represents a value in one way only)
+__device__ __forceinline__ bool operator==(df64 a, df64 b) { return a.hi == b.hi && a.lo == b.lo; }
 __device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
 __device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
 __device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = a * b; }

@@ -905,12 +905,21 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
   } else {
     const bool det = g.det != 0;
     const double dscale = det ? g.det_scale[0] : 0.0;
+    // both sources of each pair equally occupied (the usual case): -f phi is
+    // formed once per pair and point, one multiplication fewer per update
+    const bool same_f = f[0] == f[1] && f[2] == f[3];
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
       const int i2 = e / N, i3 = e - i2 * N;
       const C z = Q[i2 * NCP + i3];
       T c[4];
+      if (same_f) {
+        const T ga = -f[0] * z.x, gb = -f[2] * z.y;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) c[k] = tgt[k] < 0 ? T(0) : -f[k] * ps[k][e] * (k < 2 ? z.x : z.y);
+        for (int k = 0; k < 4; ++k) c[k] = tgt[k] < 0 ? T(0) : ps[k][e] * (k < 2 ? ga : gb);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k] = tgt[k] < 0 ? T(0) : -f[k] * ps[k][e] * (k < 2 ? z.x : z.y);
+      }
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         if (tgt[r] < 0 || into[r] != r) continue;
