@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_COLF, Geo<T, N>::MIN_CTAS)
 
 // Inverse plane pass of a pair and the W updates.
 template <class T, int N>
-__global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
+__global__ void __launch_bounds__(Geo<T, N>::THR_PLANE, Geo<T, N>::MIN_CTAS_KINV)
     k_kpair_inv(DevPlan g, const cplx<T>* __restrict__ u, cplx<T>* __restrict__ W,
                 const T* __restrict__ occw, const Chain* __restrict__ chains, const cplx<T>* __restrict__ H) {
   using C = cplx<T>;
