@@ -22,15 +22,6 @@
 
 namespace fockx {
 
-// One complex value global -> shared without a register (cp.async).
-template <class C>
-__device__ __forceinline__ void cp_async_c(C* dst, const C* src) {
-  static_assert(sizeof(C) == 8 || sizeof(C) == 16, "cp.async copies 8 or 16 bytes");
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"((int)sizeof(C)) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // X[q] = scatter(c_{band0 + q}) on the sphere of one k point (X zeroed before).
 template <class T>
 __global__ void k_scatter_k(int npw, const int* __restrict__ gidx, int64_t ntot,
