@@ -152,16 +152,21 @@ def test_invalid_calls_fail_cleanly():
     assert abs(ex - eref) <= TOL64 * abs(eref)
 
 
+@pytest.mark.parametrize("prec,tol_v,tol_e", [(_lib.PREC_FP64, TOL64, TOL64), (_lib.PREC_DF64, TOL64, TOL64),
+                                              (_lib.PREC_MIXED32, TOL32_V, TOL32_E)],
+                         ids=["fp64", "df64", "mixed32"])
 @pytest.mark.parametrize("N", [8, 12, 16, 36, 64, 72])
-def test_double_float_form_on_every_other_compiled_size(N):
-    # the grid sizes the tests above do not reach (24, 32, 48 are covered):
-    # cells with L = 0.3 N bohr and Ecut = 6 Ha, a few bands, FP64 tolerance
+def test_every_other_compiled_size_in_every_form(N, prec, tol_v, tol_e):
+    # the grid sizes the tests above do not reach (24, 32, 48 are covered),
+    # each with its own radix plan (8 and 12 in one stage, 16 = 4 x 4 in
+    # registers, 36 = 6 x 6, 64 = 8 x 8, 72 = 12 x 6): cells with L = 0.3 N
+    # bohr and Ecut = 6 Ha, a few unevenly occupied bands
     nb = 5 if N <= 36 else 3
-    case = setup_case(N, 0.3 * N, 6.0, nb, 500 + N, prec=_lib.PREC_DF64, occ=np.linspace(2.0, 1.0, nb))
+    case = setup_case(N, 0.3 * N, 6.0, nb, 500 + N, prec=prec, occ=np.linspace(2.0, 1.0, nb))
     vpsi, ex, _ = case["plan"].apply(case["psi"], case["occ"])
     vref, eref, _ = oracle_of(case)
-    assert rel_inf(vpsi.cpu().numpy(), vref) <= TOL64
-    assert abs(ex - eref) <= TOL64 * abs(eref)
+    assert rel_inf(vpsi.cpu().numpy(), vref) <= tol_v
+    assert abs(ex - eref) <= tol_e * abs(eref)
 
 
 def test_double_float_form_refused_where_not_built():
