@@ -147,8 +147,10 @@ struct Geo {
   static constexpr int MIN_CTAS = (sizeof(T) == 4) ? 2 : 1;
   // CTAs per SM the k-point inverse plane pass is register-budgeted for: in
   // FP32, eight where eight CTAs of 40 registers a thread fit the register file
-  // (its shared memory allows that many up to N = 48)
-  static constexpr int MIN_CTAS_KINV = (sizeof(T) == 4 && 8 * 40 * THR_PLANE <= 65536) ? 8 : 1;
+  // (its shared memory allows that many up to N = 48); 0 leaves the choice to
+  // the compiler, as a bound without a minimum does (a minimum of 1 changes
+  // its register allocation: 89 instead of 78 registers at 96^3 in FP32)
+  static constexpr int MIN_CTAS_KINV = (sizeof(T) == 4 && 8 * 40 * THR_PLANE <= 65536) ? 8 : 0;
   static constexpr size_t SMEM_PLANE = sizeof(C) * (size_t)(N * RP + N);
   static constexpr size_t SMEM_COLH =
       sizeof(C) * (size_t)(N * NC + N) + 32 * 4 * sizeof(double) + NC * sizeof(int);
