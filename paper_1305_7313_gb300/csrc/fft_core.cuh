@@ -30,7 +30,13 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "df64.cuh"
+
+// The butterflies and their complex helpers compile for the host too, so that
+// they can be checked on a CPU; the kernels use them on the device only.
+#define FFT_HD __host__ __device__ __forceinline__
 
 namespace fockx {
 
@@ -177,36 +183,48 @@ template <> struct FftTraits<df64> {
 template <class T> using cplx = typename CplxOf<T>::type;
 
 // S * x for S = +1 or -1 (a sign flip, never a multiplication)
-template <int S, class T> __device__ __forceinline__ T sgn(T x) {
+template <int S, class T> FFT_HD T sgn(T x) {
   if constexpr (S > 0) return x;
   else return -x;
 }
 // x / 2, exact
-__device__ __forceinline__ float half_of(float x) { return 0.5f * x; }
-__device__ __forceinline__ double half_of(double x) { return 0.5 * x; }
+FFT_HD float half_of(float x) { return 0.5f * x; }
+FFT_HD double half_of(double x) { return 0.5 * x; }
 __device__ __forceinline__ df64 half_of(df64 x) { return ldexp_pow2(x, 0.5f); }
 
 // a * b + c with one rounding
-__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+FFT_HD float fmadd(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
+FFT_HD double fmadd(double a, double b, double c) {
+#ifdef __CUDA_ARCH__
+  return __fma_rn(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
 
 template <class T>
-__device__ __forceinline__ cplx<T> cmake(T x, T y) {
+FFT_HD cplx<T> cmake(T x, T y) {
   cplx<T> r;
   r.x = x;
   r.y = y;
   return r;
 }
-template <class C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
-template <class C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
-template <class C> __device__ __forceinline__ C cmul(C a, C b) {
+template <class C> FFT_HD C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <class C> FFT_HD C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <class C> FFT_HD C cmul(C a, C b) {
   C r;
   r.x = a.x * b.x - a.y * b.y;
   r.y = a.x * b.y + a.y * b.x;
   return r;
 }
 // S * i * a for S = +1 or -1
-template <int S, class C> __device__ __forceinline__ C cmul_si(C a) {
+template <int S, class C> FFT_HD C cmul_si(C a) {
   C r;
   r.x = S > 0 ? -a.y : a.y;
   r.y = S > 0 ? a.x : -a.x;
@@ -216,14 +234,14 @@ template <int S, class C> __device__ __forceinline__ C cmul_si(C a) {
 // In-register DFTs, y_q = sum_r x_r exp(SIGN 2 pi i r q / R).
 template <int SIGN, class T> struct Dft {
   using C = cplx<T>;
-  static __device__ __forceinline__ void r2(C* x) {
+  static FFT_HD void r2(C* x) {
     C a = x[0];
     x[0] = cadd(a, x[1]);
     x[1] = csub(a, x[1]);
   }
-  static __device__ __forceinline__ void r3(C* x) { r3_sd(x, cadd(x[1], x[2]), csub(x[1], x[2])); }
+  static FFT_HD void r3(C* x) { r3_sd(x, cadd(x[1], x[2]), csub(x[1], x[2])); }
   // the length-3 DFT from x0, s = x1 + x2 and d = x1 - x2
-  static __device__ __forceinline__ void r3_sd(C* x, C s, C d) {
+  static FFT_HD void r3_sd(C* x, C s, C d) {
     constexpr T h0 = T(0.86602540378443864676372317075293618);  // sin(2 pi / 3)
     const T h = sgn<SIGN>(h0);
     C m = cmake<T>(x[0].x - half_of(s.x), x[0].y - half_of(s.y));
@@ -232,15 +250,15 @@ template <int SIGN, class T> struct Dft {
     x[1] = cadd(m, u);
     x[2] = csub(m, u);
   }
-  static __device__ __forceinline__ void r4v(C& x0, C& x1, C& x2, C& x3) {
+  static FFT_HD void r4v(C& x0, C& x1, C& x2, C& x3) {
     C a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = cmul_si<SIGN>(csub(x1, x3));
     x0 = cadd(a, c);
     x2 = csub(a, c);
     x1 = cadd(b, d);
     x3 = csub(b, d);
   }
-  static __device__ __forceinline__ void r4(C* x) { r4v(x[0], x[1], x[2], x[3]); }
-  static __device__ __forceinline__ void r8(C* x) {
+  static FFT_HD void r4(C* x) { r4v(x[0], x[1], x[2], x[3]); }
+  static FFT_HD void r8(C* x) {
     constexpr T c = T(0.70710678118654752440084436210484904);  // cos(pi / 4)
     C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
     C o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
@@ -260,7 +278,7 @@ template <int SIGN, class T> struct Dft {
     x[7] = csub(e3, t3);
   }
   // x *= exp(SIGN 2 pi i M / R) with compile-time M, R (exact for the quarter turns)
-  template <int M, int R> static __device__ __forceinline__ C twiddle(C x) {
+  template <int M, int R> static FFT_HD C twiddle(C x) {
     constexpr int m = ((M % R) + R) % R;
     if constexpr (m == 0) {
       return x;
@@ -283,28 +301,28 @@ template <int SIGN, class T> struct Dft {
   // saves the separate rounding of w x and a quarter of the instructions of the
   // twiddled sums.
   // a + w x
-  static __device__ __forceinline__ C cfma(C a, C w, C x) {
+  static FFT_HD C cfma(C a, C w, C x) {
     return cmake<T>(fmadd(w.x, x.x, fmadd(-w.y, x.y, a.x)), fmadd(w.x, x.y, fmadd(w.y, x.x, a.y)));
   }
   // 2 a - b
-  static __device__ __forceinline__ C ctwice_sub(C a, C b) {
+  static FFT_HD C ctwice_sub(C a, C b) {
     return cmake<T>(fmadd(T(2), a.x, -b.x), fmadd(T(2), a.y, -b.y));
   }
   // a - 2 b
-  static __device__ __forceinline__ C csub_twice(C a, C b) {
+  static FFT_HD C csub_twice(C a, C b) {
     return cmake<T>(fmadd(T(-2), b.x, a.x), fmadd(T(-2), b.y, a.y));
   }
-  static __device__ __forceinline__ void r2_tw(C& x0, C& x1, C w1) {
+  static FFT_HD void r2_tw(C& x0, C& x1, C w1) {
     const C a = cfma(x0, w1, x1);
     x1 = ctwice_sub(x0, a);
     x0 = a;
   }
-  static __device__ __forceinline__ void r3_tw(C* x, C w1, C w2) {
+  static FFT_HD void r3_tw(C* x, C w1, C w2) {
     const C x1w = cmul(x[1], w1);
     const C s = cfma(x1w, w2, x[2]);  // w1 x1 + w2 x2
     r3_sd(x, s, ctwice_sub(x1w, s));
   }
-  static __device__ __forceinline__ void r4v_tw(C& x0, C& x1, C& x2, C& x3, C w1, C w2, C w3) {
+  static FFT_HD void r4v_tw(C& x0, C& x1, C& x2, C& x3, C w1, C w2, C w3) {
     const C a = cfma(x0, w2, x2);      // x0 + w2 x2
     const C b = ctwice_sub(x0, a);     // x0 - w2 x2
     const C x3w = cmul(x3, w3);
@@ -315,7 +333,7 @@ template <int SIGN, class T> struct Dft {
     x1 = cadd(b, d);
     x3 = csub(b, d);
   }
-  static __device__ __forceinline__ void r8_tw(C* x, const C* w) {
+  static FFT_HD void r8_tw(C* x, const C* w) {
     constexpr T c = T(0.70710678118654752440084436210484904);  // cos(pi / 4)
     C e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
     C o0 = cmul(x[1], w[1]), o1 = x[3], o2 = x[5], o3 = x[7];
@@ -335,7 +353,7 @@ template <int SIGN, class T> struct Dft {
     x[7] = cmake<T>(fmadd(c, q.x, e3.x), fmadd(-c, q.y, e3.y));
   }
   // W0: x_0 carries a twiddle w_0 too
-  template <int R, bool W0> static __device__ __forceinline__ void run_tw(C* x, const C* w) {
+  template <int R, bool W0> static FFT_HD void run_tw(C* x, const C* w) {
     if constexpr (W0) x[0] = cmul(x[0], w[0]);
     if constexpr (R == 2) r2_tw(x[0], x[1], w[1]);
     else if constexpr (R == 3) r3_tw(x, w[1], w[2]);
@@ -360,7 +378,7 @@ template <int SIGN, class T> struct Dft {
   // the stage twiddles w[R2 n1 + n2] on their inputs), twiddle w_R^(n2 k1),
   // R1 DFTs of length R2; output k = k1 + R1 k2.
   template <int R1, int R2, bool TW, int N2 = 0>
-  static __device__ __forceinline__ void inner(C* x, const C* w, C* a) {
+  static FFT_HD void inner(C* x, const C* w, C* a) {
     if constexpr (N2 < R2) {
       C t[R1];
 #pragma unroll
@@ -379,7 +397,7 @@ template <int SIGN, class T> struct Dft {
     }
   }
   template <int R1, int R2, int K1 = 0>
-  static __device__ __forceinline__ void outer(const C* a, C* x) {
+  static FFT_HD void outer(const C* a, C* x) {
     if constexpr (K1 < R1) {
       C t[R2];
 #pragma unroll
@@ -400,19 +418,19 @@ template <int SIGN, class T> struct Dft {
     }
   }
   template <int R1, int R2, int K1, int N2>
-  static __device__ __forceinline__ void twiddle_col(C* t) {
+  static FFT_HD void twiddle_col(C* t) {
     if constexpr (N2 < R2) {
       t[N2] = twiddle<N2 * K1, R1 * R2>(t[N2]);
       twiddle_col<R1, R2, K1, N2 + 1>(t);
     }
   }
   template <int R1, int R2, bool TW = false>
-  static __device__ __forceinline__ void composite(C* x, const C* w = nullptr) {
+  static FFT_HD void composite(C* x, const C* w = nullptr) {
     C a[R1 * R2];
     inner<R1, R2, TW>(x, w, a);
     outer<R1, R2>(a, x);
   }
-  template <int R> static __device__ __forceinline__ void run(C* x) {
+  template <int R> static FFT_HD void run(C* x) {
     if constexpr (R == 2) r2(x);
     else if constexpr (R == 3) r3(x);
     else if constexpr (R == 4) r4(x);
