@@ -153,13 +153,12 @@ __host__ __device__ constexpr RadixPlan make_radix_plan(int n, int maxt = kMaxTh
   return best;
 }
 
-// Elements a thread may hold across a stage, per working type: double-float
-// values take twice the instructions and live registers of a float, so their
-// plans use more threads per line (e.g. 96 = 12 x 4 x 2 with 8 threads per
-// line instead of 12 x 8 with 4).
-// emax: elements a thread may hold across a stage.  fused: the type has a
-// hardware fused multiply-add, so twiddle products are folded into the
-// butterfly sums (Dft::run_tw) instead of being rounded on their own.
+// Per working type.  emax: elements a thread may hold across a stage (24 in
+// FP32; 12 in FP64 and double-float, whose values take twice the registers of
+// a float, so their plans use more threads per line: 96 = 12 x 4 x 2 with 8
+// threads per line instead of 12 x 8 with 4).  fused: the type has a hardware
+// fused multiply-add, so twiddle products are folded into the butterfly sums
+// (Dft::run_tw) instead of being rounded on their own.
 template <class T> struct FftTraits {
   static constexpr int emax = kEmax;
   static constexpr bool fused = true;
@@ -169,9 +168,8 @@ template <class T> struct CplxOf;
 template <> struct CplxOf<float> { using type = float2; };
 template <> struct CplxOf<double> { using type = double2; };
 template <> struct CplxOf<df64> { using type = cdf64; };
-// FP64: 12 elements a thread (96 = 12 x 4 x 2 with 8 threads per line) keeps
-// twice the warps of a 24-element plan in flight on the FP64 pipe at the same
-// instruction count
+// FP64: the 12-element plans keep twice the warps of the 24-element ones in
+// flight on the FP64 pipe at the same instruction count
 template <> struct FftTraits<double> {
   static constexpr int emax = 12;
   static constexpr bool fused = true;

@@ -6,9 +6,15 @@
 // mode 0: Dft::run (y = DFT of x), 1: Dft::run_tw<R, false> (DFT of x_0,
 // w_1 x_1, ..., w_{R-1} x_{R-1}), 2: Dft::run_tw<R, true> (w_0 x_0 as well).
 // The DFT is y_q = sum_r x_r exp(SIGN 2 pi i r q / R); the test recomputes it.
+//
+// With the argument "plans" it prints instead the radix plan make_radix_plan
+// picks for every compiled grid size and (CTA size limit, elements per thread)
+// pair the kernels use:
+//   plan <N> <maxt> <emax> <stages> <radix 0..3, 0: none> <tl_plane> <tl_colh>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 
 #include "fft_core.cuh"
 
@@ -67,9 +73,43 @@ void all_radices() {
   cases<T, SIGN, 16>();
 }
 
+// evaluated at compile time, as the kernels do
+template <int N, int MAXT, int EMAX>
+void plan_line() {
+  constexpr RadixPlan p = make_radix_plan(N, MAXT, EMAX);
+  std::printf("plan %d %d %d %d", N, MAXT, EMAX, p.nst);
+  for (int s = 0; s < 4; ++s) std::printf(" %d", s < p.nst ? p.r[s] : 0);
+  std::printf(" %d %d\n", p.tl_plane, p.tl_colh);
+}
+
+template <int N>
+void plan_lines() {
+  plan_line<N, kMaxThreads, 24>();
+  plan_line<N, kMaxThreads, 12>();
+  plan_line<N, 416, 24>();
+  plan_line<N, 800, 12>();
+}
+
+void plans() {
+  plan_lines<8>();
+  plan_lines<12>();
+  plan_lines<16>();
+  plan_lines<24>();
+  plan_lines<32>();
+  plan_lines<36>();
+  plan_lines<48>();
+  plan_lines<64>();
+  plan_lines<72>();
+  plan_lines<96>();
+}
+
 }  // namespace
 
-int main() {
+int main(int argc, char** argv) {
+  if (argc > 1 && std::strcmp(argv[1], "plans") == 0) {
+    plans();
+    return 0;
+  }
   all_radices<float, -1>();
   all_radices<float, +1>();
   all_radices<double, -1>();
