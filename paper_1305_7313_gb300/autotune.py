@@ -25,9 +25,6 @@ import json
 import os
 import statistics
 
-import numpy as np
-
-from . import _lib
 from .plan import FockBatch
 
 

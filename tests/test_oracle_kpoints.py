@@ -3,7 +3,6 @@
 that unfolds it), Hermiticity within each k, and the E_x identity."""
 
 import numpy as np
-import pytest
 
 import oracle
 from oracle.kernels import ERFC, SPENCER_ALAVI
