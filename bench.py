@@ -35,9 +35,9 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP64 rate of GB300 from its unit counts: 1.25 TFLOP/s nominal at the 2070 MHz
-# maximum SM clock, i.e. 604 FP64 flops per clock over the 152 SMs (2 FMA per SM
-# per clock).
+# FP64 rate of GB300: the nominal 1.25 TFLOP/s at the 2070 MHz maximum SM clock
+# (604 flops per clock; the unit count, 2 FP64 FMA per SM per clock over 152
+# SMs, gives 608, i.e. 1.26 TFLOP/s, so the nominal is the stricter denominator).
 FP64_FLOPS_PER_CLK = 1.25e12 / 2.070e9
 # Double-float form: the FP32 pipe issues 128 lanes per SM per clock (152 SMs);
 # a double-float add costs 11 FP32 instructions, a multiply 7, so the radix-2
