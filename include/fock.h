@@ -20,6 +20,12 @@
  * Conventions shared by every entry point
  *  - Every call returns a fock_status; nothing is thrown and nothing exits.
  *    fock_last_error(plan) gives a one-line description of the last failure.
+ *  - Errors every entry point shares (each entry lists the others it has): a
+ *    NULL handle or output pointer, or an argument outside its stated range,
+ *    gives FOCK_ERR_INVALID_ARG (the *_destroy calls accept NULL and return
+ *    FOCK_OK); a call that queues GPU work can also give FOCK_ERR_CUDA (a
+ *    CUDA call failed; the last-error text names it) and, where it grows its
+ *    workspace, FOCK_ERR_OOM.
  *  - "device" pointers are CUDA global-memory pointers of the current device;
  *    "host" pointers are ordinary CPU memory.  The caller owns every buffer it
  *    passes; the library never frees or keeps them past the call.
@@ -203,7 +209,9 @@ fock_status fock_plan_set_deterministic(fock_plan_t plan, int enable);
 
 /* Columns of the stored half spectrum (N x 2(N/2+1) per plane, both pairs of a
  * chain) that the pair-density ball |G| <= 2 Gmax reaches and the column pass
- * transforms (`kept`), out of `total`.  Host outputs; either may be NULL. */
+ * transforms (`kept`), out of `total`: the overlap densities of §4 are products
+ * of two orbitals on the sphere, so their spectra live in that ball.  Host
+ * outputs; either may be NULL.  Errors: INVALID_ARG (plan NULL). */
 fock_status fock_plan_columns(fock_plan_t plan, int64_t* kept, int64_t* total);
 
 /*
