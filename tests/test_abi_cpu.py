@@ -103,6 +103,31 @@ def test_null_arguments_are_rejected(lib):
     assert lib.fock_plan_set_batch(None, 4) == 1
 
 
+STRING_ENTRIES = {"fock_status_string", "fock_last_error", "fock_batch_last_error", "fock_kplan_last_error"}
+
+
+def _zero_args(argtypes):
+    return [0.0 if t is ctypes.c_double else (0 if t in (ctypes.c_int, ctypes.c_uint, ctypes.c_int64) else None)
+            for t in argtypes]
+
+
+def test_every_entry_point_rejects_null_handles_and_pointers(lib):
+    # the header's shared rule: a NULL handle or pointer (or a zero where a
+    # count must be positive) is INVALID_ARG, the *_destroy calls accept NULL;
+    # nothing reaches the GPU, so this runs without one
+    for name, argtypes in _lib._SIGNATURES.items():
+        if name in STRING_ENTRIES:
+            continue
+        st = getattr(lib, name)(*_zero_args(argtypes))
+        expect = 0 if name.endswith("_destroy") else 1
+        assert st == expect, (name, _lib.STATUS.get(st, st))
+
+
+def test_error_text_entries_accept_null_handles(lib):
+    for name in ("fock_last_error", "fock_batch_last_error", "fock_kplan_last_error"):
+        assert isinstance(getattr(lib, name)(None), bytes)
+
+
 def test_kpoint_spheres_are_bit_identical_to_the_oracle(lib):
     cells = [np.diag([7.0, 7.0, 7.0]), np.array([[6.0, 0.4, 0.0], [0.0, 6.5, 0.3], [0.2, 0.0, 5.5]])]
     for cell in cells:
