@@ -21,7 +21,41 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <cstring>
+
+// The operations compile for the host too, so that they can be checked on a
+// CPU (with floating-point contraction off); the kernels use them on the device.
+#define DF_HD __host__ __device__ __forceinline__
+
 namespace fockx {
+
+// a * b + c with one rounding, in float
+DF_HD float df_fmaf(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
+DF_HD unsigned df_float_bits(float f) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(f);
+#else
+  unsigned u;
+  std::memcpy(&u, &f, sizeof u);
+  return u;
+#endif
+}
+DF_HD double df_double_from_bits(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double d;
+  std::memcpy(&d, &b, sizeof d);
+  return d;
+#endif
+}
 
 struct df64 {
   float hi, lo;
@@ -37,9 +71,9 @@ struct __align__(16) cdf64 {
   df64 x, y;
 };
 
-__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+DF_HD df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
 
-__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+DF_HD df64 operator+(df64 a, df64 b) {
   const float s = a.hi + b.hi;
   const float bb = s - a.hi;
   float e = (a.hi - (s - bb)) + (b.hi - bb);  // TwoSum error of the high parts
@@ -48,41 +82,41 @@ __device__ __forceinline__ df64 operator+(df64 a, df64 b) {
   return df64(h, e - (h - s));
 }
 
-__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+DF_HD df64 operator-(df64 a, df64 b) { return a + (-b); }
 
-__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+DF_HD df64 operator*(df64 a, df64 b) {
   const float p = a.hi * b.hi;
-  float e = __fmaf_rn(a.hi, b.hi, -p);  // TwoProd error
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
+  float e = df_fmaf(a.hi, b.hi, -p);  // TwoProd error
+  e = df_fmaf(a.hi, b.lo, e);
+  e = df_fmaf(a.lo, b.hi, e);
   const float h = p + e;
   return df64(h, e - (h - p));
 }
 
 // equal values (a normalised pair represents a value in one way only)
-__device__ __forceinline__ bool operator==(df64 a, df64 b) { return a.hi == b.hi && a.lo == b.lo; }
-__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
-__device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
-__device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = a * b; }
+DF_HD bool operator==(df64 a, df64 b) { return a.hi == b.hi && a.lo == b.lo; }
+DF_HD df64& operator+=(df64& a, df64 b) { return a = a + b; }
+DF_HD df64& operator-=(df64& a, df64 b) { return a = a - b; }
+DF_HD df64& operator*=(df64& a, df64 b) { return a = a * b; }
 
 // Exact scaling by a power of two.
-__device__ __forceinline__ df64 ldexp_pow2(df64 a, float p2) { return df64(a.hi * p2, a.lo * p2); }
+DF_HD df64 ldexp_pow2(df64 a, float p2) { return df64(a.hi * p2, a.lo * p2); }
 
 // The double nearest hi + lo (FP64 instructions: for O(nb) work and reductions).
-__device__ __forceinline__ double to_double(df64 a) { return (double)a.hi + (double)a.lo; }
-__device__ __forceinline__ double to_double(double a) { return a; }
-__device__ __forceinline__ double to_double(float a) { return (double)a; }
+DF_HD double to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+DF_HD double to_double(double a) { return a; }
+DF_HD double to_double(float a) { return (double)a; }
 
 // The double equal to a normal float, formed with integer instructions only
 // (the sign, the rebiased exponent and the mantissa moved into place); zeros
 // and subnormals (|f| < 2^-126) give 0.
-__device__ __forceinline__ double float_bits_to_double(float f) {
-  const unsigned u = __float_as_uint(f);
+DF_HD double float_bits_to_double(float f) {
+  const unsigned u = df_float_bits(f);
   const unsigned ex = (u >> 23) & 0xffu;
   const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
                                   ((unsigned long long)(ex + 896u) << 52) |
                                   ((unsigned long long)(u & 0x7fffffu) << 29);
-  return ex == 0u ? 0.0 : __longlong_as_double((long long)bits);
+  return ex == 0u ? 0.0 : df_double_from_bits(bits);
 }
 
 }  // namespace fockx

@@ -40,3 +40,25 @@ def rel_inf(a, b):
     a = np.asarray(a)
     b = np.asarray(b)
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def host_program(source, exe_dir, extra=()):
+    """Compile a host-only test program from tests/<source> with nvcc (the
+    kernels' headers compile for the host as well) and return its path; skip
+    when nvcc is not available."""
+    import shutil
+    import subprocess
+    nvcc = None
+    for home in (os.environ.get("CUDA_HOME"), os.environ.get("CUDA_PATH"), "/usr/local/cuda"):
+        if home and os.path.exists(os.path.join(home, "bin", "nvcc")):
+            nvcc = os.path.join(home, "bin", "nvcc")
+            break
+    nvcc = nvcc or shutil.which("nvcc")
+    if nvcc is None:
+        pytest.skip("nvcc not found")
+    exe = os.path.join(str(exe_dir), os.path.splitext(source)[0])
+    csrc = os.path.join(ROOT, "paper_1305_7313_gb300", "csrc")
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-Xcompiler", "-ffp-contract=off", "-I" + csrc,
+                    "-I" + os.path.join(ROOT, "include"), *extra, os.path.join(ROOT, "tests", source), "-o", exe],
+                   check=True, capture_output=True)
+    return exe

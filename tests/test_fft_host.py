@@ -12,37 +12,21 @@ double u = 2^-53) errs by at most a few u log2(R) times sum_r |x_r|; the
 tolerances are 2e-6 (float) and 1e-14 (double) of that sum.
 """
 
-import os
-import shutil
 import subprocess
 
 import numpy as np
 import pytest
 
-HERE = os.path.dirname(os.path.abspath(__file__))
-ROOT = os.path.dirname(HERE)
-CSRC = os.path.join(ROOT, "paper_1305_7313_gb300", "csrc")
+from tests._common import host_program
+
 RADICES = (2, 3, 4, 6, 8, 9, 12, 16)
 TOL = {0: 2e-6, 1: 1e-14}
-
-
-def _nvcc():
-    for home in (os.environ.get("CUDA_HOME"), os.environ.get("CUDA_PATH"), "/usr/local/cuda"):
-        if home and os.path.exists(os.path.join(home, "bin", "nvcc")):
-            return os.path.join(home, "bin", "nvcc")
-    return shutil.which("nvcc")
 
 
 @pytest.fixture(scope="module")
 def driver(tmp_path_factory):
     """The host driver, compiled by nvcc into a temporary folder."""
-    nvcc = _nvcc()
-    if nvcc is None:
-        pytest.skip("nvcc not found")
-    exe = str(tmp_path_factory.mktemp("fft_host") / "driver")
-    subprocess.run([nvcc, "-std=c++17", "-O2", "-I" + CSRC, "-I" + os.path.join(ROOT, "include"),
-                    os.path.join(HERE, "fft_host_driver.cu"), "-o", exe], check=True, capture_output=True)
-    return exe
+    return host_program("fft_host_driver.cu", tmp_path_factory.mktemp("fft_host"))
 
 
 @pytest.fixture(scope="module")
