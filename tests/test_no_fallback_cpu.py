@@ -1,7 +1,8 @@
 """The product path has no fallback: without ``libfockx.so`` every entry point
 of the binding raises, telling the user to build, and no module of the
 package imports the oracle (only the tests, ``__graft_entry__.smoke`` and the
-benchmark's baseline arms may).  No GPU is needed."""
+benchmark's baseline arms may), nor does the oracle import anything of the
+package.  No GPU is needed."""
 
 import ast
 import os
@@ -40,3 +41,18 @@ def test_the_package_never_imports_the_oracle():
                     names = [node.module or ""]
                 assert not any(n == "oracle" or n.startswith("oracle.") for n in names), (path, names)
     assert "_lib.py" in seen and "plan.py" in seen
+
+
+def test_the_oracle_imports_nothing_from_the_package():
+    odir = os.path.join(ROOT, "oracle")
+    for f in sorted(os.listdir(odir)):
+        if not f.endswith(".py"):
+            continue
+        for node in ast.walk(ast.parse(open(os.path.join(odir, f)).read())):
+            names = []
+            if isinstance(node, ast.Import):
+                names = [a.name for a in node.names]
+            elif isinstance(node, ast.ImportFrom) and node.level == 0:
+                names = [node.module or ""]
+            for n in names:
+                assert n.split(".")[0] in {"numpy", "scipy", "math", "itertools", "functools", "os"}, (f, n)
