@@ -44,3 +44,56 @@ def test_every_function_the_benchmark_calls_is_defined_or_imported():
             known.update(t.id for t in n.targets if isinstance(t, ast.Name))
     called = {n.func.id for n in ast.walk(tree) if isinstance(n, ast.Call) and isinstance(n.func, ast.Name)}
     assert called <= known, sorted(called - known)
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+class _Plan:
+    grid = (96, 96, 96)
+
+    def __init__(self, kept_fraction=0.6014030612244898):
+        self.total = 96 * 2 * 49
+        self.kept = round(kept_fraction * self.total)
+
+    def columns(self):
+        return self.kept, self.total
+
+
+def _res(dom_ms, launches=10, chains=380):
+    phases = {"pair_fwd": 1.0, "pair_col": 1.0, "pair_inv": dom_ms}
+    return {"phase_ms": phases, "clocks": {"sm_mhz": 2070.0},
+            "stats": {"phase_launches": {k: launches for k in phases}, "chains": chains}}
+
+
+def test_roofline_arithmetic_matches_the_documented_figures():
+    # the per-unit figures the design quotes, computed by the code that reports them
+    import numpy as np
+    b = _bench_module()
+    peaks = {"hbm_gbs": 6688.8}
+    # FP64: 5 n log2 n per line; per pair (fwd + col + inv) / 2 = 88.0 MFLOP at
+    # 96^3 (87.4 without the column pass's two extra stored half-columns)
+    r = b.roofline("fp64", _Plan(), _res(10.0), 1, peaks, "measured")
+    n3, lg = 96.0 ** 3, np.log2(96)
+    per_pair = (5 * n3 * 2 * lg * 2 + 2 * 5 * n3 * lg * 98 / 96) / 2
+    assert abs(per_pair / 1e6 - 88.0) < 0.05
+    assert abs(5 * n3 * np.log2(n3) / 1e6 - 87.4) < 0.05
+    assert r["kernel"] == "pair_inv" and abs(r["peak"] - 1.25) < 1e-9
+    assert abs(r["achieved"] - 5 * n3 * 2 * lg * 38 / 1e-3 / 1e12) < 1e-9  # 38 chains in 1 ms
+    assert r["traffic"] is None  # band block 16: not captured
+    r32 = b.roofline("fp64", _Plan(), _res(10.0), 1, peaks, "measured", band_block=32)
+    assert abs(r32["traffic"] / 1e6 - 2025.4) < 0.1  # 53.3 MB x 38: the ncu capture's 2025.6 MB
+    # double-float peak: 152 SMs x 128 lanes / 9.4 instructions per flop at 2070 MHz
+    rd = b.roofline("df64", _Plan(), _res(10.0), 1, peaks, "measured")
+    assert abs(rd["peak"] - 4.284) < 0.001
+    # mixed: kept half spectrum 4.34 MB; inverse pass 9.65 MB per chain at band block 8
+    rm = b.roofline("mixed32", _Plan(), _res(10.0), 1, peaks, "measured", band_block=8)
+    hbytes = 96 * 96 * 98 * 8.0 * _Plan().kept / _Plan().total
+    assert abs(hbytes / 1e6 - 4.34) < 0.01
+    assert abs(rm["bytes_per_chain"] / 1e6 - 9.65) < 0.01 and rm["bound"] == "hbm"
+    assert abs(rm["traffic"] / 1e6 - 15.35 * 38) < 1e-6
