@@ -15,7 +15,9 @@
 //
 // which leaves the result in natural order after the last stage.  A stage is
 // done in place: each thread loads all its butterfly inputs into registers,
-// the CTA synchronises, then the outputs are written back.
+// the CTA synchronises, then the outputs are written back.  In float and
+// double the products x_r w are not rounded on their own but folded into the
+// first butterfly sums as fused multiply-adds (Dft::run_tw).
 //
 // Thread mapping: thread `tid` works on line (tid mod NLINES) as sub-thread
 // (tid / NLINES) of TL sub-threads per line; consecutive threads therefore
