@@ -155,6 +155,17 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _rows(t, name, npw, nrows=None):
+    """Check that orbital tensor ``t`` is [nrows, npw] for the plan's sphere of
+    npw plane waves, before it is touched: the library takes the row length
+    from the plan, so a tensor of another sphere would be read past its end."""
+    shape = tuple(getattr(t, "shape", ()))
+    if len(shape) != 2 or shape[1] != npw or (nrows is not None and shape[0] != nrows):
+        want = "[%s, %d]" % ("nb" if nrows is None else nrows, npw)
+        raise ValueError("%s has shape %s, expected %s (the plan's sphere)" % (name, shape, want))
+    return shape[0]
+
+
 def _dev_ptr(t, name, shape=None):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
@@ -278,7 +289,9 @@ def fock_plan_columns(plan):
 
 def fock_apply(plan, psi_G, occ, vpsi_G, want_ex=True, want_dex=False, stream=None):
     """V_x psi into ``vpsi_G``; returns (E_x or None, dE_x/domega or None)."""
-    nb, npw = psi_G.shape
+    npw = fock_plan_npw(plan)
+    nb = _rows(psi_G, "psi_G", npw)
+    _rows(vpsi_G, "vpsi_G", npw, nb)
     a = _dev_ptr(psi_G, "psi_G")
     b = _dev_ptr(vpsi_G, "vpsi_G", (nb, npw))
     o, op = _dbl_array(occ)
@@ -292,7 +305,9 @@ def fock_apply(plan, psi_G, occ, vpsi_G, want_ex=True, want_dex=False, stream=No
 
 def fock_apply_shard(plan, psi_G, occ, shard, nshards, vpsi_G, want_ex=True, want_dex=False, stream=None):
     """Part ``shard`` of ``nshards`` of the pair loop; returns the partial (E_x, dE_x/domega)."""
-    nb, npw = psi_G.shape
+    npw = fock_plan_npw(plan)
+    nb = _rows(psi_G, "psi_G", npw)
+    _rows(vpsi_G, "vpsi_G", npw, nb)
     a = _dev_ptr(psi_G, "psi_G")
     b = _dev_ptr(vpsi_G, "vpsi_G", (nb, npw))
     o, op = _dbl_array(occ)
@@ -305,7 +320,7 @@ def fock_apply_shard(plan, psi_G, occ, shard, nshards, vpsi_G, want_ex=True, wan
 
 def fock_set_occupied(plan, psi_G, occ, stream=None):
     """Fix the occupied orbitals (device [nb, npw] complex128) that define V_x."""
-    nb = psi_G.shape[0]
+    nb = _rows(psi_G, "psi_G", fock_plan_npw(plan))
     a = _dev_ptr(psi_G, "psi_G")
     o, op = _dbl_array(occ)
     if o.shape != (nb,):
@@ -315,7 +330,9 @@ def fock_set_occupied(plan, psi_G, occ, stream=None):
 
 def fock_apply_fixed(plan, phi_G, vphi_G, stream=None):
     """V_x phi for trial orbitals with the V_x fixed by fock_set_occupied."""
-    nt, npw = phi_G.shape
+    npw = fock_plan_npw(plan)
+    nt = _rows(phi_G, "phi_G", npw)
+    _rows(vphi_G, "vphi_G", npw, nt)
     a = _dev_ptr(phi_G, "phi_G")
     b = _dev_ptr(vphi_G, "vphi_G", (nt, npw))
     _check(load().fock_apply_fixed(plan, a, nt, b, _stream(stream)), plan)
@@ -323,7 +340,7 @@ def fock_apply_fixed(plan, phi_G, vphi_G, stream=None):
 
 def fock_pair_energies(plan, psi_G, pairs, want_d=False, stream=None):
     """e_ij (and d_ij) for the listed (i, j) pairs; numpy float64 arrays."""
-    nb = psi_G.shape[0]
+    nb = _rows(psi_G, "psi_G", fock_plan_npw(plan))
     a = _dev_ptr(psi_G, "psi_G")
     pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
     e = np.empty(len(pr))
@@ -337,7 +354,7 @@ def fock_pair_energies(plan, psi_G, pairs, want_d=False, stream=None):
 
 def fock_pair_energies_static(plan, psi_G, pairs, want_d=False, stream=None):
     """fock_pair_energies computed in the library's static device scratch (no allocation)."""
-    nb = psi_G.shape[0]
+    nb = _rows(psi_G, "psi_G", fock_plan_npw(plan))
     a = _dev_ptr(psi_G, "psi_G")
     pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
     e = np.empty(len(pr))
@@ -367,8 +384,15 @@ def fock_batch_create(plans, psi_G, occ, vpsi_G, **options):
     _check_batch(load().fock_batch_default_options(ctypes.byref(o)))
     for k, v in options.items():
         setattr(o, k, v)
+    if not (len(psi_G) == len(vpsi_G) == len(occ) == n):
+        raise ValueError("one psi_G, vpsi_G and occ per plan")
+    rows = []
+    for k, (pl, p, v) in enumerate(zip(plans, psi_G, vpsi_G)):
+        npw = fock_plan_npw(pl)
+        rows.append(_rows(p, "psi_G[%d]" % k, npw))
+        _rows(v, "vpsi_G[%d]" % k, npw, rows[-1])
     ph = (_vp * n)(*plans)
-    nb = (ctypes.c_int * n)(*[int(p.shape[0]) for p in psi_G])
+    nb = (ctypes.c_int * n)(*rows)
     pp = (_vp * n)(*[_dev_ptr(p, "psi_G").value for p in psi_G])
     vp = (_vp * n)(*[_dev_ptr(v, "vpsi_G", tuple(p.shape)).value for v, p in zip(vpsi_G, psi_G)])
     occ_arrays = [np.ascontiguousarray(np.asarray(x, dtype=np.float64)) for x in occ]
@@ -436,6 +460,13 @@ def fock_gsphere_k(grid, cell, ecut, kpt):
     return out
 
 
+def fock_kplan_npw(plan, k):
+    """Number of plane waves of k point ``k``."""
+    n = ctypes.c_int64()
+    _check_k(load().fock_kplan_npw(plan, int(k), ctypes.byref(n)), plan)
+    return n.value
+
+
 def fock_kplan_gvectors(plan, k):
     n = ctypes.c_int64()
     _check_k(load().fock_kplan_npw(plan, int(k), ctypes.byref(n)), plan)
@@ -451,7 +482,13 @@ def fock_kplan_set_batch(plan, chain_batch):
 def fock_kplan_apply(plan, psi_G, occ, vpsi_G, want_ex=True, stream=None):
     """V_x psi for every k (lists of device tensors [nb, npw_k]); returns E_x or None."""
     nk = len(psi_G)
-    nb = int(psi_G[0].shape[0])
+    if len(vpsi_G) != nk:
+        raise ValueError("one vpsi_G per k point")
+    nb = None
+    for k in range(nk):
+        npw = fock_kplan_npw(plan, k)
+        nb = _rows(psi_G[k], "psi_G[%d]" % k, npw, nb)  # every k point holds the same bands
+        _rows(vpsi_G[k], "vpsi_G[%d]" % k, npw, nb)
     pp = (_vp * nk)(*[_dev_ptr(p, "psi_G").value for p in psi_G])
     vp = (_vp * nk)(*[_dev_ptr(v, "vpsi_G", tuple(p.shape)).value for v, p in zip(vpsi_G, psi_G)])
     o, op = _dbl_array(np.asarray(occ, dtype=np.float64).reshape(nk, nb).ravel())

@@ -174,3 +174,13 @@ def test_double_float_form_refused_where_not_built():
     with pytest.raises(_lib.FockError):
         _lib.fock_kplan_create((16, 16, 16), cubic(7.0), 6.0, [[0.0, 0.0, 0.0]], [1.0], _lib.ERFC, (0.5,),
                                _lib.PREC_DF64)
+
+
+def test_orbitals_of_another_sphere_are_refused_before_any_device_work():
+    case = setup_case(24, 10.0, 10.0, 3, 7)
+    torch = case["torch"]
+    wrong = torch.zeros((3, case["psi"].shape[1] - 1), dtype=torch.complex128, device="cuda")
+    with pytest.raises(ValueError, match="plan's sphere"):
+        case["plan"].apply(wrong, case["occ"])
+    vpsi, ex, _ = case["plan"].apply(case["psi"], case["occ"])  # the plan still works
+    assert np.isfinite(ex)

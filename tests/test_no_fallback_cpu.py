@@ -56,3 +56,39 @@ def test_the_oracle_imports_nothing_from_the_package():
                 names = [node.module or ""]
             for n in names:
                 assert n.split(".")[0] in {"numpy", "scipy", "math", "itertools", "functools", "os"}, (f, n)
+
+
+def test_orbital_tensors_are_checked_against_the_plan_before_any_device_use(monkeypatch):
+    # the library takes the row length from the plan; a tensor of another
+    # sphere is refused by the binding before a device pointer is formed
+    torch = pytest.importorskip("torch")
+    monkeypatch.setattr(_lib, "fock_plan_npw", lambda plan: 100)
+    monkeypatch.setattr(_lib, "fock_kplan_npw", lambda plan, k: 100 + k)
+    good = torch.zeros((3, 100), dtype=torch.complex128)
+    bad = torch.zeros((3, 99), dtype=torch.complex128)
+    occ = [2.0, 2.0, 2.0]
+    calls = [
+        lambda psi, v: _lib.fock_apply(None, psi, occ, v),
+        lambda psi, v: _lib.fock_apply_shard(None, psi, occ, 0, 2, v),
+        lambda psi, v: _lib.fock_set_occupied(None, psi, occ),
+        lambda psi, v: _lib.fock_apply_fixed(None, psi, v),
+        lambda psi, v: _lib.fock_pair_energies(None, psi, [(0, 1)]),
+        lambda psi, v: _lib.fock_pair_energies_static(None, psi, [(0, 1)]),
+        lambda psi, v: _lib.fock_batch_create([None], [psi], [occ], [v]),
+    ]
+    for call in calls:
+        with pytest.raises(ValueError, match="plan's sphere"):
+            call(bad, good)
+        with pytest.raises(TypeError, match="CUDA tensor"):
+            call(good, good)
+    with pytest.raises(ValueError, match="plan's sphere"):  # output of the wrong shape
+        _lib.fock_apply(None, good, occ, bad)
+    # k points: row length per k, the same bands at every k
+    k0 = torch.zeros((3, 100), dtype=torch.complex128)
+    k1 = torch.zeros((3, 101), dtype=torch.complex128)
+    with pytest.raises(ValueError, match="plan's sphere"):
+        _lib.fock_kplan_apply(None, [k0, k0], [[2.0] * 3] * 2, [k0, k0])
+    with pytest.raises(ValueError, match="plan's sphere"):
+        _lib.fock_kplan_apply(None, [k0, torch.zeros((2, 101), dtype=torch.complex128)], [[2.0] * 3] * 2, [k0, k1])
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        _lib.fock_kplan_apply(None, [k0, k1], [[2.0] * 3] * 2, [k0, k1])
