@@ -386,12 +386,14 @@ fock_status fock_batch_destroy(fock_batch_t batch);
  *   (V_x psi_nk)(G) = (sqrt(Omega)/Ntot) FFT[- sum_k' w_k' sum_m f_mk' u_mk' phi](G),  G in S_k
  *   E_x             = 1/2 sum_k w_k sum_n f_nk <psi_nk | V_x psi_nk>
  * Orbitals are general complex functions (no Gamma symmetry); every unique
- * pair of states takes one complex transform (the reverse pair is its complex
- * conjugate).  The kernel is zero on the Nyquist planes (frequency -N/2 of an
- * even axis): there the reverse pair is not the conjugate for q != 0.  Grids
- * that hold the pair-density sphere (N > 2 max |m|) have nothing on them.  Each S_k is in canonical order: ascending |k + G|^2 evaluated
- * as in fock_plan_create with m_a replaced by (m_a + k_a) formed first, ties
- * lexicographic on (m1, m2, m3).
+ * pair of states takes one complex transform, and the reverse pair's potential
+ * is its complex conjugate.  That is the plain sum over ordered pairs exactly
+ * when no pair density u_a* u_b reaches a Nyquist plane (frequency -N/2 of an
+ * even axis), so the grid must hold every pair density: for every two k points
+ * k, k' (k = k' included) and every axis a, 2 (max m_a over S_k - min m_a over
+ * S_k') < N (else fock_kplan_create returns GRID_TOO_SMALL).  Each S_k is in
+ * canonical order: ascending |k + G|^2 evaluated as in fock_plan_create with
+ * m_a replaced by (m_a + k_a) formed first, ties lexicographic on (m1, m2, m3).
  */
 typedef struct fock_kplan* fock_kplan_t;
 
@@ -400,7 +402,10 @@ typedef struct fock_kplan* fock_kplan_t;
  * and the FFT plan.
  *   kpts   host double [nk][3]: k in reduced coordinates (k = sum_a kpts_a b_a).
  *   wk     host double [nk]: k-point weights (usually summing to 1).
- *   Other arguments as fock_plan_create (the grid must hold every S_k).
+ *   Other arguments as fock_plan_create.
+ * The grid is checked on the host before any CUDA call: GRID_TOO_SMALL when
+ * an S_k does not fit (2 |m_a| >= N) or a pair density reaches the Nyquist
+ * frequency (the condition above).
  * Errors: INVALID_ARG, UNSUPPORTED_SIZE, GRID_TOO_SMALL, OOM, CUDA.
  */
 fock_status fock_kplan_create(fock_kplan_t* out, const int grid[3], const double cell[9], double ecut_ha,
@@ -412,6 +417,10 @@ fock_status fock_kplan_create(fock_kplan_t* out, const int grid[3], const double
 fock_status fock_gsphere_k(const int grid[3], const double cell[9], double ecut_ha, const double* kpt,
                            int64_t* npw, int32_t* miller, int64_t capacity);
 
+/* Number of k points of the plan (host output): the length of the psi_G and
+ * vpsi_G pointer arrays and the rows of occ that fock_kplan_apply reads. */
+fock_status fock_kplan_nk(fock_kplan_t plan, int* nk);
+
 /* Plane waves and Miller indices of S_k (host outputs; miller int32 [npw_k][3]). */
 fock_status fock_kplan_npw(fock_kplan_t plan, int k, int64_t* npw);
 fock_status fock_kplan_gvectors(fock_kplan_t plan, int k, int32_t* miller);
@@ -421,7 +430,9 @@ fock_status fock_kplan_set_batch(fock_kplan_t plan, int chain_batch);
 
 /*
  * fock_kplan_apply — V_x psi_nk for every k and E_x.
- *   psi_G    host array [nk] of device pointers, complex128 [nb][npw_k] each.
+ *   psi_G    host array [nk] of device pointers, complex128 [nb][npw_k] each;
+ *            nk is the plan's (fock_kplan_nk): the call reads exactly nk
+ *            entries of psi_G and vpsi_G and nk * nb occupations.
  *   nb       bands per k point.
  *   occ      host double [nk][nb]: occupations f_nk.
  *   vpsi_G   host array [nk] of device pointers, complex128 [nb][npw_k] each

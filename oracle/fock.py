@@ -195,12 +195,6 @@ def fock_apply_kpoints(c_list, occ, miller_list, kfrac, weights, grid, cell, kin
     ``kfrac``: [nk, 3] reduced coordinates; ``weights``: [nk].  Every ordered
     pair of states is evaluated with its own transforms.  Returns (list of
     [nb, npw_k] arrays, E_x).
-
-    Reading: on an axis of even length the Nyquist plane (m = -N/2) has no +N/2
-    partner, so for q != 0 the pair (b, a) would not be the complex conjugate of
-    the pair (a, b) there and V_x would lose its Hermiticity under pair
-    reversal.  The kernel is set to zero on the Nyquist planes (the pair density
-    has no component there on grids that hold the pair-density sphere).
     """
     from .lattice import reciprocal_lattice, g2_of_miller_k
     grid = tuple(int(n) for n in grid)
@@ -214,10 +208,6 @@ def fock_apply_kpoints(c_list, occ, miller_list, kfrac, weights, grid, cell, kin
     u = [orbitals_to_real(c_list[k], miller_list[k], grid, cell, real=False) for k in range(nk)]
     from .lattice import grid_miller
     gm = np.moveaxis(grid_miller(grid), 0, -1)
-    nyquist = np.zeros(grid, dtype=bool)
-    for a in range(3):
-        if grid[a] % 2 == 0:
-            nyquist |= gm[..., a] == -grid[a] // 2
     out = []
     esum = 0.0
     for k in range(nk):
@@ -227,7 +217,6 @@ def fock_apply_kpoints(c_list, occ, miller_list, kfrac, weights, grid, cell, kin
             acc = np.zeros(grid, dtype=np.complex128)
             for kp in range(nk):
                 vq = coulomb_kernel(kind, g2_of_miller_k(gm, b, kf[k] - kf[kp]), vol, omega)
-                vq[nyquist] = 0.0
                 for m in range(u[kp].shape[0]):
                     rho_g = _fftn(np.conj(u[kp][m]) * u[k][n])
                     acc -= w[kp] * occ[kp, m] * u[kp][m] * _ifftn(vq * rho_g)

@@ -103,6 +103,7 @@ _SIGNATURES = {
     "fock_kplan_create": [ctypes.POINTER(_vp), _c_int_p, _c_dbl_p, ctypes.c_double, ctypes.c_int, _c_dbl_p,
                           _c_dbl_p, ctypes.c_int, _c_dbl_p, ctypes.c_int, ctypes.c_int],
     "fock_gsphere_k": [_c_int_p, _c_dbl_p, ctypes.c_double, _c_dbl_p, _c_i64_p, _c_i32_p, ctypes.c_int64],
+    "fock_kplan_nk": [_vp, _c_int_p],
     "fock_kplan_npw": [_vp, ctypes.c_int, _c_i64_p],
     "fock_kplan_gvectors": [_vp, ctypes.c_int, _c_i32_p],
     "fock_kplan_set_batch": [_vp, ctypes.c_int],
@@ -460,6 +461,13 @@ def fock_gsphere_k(grid, cell, ecut, kpt):
     return out
 
 
+def fock_kplan_nk(plan):
+    """Number of k points of the plan."""
+    n = ctypes.c_int()
+    _check_k(load().fock_kplan_nk(plan, ctypes.byref(n)), plan)
+    return n.value
+
+
 def fock_kplan_npw(plan, k):
     """Number of plane waves of k point ``k``."""
     n = ctypes.c_int64()
@@ -480,18 +488,27 @@ def fock_kplan_set_batch(plan, chain_batch):
 
 
 def fock_kplan_apply(plan, psi_G, occ, vpsi_G, want_ex=True, stream=None):
-    """V_x psi for every k (lists of device tensors [nb, npw_k]); returns E_x or None."""
-    nk = len(psi_G)
-    if len(vpsi_G) != nk:
-        raise ValueError("one vpsi_G per k point")
+    """V_x psi for every k (lists of device tensors [nb, npw_k]); returns E_x or None.
+
+    The library reads one psi_G / vpsi_G pointer and one row of ``occ`` per k
+    point of the plan, so the list lengths and the occupation shape are checked
+    against the plan's k-point count before any pointer is formed."""
+    nk = fock_kplan_nk(plan)
+    if len(psi_G) != nk or len(vpsi_G) != nk:
+        raise ValueError("the plan has %d k points: got %d psi_G and %d vpsi_G tensors"
+                         % (nk, len(psi_G), len(vpsi_G)))
     nb = None
     for k in range(nk):
         npw = fock_kplan_npw(plan, k)
         nb = _rows(psi_G[k], "psi_G[%d]" % k, npw, nb)  # every k point holds the same bands
         _rows(vpsi_G[k], "vpsi_G[%d]" % k, npw, nb)
+    occ = np.asarray(occ, dtype=np.float64)
+    if occ.shape != (nk, nb):
+        raise ValueError("occ has shape %s, expected (%d, %d): one row of occupations per k point"
+                         % (occ.shape, nk, nb))
     pp = (_vp * nk)(*[_dev_ptr(p, "psi_G").value for p in psi_G])
     vp = (_vp * nk)(*[_dev_ptr(v, "vpsi_G", tuple(p.shape)).value for v, p in zip(vpsi_G, psi_G)])
-    o, op = _dbl_array(np.asarray(occ, dtype=np.float64).reshape(nk, nb).ravel())
+    o, op = _dbl_array(occ.ravel())
     ex = ctypes.c_double()
     _check_k(load().fock_kplan_apply(plan, pp, nb, op, vp, ctypes.byref(ex) if want_ex else None,
                                      _stream(stream)), plan)

@@ -199,26 +199,54 @@ fock_status fock_kplan_create(fock_kplan_t* out, const int grid[3], const double
   const double vs = fockx::lattice::reciprocal(cell, p->recip);
   if (!(std::fabs(vs) > 0.0)) return bail(kfail(p, FOCK_ERR_INVALID_ARG, "the cell is degenerate"));
   p->vol = std::fabs(vs);
-  cudaError_t e = cudaGetDevice(&p->device);
-  if (e != cudaSuccess) return bail(kcuda(p, e, "cudaGetDevice"));
 
-  // one sphere per k point
+  // one sphere per k point (host only: a grid is refused before any CUDA call)
   const int64_t ntot = (int64_t)n * n * n;
   auto off = [n](int m1, int m2, int m3) {
     return ((((m1 % n) + n) % n) * n + (((m2 % n) + n) % n)) * n + (((m3 % n) + n) % n);
   };
   std::vector<fockx::lattice::GEntry> sph;
+  std::vector<int> mlo((size_t)3 * nk), mhi((size_t)3 * nk);
   for (int k = 0; k < nk; ++k) {
     if (!fockx::lattice::build_sphere(cell, p->recip, ecut_ha, n, sph, &p->kfrac[3 * k]))
       return bail(kfail(p, FOCK_ERR_GRID_TOO_SMALL, "a G-sphere does not fit on the grid"));
     std::vector<int32_t> mill(3 * sph.size());
-    std::vector<int> gidx(sph.size());
+    for (int a = 0; a < 3; ++a) {
+      mlo[3 * k + a] = 0;
+      mhi[3 * k + a] = 0;
+    }
     for (size_t g = 0; g < sph.size(); ++g) {
-      for (int a = 0; a < 3; ++a) mill[3 * g + a] = sph[g].m[a];
-      gidx[g] = off(sph[g].m[0], sph[g].m[1], sph[g].m[2]);
+      for (int a = 0; a < 3; ++a) {
+        mill[3 * g + a] = sph[g].m[a];
+        mlo[3 * k + a] = std::min(mlo[3 * k + a], sph[g].m[a]);
+        mhi[3 * k + a] = std::max(mhi[3 * k + a], sph[g].m[a]);
+      }
     }
     p->miller.push_back(mill);
     p->npw.push_back((int)sph.size());
+  }
+  // The pair kernels evaluate each unique pair of states once and take the
+  // reverse pair's potential as the complex conjugate.  That equals the plain
+  // sum over ordered pairs exactly when no pair density u_a* u_b has a
+  // component on a Nyquist plane (frequency -N/2 of an even axis): there the
+  // partner frequency +N/2 is the same grid point, so the reverse pair would
+  // see the kernel at another |G + q|.  The frequencies of u_a* u_b are the
+  // differences m_b - m_a of the two spheres, so every pair of k points
+  // (k = k' included) must keep max m_b - min m_a below N/2 on every axis.
+  if (n % 2 == 0)
+    for (int ka = 0; ka < nk; ++ka)
+      for (int kb = 0; kb < nk; ++kb)
+        for (int a = 0; a < 3; ++a)
+          if (2 * (mhi[3 * kb + a] - mlo[3 * ka + a]) >= n)
+            return bail(kfail(p, FOCK_ERR_GRID_TOO_SMALL,
+                              "the pair densities reach the Nyquist frequency -N/2 of the grid "
+                              "(need N > 2 (max m - min m') over every pair of spheres)"));
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) return bail(kcuda(p, e, "cudaGetDevice"));
+  for (int k = 0; k < nk; ++k) {
+    const std::vector<int32_t>& mill = p->miller[k];
+    std::vector<int> gidx(mill.size() / 3);
+    for (size_t g = 0; g < gidx.size(); ++g) gidx[g] = off(mill[3 * g], mill[3 * g + 1], mill[3 * g + 2]);
     int* d = nullptr;
     if ((e = cudaMalloc((void**)&d, sizeof(int) * std::max<size_t>(1, gidx.size()))) != cudaSuccess)
       return bail(kcuda(p, e, "cudaMalloc"));
@@ -255,9 +283,6 @@ fock_status fock_kplan_create(fock_kplan_t* out, const int grid[3], const double
                                                   &qs[3 * j]);
           double v, dv;
           fockx::lattice::kernel_value(kind, p->vol, omega, g2, &v, &dv);
-          // Nyquist planes carry no kernel: there the pair (b, a) is not the
-          // conjugate of the pair (a, b) when q != 0, and one transform serves both
-          if (n % 2 == 0 && (2 * k1 == n || 2 * k2 == n || 2 * k3 == n)) v = 0.0;
           v64[(size_t)j * ntot + ((size_t)k1 * n + k2) * n + k3] = v;
         }
   if ((e = cudaMalloc((void**)&p->d_vq64, sizeof(double) * v64.size())) != cudaSuccess ||
@@ -337,6 +362,12 @@ fock_status fock_gsphere_k(const int grid[3], const double cell[9], double ecut_
     for (size_t g = 0; g < sph.size(); ++g)
       for (int a = 0; a < 3; ++a) miller[3 * g + a] = sph[g].m[a];
   }
+  return FOCK_OK;
+}
+
+fock_status fock_kplan_nk(fock_kplan_t p, int* nk) {
+  if (!p || !nk) return kfail(p, FOCK_ERR_INVALID_ARG, "bad argument");
+  *nk = p->nk;
   return FOCK_OK;
 }
 

@@ -135,3 +135,37 @@ def test_kpoint_spheres_are_bit_identical_to_the_oracle(lib):
             m = _lib.fock_gsphere_k((24, 24, 24), cell.ravel(), 6.0, kf)
             mo, _ = oracle.gsphere_k((24, 24, 24), cell.ravel(), 6.0, kf)
             assert np.array_equal(m, mo)
+
+
+def _pair_density_reach(grid, cell, ecut, kpts):
+    # largest frequency difference m_b - m_a between two spheres of the mesh
+    lo, hi = [], []
+    for k in kpts:
+        m, _ = oracle.gsphere_k(grid, cell, ecut, k)
+        lo.append(m.min(0))
+        hi.append(m.max(0))
+    return max(int((hi[b] - lo[a]).max()) for a in range(len(kpts)) for b in range(len(kpts)))
+
+
+@pytest.mark.parametrize("n,L,ecut,kpts,refused", [
+    (16, 7.0, 6.0, [[0, 0, 0], [0.5, 0, 0], [0, 0.5, 0.5], [0.25, -0.25, 0.5]], True),
+    (16, 7.0, 4.0, [[0, 0, 0], [0.5, 0, 0], [0, 0.5, 0.5], [0.25, -0.25, 0.5]], False),
+    (8, 6.0, 4.0, [[0, 0, 0]], True),            # one k point: a Gamma-only aliasing grid
+    (24, 10.0, 6.0, [[0, 0, 0]], False),
+    (48, 13.5, 12.0, [[a, b, c] for a in (0, 0.5) for b in (0, 0.5) for c in (0, 0.5)], False),
+])
+def test_kplan_refuses_grids_whose_pair_densities_reach_the_nyquist_plane(lib, n, L, ecut, kpts, refused):
+    # the refusal is decided on the host before any CUDA call, so it is seen
+    # here without a GPU; an accepted grid goes on to the device and fails
+    # there (CUDA error) on this machine, or returns a plan on a GPU
+    cell = cubic(L)
+    reach = _pair_density_reach((n, n, n), cell, ecut, np.asarray(kpts, dtype=float))
+    assert (2 * reach >= n) == refused
+    kp = np.asarray(kpts, dtype=float)
+    try:
+        h = _lib.fock_kplan_create((n, n, n), cell, ecut, kp, np.full(len(kp), 1.0 / len(kp)), 1, (0.5,), 1)
+    except _lib.FockError as e:
+        assert (e.status == 3) == refused, (e.status, str(e))
+        return
+    _lib.fock_kplan_destroy(h)
+    assert not refused

@@ -33,8 +33,10 @@ def kcase(N, L, ecut, nb, kind, omega, prec, kpts=KPTS, wk=WK, seed=40):
 
 @pytest.mark.parametrize("prec,tol_v,tol_e", [(_lib.PREC_FP64, 1e-10, 1e-10), (_lib.PREC_MIXED32, 2e-5, 5e-6)])
 def test_kpoints_match_the_oracle(prec, tol_v, tol_e):
+    # 16^3 at L = 7, Ecut = 4: the pair densities of the four spheres reach
+    # frequency differences of 6 < 8, so no pair reaches the Nyquist plane
     N = 16
-    torch, plan, cs, mills, psi, occ, cell = kcase(N, 7.0, 6.0, 3, _lib.ERFC, 0.5, prec)
+    torch, plan, cs, mills, psi, occ, cell = kcase(N, 7.0, 4.0, 3, _lib.ERFC, 0.5, prec)
     plan.set_batch(4)  # several pair launches, ragged tail
     vk, ex = plan.apply(psi, occ)
     vref, eref = oracle.fock_apply_kpoints(cs, occ, mills, KPTS, WK, (N, N, N), cell, "erfc", 0.5)
@@ -45,8 +47,7 @@ def test_kpoints_match_the_oracle(prec, tol_v, tol_e):
 
 
 def test_gamma_only_complex_orbitals_match_the_gamma_oracle():
-    # Ecut 6 at L = 10: the pair densities reach |m| = 10 < 12, so the Nyquist
-    # planes (where the k-point kernel is zero) carry nothing
+    # Ecut 6 at L = 10: the pair densities reach |m| = 10 < 12
     N = 24
     kp = np.zeros((1, 3))
     torch, plan, cs, mills, psi, occ, cell = kcase(N, 10.0, 6.0, 5, _lib.SPENCER_ALAVI, None, _lib.PREC_FP64,
@@ -77,7 +78,7 @@ def test_two_k_points_spencer_alavi_several_launches(prec, tol_v, tol_e):
 def test_one_band_per_k_point_and_empty_bands():
     # nb = 1 (only pairs across k points and self pairs), then a zero occupation
     N = 16
-    torch, plan, cs, mills, psi, occ, cell = kcase(N, 7.0, 6.0, 1, _lib.ERFC, 0.5, _lib.PREC_FP64, seed=120)
+    torch, plan, cs, mills, psi, occ, cell = kcase(N, 7.0, 4.0, 1, _lib.ERFC, 0.5, _lib.PREC_FP64, seed=120)
     vk, ex = plan.apply(psi, occ)
     vref, eref = oracle.fock_apply_kpoints(cs, occ, mills, KPTS, WK, (N, N, N), cell, "erfc", 0.5)
     assert abs(ex - eref) <= 1e-10 * abs(eref)
@@ -90,4 +91,24 @@ def test_one_band_per_k_point_and_empty_bands():
     vref, eref = oracle.fock_apply_kpoints(cs, occ0, mills, KPTS, WK, (N, N, N), cell, "erfc", 0.5)
     assert abs(ex - eref) <= 1e-10 * abs(eref)
     for k in range(len(KPTS)):
+        assert np.max(np.abs(vk[k].cpu().numpy() - vref[k])) <= 1e-10 * vmax
+
+
+def test_aliasing_grid_is_refused_and_the_device_stays_usable():
+    # 16^3 at L = 7, Ecut = 6: frequency differences reach 8 = N/2; the plan is
+    # refused on the host, then a plan on a grid that holds the pair densities
+    # runs and matches the oracle
+    require_gpu()
+    with pytest.raises(_lib.FockError) as e:
+        FockKPlan(16, cubic(7.0), 6.0, KPTS, WK, _lib.ERFC, 0.5, _lib.PREC_FP64)
+    assert e.value.status == 3 and "Nyquist" in str(e.value)
+    N = 24
+    kp = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0]])
+    torch, plan, cs, mills, psi, occ, cell = kcase(N, 7.0, 6.0, 2, _lib.ERFC, 0.5, _lib.PREC_FP64, kpts=kp,
+                                                    wk=[0.5, 0.5], seed=140)
+    vk, ex = plan.apply(psi, occ)
+    vref, eref = oracle.fock_apply_kpoints(cs, occ, mills, kp, [0.5, 0.5], (N, N, N), cell, "erfc", 0.5)
+    assert abs(ex - eref) <= 1e-10 * abs(eref)
+    vmax = max(np.max(np.abs(v)) for v in vref)
+    for k in range(2):
         assert np.max(np.abs(vk[k].cpu().numpy() - vref[k])) <= 1e-10 * vmax

@@ -64,6 +64,7 @@ def test_orbital_tensors_are_checked_against_the_plan_before_any_device_use(monk
     torch = pytest.importorskip("torch")
     monkeypatch.setattr(_lib, "fock_plan_npw", lambda plan: 100)
     monkeypatch.setattr(_lib, "fock_kplan_npw", lambda plan, k: 100 + k)
+    monkeypatch.setattr(_lib, "fock_kplan_nk", lambda plan: 2)
     good = torch.zeros((3, 100), dtype=torch.complex128)
     bad = torch.zeros((3, 99), dtype=torch.complex128)
     occ = [2.0, 2.0, 2.0]
@@ -92,3 +93,15 @@ def test_orbital_tensors_are_checked_against_the_plan_before_any_device_use(monk
         _lib.fock_kplan_apply(None, [k0, torch.zeros((2, 101), dtype=torch.complex128)], [[2.0] * 3] * 2, [k0, k1])
     with pytest.raises(TypeError, match="CUDA tensor"):
         _lib.fock_kplan_apply(None, [k0, k1], [[2.0] * 3] * 2, [k0, k1])
+    # the plan's k-point count: fewer (or more) tensor lists than k points, or
+    # occupations of another shape, are refused before any pointer is formed
+    with pytest.raises(ValueError, match="k points"):
+        _lib.fock_kplan_apply(None, [k0], [[2.0] * 3], [k0])
+    with pytest.raises(ValueError, match="k points"):
+        _lib.fock_kplan_apply(None, [k0, k1, k1], [[2.0] * 3] * 3, [k0, k1, k1])
+    with pytest.raises(ValueError, match="k points"):
+        _lib.fock_kplan_apply(None, [k0, k1], [[2.0] * 3] * 2, [k0])
+    with pytest.raises(ValueError, match="one row of occupations per k point"):
+        _lib.fock_kplan_apply(None, [k0, k1], [2.0] * 6, [k0, k1])
+    with pytest.raises(ValueError, match="one row of occupations per k point"):
+        _lib.fock_kplan_apply(None, [k0, k1], [[2.0] * 2] * 3, [k0, k1])

@@ -10,8 +10,9 @@ from paper_1305_7313_gb300 import synth
 
 
 def test_single_gamma_point_is_the_gamma_oracle_with_complex_orbitals():
-    # a grid that holds the pair-density sphere, so the Nyquist planes carry nothing
-    grid = (12, 12, 12)
+    # 8^3 at L = 6, Ecut = 4: the pair densities alias (|m| reaches 8 > 4), and
+    # the k-point sum at k = 0 is still the Gamma sum term by term
+    grid = (8, 8, 8)
     cell = (6.0 * np.eye(3)).ravel()
     mill, _ = oracle.gsphere(grid, cell, 4.0)
     mk, _ = oracle.gsphere_k(grid, cell, 4.0, (0.0, 0.0, 0.0))
@@ -27,9 +28,10 @@ def test_single_gamma_point_is_the_gamma_oracle_with_complex_orbitals():
 def test_two_k_points_equal_the_gamma_point_of_the_doubled_cell():
     # cell (L1, L, L) sampled at k = 0 and k = b1/2 (weights 1/2) is the Gamma
     # point of the supercell (2 L1, L, L): k + G = 2 (m1 + kf1) b1' + m2 b2 + m3 b3
-    # grids that hold the pair-density sphere, so the Nyquist planes carry nothing
+    # on grids that alias the pair densities: the identity is exact for the
+    # plain sum over ordered pairs on any pair of matching grids
     L1, L, ecut, nb = 5.0, 6.0, 3.0, 3
-    grid, sgrid = (12, 12, 12), (24, 12, 12)
+    grid, sgrid = (8, 8, 8), (16, 8, 8)
     cell = np.diag([L1, L, L]).ravel()
     scell = np.diag([2 * L1, L, L]).ravel()
     kf = np.array([[0.0, 0, 0], [0.5, 0, 0]])
@@ -79,9 +81,10 @@ def test_kpoint_operator_is_hermitian_per_k_and_gives_the_energy():
     assert abs(e2 - ek) <= 1e-12 * abs(ek)
 
 
-def test_pair_reversal_symmetry_holds_with_nyquist_planes_dropped():
-    # on a grid too small for the pair densities (aliasing), V_x stays Hermitian
-    # per k because the kernel is zero on the Nyquist planes
+def test_kpoint_operator_is_hermitian_per_k_on_an_aliasing_grid():
+    # the pair densities reach the Nyquist planes (|m| up to 8 on 8^3); within
+    # one k, <psi_a|V_x|psi_b> = -sum over k', m of sum_G conj(rho_ma) v(G + q) rho_mb
+    # with the same real kernel for a and b, so the matrix stays Hermitian
     grid = (8, 8, 8)
     cell = (6.0 * np.eye(3)).ravel()
     kf = np.array([[0.0, 0, 0], [0.5, 0.25, 0]])
@@ -91,6 +94,9 @@ def test_pair_reversal_symmetry_holds_with_nyquist_planes_dropped():
         mills.append(m)
         cs.append(synth.orbitals_k(m, cell, kf[k], 3, 70 + k))
     vk, ek = oracle.fock_apply_kpoints(cs, np.full((2, 3), 2.0), mills, kf, [0.5, 0.5], grid, cell, ERFC, 0.7)
+    e2 = 0.0
     for k in range(2):
         m = np.conj(cs[k]) @ vk[k].T
         assert np.max(np.abs(m - m.conj().T)) <= 1e-13 * np.max(np.abs(m))
+        e2 += 0.5 * 0.5 * float(np.sum(2.0 * np.diag(m).real))
+    assert abs(e2 - ek) <= 1e-12 * abs(ek)
