@@ -282,20 +282,24 @@ fock_status fock_pair_energies(fock_plan_t plan, const void* psi_G, int nb, cons
 
 /*
  * fock_pair_energies_static — fock_pair_energies without any device
- * allocation.  The paper has no counterpart: this serves callers that cannot
- * call cudaMalloc when they need the pair energies (code running during CUDA
- * stream capture, frameworks that own every device allocation or impose a
- * fixed memory budget, latency-bound loops that cannot afford an allocation or
- * its implicit synchronisation).
+ * allocation.  The paper has no counterpart: this serves callers that must not
+ * call cudaMalloc when they need the pair energies (frameworks that own every
+ * device allocation or hold the process to a fixed memory budget, loops that
+ * cannot take an allocation's latency or the device-wide synchronisation
+ * cudaMalloc and cudaFree may imply).
  *   Arguments, results and errors as in fock_pair_energies (pairs, e and d are
- *   host arrays; the call synchronises the stream).
+ *   host arrays).
+ *   It is a synchronising call: it copies the host pair list to the device,
+ *   waits for the stream and scales the results on the host, so it must not be
+ *   issued on a stream that is being captured into a CUDA graph.
  *   Working memory: one static device array of 32 MiB per device, held from
  *   library load to process exit.  It must hold nb*N^3 reals of the plan's
  *   precision (8 or 4 bytes), 8*npairs + 16*npairs + 16*npairs bytes, and one
  *   transform buffer of N^2 (N+2) complex elements; larger requests fail with
  *   FOCK_ERR_INVALID_ARG before any work is queued.
- *   The first call on a device (with that device current) looks up the array's
- *   device address; make that first call before any stream capture.
+ *   The first call in a CUDA context of a device (with that device current)
+ *   looks up the array's device address; a new context (after a device reset)
+ *   looks it up again.
  *   All calls share the array: calls whose work overlaps on the GPU race.
  *   The plan's own workspace is not touched, but its tables are used.
  */
@@ -323,8 +327,9 @@ typedef struct {
   int use_graph;        /* 1: capture once into a CUDA graph and replay it (default 1) */
   int want_dex;         /* 1: also produce dE_x/domega (erfc plans) */
   double wait_limit_s;  /* bound on each device-side dependency wait (default 10 s) */
-  int stall_segment;    /* >= 0: that segment waits for itself, which can never finish: a
-                           test hook for the bounded-wait path (FOCK_ERR_TIMEOUT); -1 normally */
+  int stall_segment;    /* TEST ONLY (leave at -1): >= 0 makes that segment wait for itself,
+                           which can never finish, so that tests can drive the bounded-wait
+                           path (FOCK_ERR_TIMEOUT) without a GPU fault */
   int persistent;       /* 1: the pair passes of all systems in one persistent launch (default);
                            0: each system's pair passes as size-specialised launches on its own
                            branch of the graph (branches run concurrently) */

@@ -2,21 +2,26 @@
 // fock_pair_energies for callers that must not allocate device memory.
 //
 // Some callers cannot call cudaMalloc at the point where they need the pair
-// energies: code that runs while a CUDA stream is being captured, code under a
-// framework that owns every device allocation (a caching allocator, a fixed
-// memory budget), or a real-time loop where an allocation's latency or its
-// implicit device synchronisation is not acceptable.  This entry point takes
+// energies: code under a framework that owns every device allocation (a
+// caching allocator, a fixed memory budget that the library may not grow),
+// or a loop that cannot take an allocation's latency or the device-wide
+// synchronisation cudaMalloc and cudaFree may imply.  This entry point takes
 // the working memory the pair passes need (real-space orbitals, the
 // half-spectrum transform buffer, the chain list and the per-pair partial
 // sums) from one file-scope device array of kStaticScratchBytes instead of the
 // plan's workspace.  It calls no cudaMalloc, cudaFree or other allocating
 // routine.
 //
+// It is still a synchronising call: it copies the caller's host pair list to
+// the device, waits for its stream, and scales the energies on the host.  It
+// must not be issued on a stream that is being captured into a CUDA graph.
+//
 // The array exists once per device for the lifetime of the process that
 // loaded the library.  Host code must not use its name as a device address:
-// the first call on each device, with that device current, asks the runtime
-// for the array's device address (cudaGetSymbolAddress) and keeps it.  That
-// first call should therefore come before any stream capture.
+// at set-up, the first call in each CUDA context of a device (with that device
+// current) asks the runtime for the array's device address
+// (cudaGetSymbolAddress) and keeps it for that context; a new context on the
+// device (after cudaDeviceReset, say) is looked up again.
 //
 // Every call uses the same array and leaves its contents behind; the call
 // clears what must start at zero.  Two calls whose work overlaps on the GPU
@@ -24,6 +29,8 @@
 #include <algorithm>
 #include <mutex>
 #include <vector>
+
+#include <cuda.h>  // driver types for the context query; the entry points come through the runtime
 
 #include "fock.h"
 #include "fock_internal.h"
@@ -36,7 +43,8 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 std::mutex g_setup_mutex;
-void* g_scratch_address[kMaxDevices];  // device address of g_static_scratch, per device
+void* g_scratch_address[kMaxDevices];         // device address of g_static_scratch, per device
+unsigned long long g_scratch_ctx[kMaxDevices];  // id of the context that address belongs to (0: none)
 
 __global__ void k_chains_from_pairs(const int2* __restrict__ pairs, int npairs,
                                     fockx::Chain* __restrict__ chains) {
@@ -74,14 +82,47 @@ fock_status cuda_fail(fock_plan_t plan, cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? FOCK_ERR_OOM : FOCK_ERR_CUDA;
 }
 
-// Device address of the scratch array on `device` (which must be current).
+// Id of the current CUDA context (unique for the life of the process), or 0
+// when the driver cannot tell; the driver entry points are fetched through
+// the runtime, so the library does not link the driver library itself.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    resolved = true;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+      get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of the scratch array on `device` (which must be current),
+// looked up once per context of the device.  When the context cannot be
+// identified the address is looked up on every call.
 cudaError_t scratch_address(int device, unsigned char** out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (g_scratch_address[device] == nullptr) {
+  const unsigned long long ctx = current_context_id();
+  if (ctx == 0 || g_scratch_ctx[device] != ctx || g_scratch_address[device] == nullptr) {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_address[device] = ptr;
+    g_scratch_ctx[device] = ctx;
   }
   *out = static_cast<unsigned char*>(g_scratch_address[device]);
   return cudaSuccess;
