@@ -35,15 +35,17 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP64 rate of GB300: the nominal 1.25 TFLOP/s at the 2070 MHz maximum SM clock
-# (604 flops per clock; the unit count, 2 FP64 FMA per SM per clock over 152
-# SMs, gives 608, i.e. 1.26 TFLOP/s, so the nominal is the stricter denominator).
-FP64_FLOPS_PER_CLK = 1.25e12 / 2.070e9
-# Double-float form: the FP32 pipe issues 128 lanes per SM per clock (152 SMs);
-# a double-float add costs 11 FP32 instructions, a multiply 7, so the radix-2
-# mix of the 5 n log2 n count (6 adds, 4 multiplies per 10 flops) costs 9.4
-# FP32 instructions per flop.
-DF64_FLOPS_PER_CLK = 152 * 128 / 9.4
+# FP64 rate of GB300, measured: a loop of independent DFMA chains over every
+# SM (csrc/probe_fma_peak.cu) runs 1.2557 TFLOP/s at the 2070 MHz maximum SM
+# clock, 99.8% of the unit count (2 FP64 FMA per SM per clock over 152 SMs).
+FP64_PEAK_TFLOPS = 1.2557
+FP64_FLOPS_PER_CLK = FP64_PEAK_TFLOPS * 1e12 / 2.070e9
+# Double-float form: the same probe's FP32 FMA loop runs 78.52 TFLOP/s (39.26 T
+# FP32 instructions/s) at 2070 MHz; a double-float add costs 11 FP32
+# instructions, a multiply 7, so the radix-2 mix of the 5 n log2 n count (6
+# adds, 4 multiplies per 10 flops) costs 9.4 FP32 instructions per flop.
+FP32_FMA_PEAK_TFLOPS = 78.52
+DF64_FLOPS_PER_CLK = FP32_FMA_PEAK_TFLOPS / 2 * 1e12 / 2.070e9 / 9.4
 
 
 def workload(name):
@@ -130,10 +132,9 @@ def time_form(plan, psi, occ, steps, warmup, want_dex=False, rank=0, world=1):
     def step():
         if world == 1:
             plan.apply(psi, occ, vpsi, True, want_dex)
-        else:
-            import torch.distributed as dist
-            plan.apply_shard(psi, occ, rank, world, vpsi, True, want_dex)
-            dist.all_reduce(torch.view_as_real(vpsi))
+        else:  # band groups: this rank's shard of the pairs, then the sums over ranks
+            from paper_1305_7313_gb300 import distributed
+            distributed.apply(plan, psi, occ, vpsi_G=vpsi, want_dex=want_dex)
 
     for _ in range(warmup):
         step()
@@ -211,13 +212,12 @@ def roofline(form, plan, res, steps, peaks, peak_src, band_block=16):
         mhz = res["clocks"].get("sm_mhz") or 2070.0
         per_clk = FP64_FLOPS_PER_CLK if form == "fp64" else DF64_FLOPS_PER_CLK
         peak = per_clk * 2070.0e6 / 1e12
-        src = ("nominal FP64 at 2070 MHz" if form == "fp64" else
-               "double-float flops at the FP32 pipe rate (9.4 FP32 instructions per flop), 2070 MHz")
+        src = ("measured DFMA loop, 2070 MHz" if form == "fp64" else
+               "measured FP32 FMA loop / 9.4 FP32 instructions per double-float flop, 2070 MHz")
         return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": measured_traffic(form, n, dom, band_block, chains_per_launch),
-                "traffic_unit": "DRAM bytes per launch (ncu)", "peak_src": src,
-                "frac_at_sampled_clock": achieved / (per_clk * mhz * 1e6 / 1e12),
+                "peak_src": src, "frac_at_sampled_clock": achieved / (per_clk * mhz * 1e6 / 1e12),
                 "ms_per_launch": ms_per_launch, "chains_per_launch": chains_per_launch}
     # Algorithmic bytes per chain (two pairs): the kept columns of the complex64
     # half spectrum (written by pair_fwd, read and written by pair_col, read by
@@ -233,10 +233,43 @@ def roofline(form, plan, res, steps, peaks, peak_src, band_block=16):
     return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak,
             "traffic": measured_traffic(form, n, dom, band_block, chains_per_launch),
-            "traffic_unit": "DRAM bytes per launch (ncu)", "algorithmic_bytes_per_launch": per_chain * chains_per_launch,
-            "peak_src": peak_src + " (hbm copy)",
-            "bytes_per_chain": per_chain, "kept_columns": kept / total, "band_block": band_block,
+            "peak_src": peak_src + " (hbm copy)", "bytes_per_chain": per_chain,
             "ms_per_launch": ms_per_launch, "chains_per_launch": chains_per_launch}
+
+
+def golden_errors(plan, c, w):
+    """Errors of `plan`'s apply on the first 64 bands of workload `w` against the
+    oracle's stored values for the same 64 bands (E_x, dE_x/domega, V_x psi at
+    sampled sphere positions; tests/golden/oracle_fullsize_N96_nb64.txt).  Run
+    outside the timed region."""
+    import importlib.util
+    import torch
+    spec = importlib.util.spec_from_file_location(
+        "fullsize_record", os.path.join(ROOT, "tests", "golden", "fullsize_record.py"))
+    rec_mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(rec_mod)
+    case = rec_mod.CASE_OF_SEED.get(w["seed"])
+    if case is None or plan.grid[0] != 96 or w["nb"] < rec_mod.NB or not os.path.exists(rec_mod.FILE):
+        return None
+    rec = rec_mod.load()
+    sub = torch.from_numpy(np.ascontiguousarray(c[:rec_mod.NB])).cuda()
+    vpsi, ex, dex = plan.apply(sub, np.full(rec_mod.NB, 2.0), want_dex=True)
+    err = rec_mod.compare(rec, case, ex, dex, vpsi.cpu().numpy())
+    err["against"] = "stored FP64 oracle, first 64 bands (E_x, dE/domega; V_x psi at %d sampled G)" % err.pop("samples")
+    del sub, vpsi
+    return err
+
+
+def form_summary(res_line, roof, err):
+    """The compact record of one form printed at the end of the JSON line."""
+    out = {"workload": res_line["workload"], "value": res_line["value"], "unit": UNIT,
+           "ms_per_step": res_line["ms_per_step"], "dtype": res_line["dtype"],
+           "frac": roof["frac"], "bound": roof["bound"], "achieved": roof["achieved"],
+           "peak": roof["peak"], "roof_unit": roof["unit"], "dominant": roof["kernel"],
+           "traffic": roof["traffic"], "pair_loop_pairs_per_s": res_line["pair_loop_pairs_per_s"]}
+    if err:
+        out.update({k: err[k] for k in ("max_abs_dVpsi_rel", "rel_dEx", "rel_ddEx_domega")})
+    return out
 
 
 def fixed_blocks(plan, args):
@@ -318,7 +351,6 @@ def run_batched(args, peaks, peak_src):
         nbytes_kernel = "k_pair_persistent"
     return {"workload": "batched16_mixed32_sa_N48-96_L13.5-27", "mode": "persistent" if persistent else
             "graph branches of size-specialised launches",
-            "systems": [{"N": sy["N"], "L": sy["L"], "nb": sy["nb"]} for sy in systems],
             "value": pairs * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
             "pairs": pairs, "dtype": "f32", "graph": True, "persistent_launches_per_step": 1 if persistent else 0,
             "gpu_launches_per_step": info["launches"], "persistent_grid": info["grid"],
@@ -328,8 +360,18 @@ def run_batched(args, peaks, peak_src):
                          "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
                          "peak_src": peak_src + " (hbm copy)", "ms_per_launch": pm},
             "tuned": {"options": tuned["options"], "band_block": tuned["band_block"],
-                      "candidates_ms": [(r["options"], r["ms"]) for r in tuned.get("table", [])]},
+                      "best_ms_by_mode": best_by_mode(tuned.get("table", []))},
             "clocks": clk.summary()}
+
+
+def best_by_mode(table):
+    """Fastest tuner candidate per pair-pass mode (persistent launch vs graph branches)."""
+    out = {}
+    for r in table:
+        key = "persistent" if r["options"].get("persistent", 1) else "branches"
+        if key not in out or r["ms"] < out[key]:
+            out[key] = r["ms"]
+    return out
 
 
 def run_kpoints(args, peaks, peak_src):
@@ -460,8 +502,7 @@ def run_cufft_comparison(args, w, nbands=128, chunk=32):
                      "rel_dEx_vs_fock_fp64": abs(float(ex) - ex_fock) / abs(ex_fock)}
         del y, cg
         torch.cuda.empty_cache()
-    out["sample"] = ("first %d bands of %s (%d pairs): torch.fft (cuFFT) R2C/C2R transforms, torch "
-                     "element-wise products, %d pairs per batch" % (nb, w["name"], nb * (nb + 1) // 2, chunk))
+    out["sample"] = "first %d bands (%d pairs), torch.fft R2C/C2R" % (nb, nb * (nb + 1) // 2)
     return out
 
 
@@ -618,6 +659,7 @@ def main():
     value = pairs * args.steps / (res["ms"] * 1e-3)
     form = {PREC_FP64: "fp64", PREC_MIXED32: "mixed32"}.get(w["prec"], "df64")
     roof = roofline(form, plan, res, args.steps, peaks, peak_src, tuned["band_block"] if tuned else 16)
+    err = golden_errors(plan, c, w) if world == 1 else None
 
     # ---- end to end through the public API from pinned host memory
     e2e = None
@@ -658,9 +700,9 @@ def main():
                  "ms_per_step": resm["ms"] / args.steps, "dtype": "f32",
                  "roofline": roofline("mixed32", planm, resm, args.steps, peaks, peak_src,
                                       tunedm["band_block"] if tunedm else 16),
-                 "phase_ms_per_step": {k: v / args.steps for k, v in resm["phase_ms"].items()},
                  "pair_loop_pairs_per_s": pair_loop_rate(pm, resm, args.steps),
                  "gpu_launches": resm["launches"], "clocks": resm["clocks"], "tuned": tunedm}
+        mixed["summary"] = form_summary(mixed, mixed["roofline"], golden_errors(planm, cm, wm) if world == 1 else None)
         planm.close()
         del psim
         torch.cuda.empty_cache()
@@ -685,9 +727,9 @@ def main():
               "ms_per_step": resd["ms"] / args.steps, "dtype": "f32x2 (double-float)",
               "roofline": roofline("df64", pland, resd, args.steps, peaks, peak_src,
                                    tunedd["band_block"] if tunedd else 16),
-              "phase_ms_per_step": {k: v / args.steps for k, v in resd["phase_ms"].items()},
               "pair_loop_pairs_per_s": pair_loop_rate(pd, resd, args.steps),
               "gpu_launches": resd["launches"], "clocks": resd["clocks"], "tuned": tunedd}
+        df["summary"] = form_summary(df, df["roofline"], golden_errors(pland, cd, wd) if world == 1 else None)
         pland.close()
         del psid
         torch.cuda.empty_cache()
@@ -718,6 +760,9 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(w, args.ref_bands)
         cpu.pop("seconds", None)
+    def brief_tuned(t):
+        return None if t is None else {k: t[k] for k in ("chain_batch", "band_block")}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -726,23 +771,24 @@ def main():
         "config": {"workload": w["name"], "grid": n, "L_bohr": w["L"], "ecut_ha": w["ecut"],
                    "nbands": w["nb"], "pairs": pairs, "npw": plan.npw,
                    "kernel": "spencer_alavi" if w["kernel"] == 0 else "erfc",
-                   "l2": "inputs larger than L2 (psi_G %.0f MB, real-space orbitals and accumulators "
-                         "%.1f GB each)" % (c.nbytes / 1e6, w["nb"] * n**3 * (4 if form == "mixed32" else 8) / 1e9),
-                   "parallelism": "pair-triangle shards + all-reduce" if world > 1 else "single GPU"},
+                   "l2": "inputs larger than L2 (real-space orbitals and accumulators %.1f GB each)"
+                         % (w["nb"] * n**3 * (4 if form == "mixed32" else 8) / 1e9),
+                   "parallelism": "band-group shards + all-reduce" if world > 1 else "single GPU"},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
-        "phase_ms_per_step": {k: v / args.steps for k, v in res["phase_ms"].items()},
+        "errors": err,
         "pair_loop_pairs_per_s": pair_loop_rate(pairs, res, args.steps),
-        "tuned": tuned,
-        "mixed32": mixed,
-        "df64": df,
+        "tuned": brief_tuned(tuned),
         "batched": batched,
         "kpoints": kpoints,
         "autograd": autograd,
         "cufft_comparison": cufft,
+        # the two other forms of the metric last, compact
+        "df64_summary": df["summary"] if df else None,
+        "mixed32_summary": dict(mixed["summary"], tuned=brief_tuned(mixed["tuned"])) if mixed else None,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

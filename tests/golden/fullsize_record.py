@@ -1,0 +1,52 @@
+"""Reader of ``oracle_fullsize_N96_nb64.txt`` (written by
+``make_fullsize_golden.py`` from the oracle alone).  It holds no arithmetic of
+the method and imports nothing from ``oracle/``, so the GPU tests and the
+benchmark's error report can compare with the stored oracle values without
+running the oracle."""
+
+import os
+
+FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_fullsize_N96_nb64.txt")
+NB = 64
+# the cases of the file: (workload seed, kernel) -> case name
+CASE_OF_SEED = {1306: "spencer_alavi_seed1306", 1307: "erfc_seed1307"}
+
+
+def parse(text):
+    """{"npw": n, "nb": 64, case: {"ex", "dex", "vmax": {b: x}, "coef": {(b, g): complex}}}"""
+    rec = {}
+    for line in text.splitlines():
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "npw":
+            rec["npw"], rec["nb"] = int(f[1]), int(f[3])
+        elif f[0] == "case":
+            rec[f[1]] = {"ex": float(f[3]), "dex": float(f[5]), "vmax": {}, "coef": {}}
+        elif f[0] == "vmax":
+            rec[f[1]]["vmax"][int(f[2])] = float(f[3])
+        elif f[0] == "coef":
+            rec[f[1]]["coef"][(int(f[2]), int(f[3]))] = complex(float(f[4]), float(f[5]))
+    return rec
+
+
+def load(path=FILE):
+    with open(path) as fh:
+        return parse(fh.read())
+
+
+def compare(rec, case, ex, dex, vpsi):
+    """Errors of a result on the 64-band subset against the stored oracle values:
+    relative E_x and dE_x/domega errors (the latter None for a kernel without
+    omega) and the largest |Delta V_x psi_b(G)| / max_G |V_x psi_b(G)| over the
+    sampled bands and sphere positions.  ``vpsi``: [64, npw] array-like."""
+    r = rec[case]
+    rel_ex = abs(ex - r["ex"]) / abs(r["ex"])
+    rel_dex = None
+    if r["dex"] != 0.0 and dex is not None:
+        rel_dex = abs(dex - r["dex"]) / abs(r["dex"])
+    worst = 0.0
+    for (b, g), z in r["coef"].items():
+        worst = max(worst, abs(complex(vpsi[b][g]) - z) / r["vmax"][b])
+    return {"rel_dEx": rel_ex, "rel_ddEx_domega": rel_dex, "max_abs_dVpsi_rel": worst,
+            "samples": len(r["coef"])}

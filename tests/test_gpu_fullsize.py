@@ -87,3 +87,29 @@ def test_full_size_against_sampled_oracle_outputs_and_invariants(form):
     plan.close()
     del psi, vpsi, m
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+def test_first_64_bands_match_the_stored_oracle_energy(form):
+    # E_x (and dE_x/domega for the erfc kernel) of the first 64 bands of the
+    # 96^3 workloads against the oracle's values over the same 64 bands
+    # (tests/golden/oracle_fullsize_N96_nb64.txt, written from oracle/ alone),
+    # plus V_x psi of three bands at 203 sampled sphere positions each
+    from tests.golden import fullsize_record
+    torch = require_gpu()
+    name, prec, _, tol_v, tol_e = FORMS[form]
+    w = WORKLOADS[name]
+    rec = fullsize_record.load()
+    case = fullsize_record.CASE_OF_SEED[w["seed"]]
+    cell = np.asarray(cubic_cell(w["L"]))
+    plan = FockPlan(N, cell, w["ecut"], w["kernel"], w["omega"], prec)
+    assert plan.npw == rec["npw"]
+    c = synth.orbitals(plan.miller, cell, w["nb"], w["seed"])[:fullsize_record.NB]
+    psi = torch.from_numpy(np.ascontiguousarray(c)).cuda()
+    vpsi, ex, dex = plan.apply(psi, np.full(fullsize_record.NB, 2.0), want_dex=True)
+    err = fullsize_record.compare(rec, case, ex, dex, vpsi.cpu().numpy())
+    assert err["rel_dEx"] <= tol_e, err
+    if err["rel_ddEx_domega"] is not None:
+        assert err["rel_ddEx_domega"] <= tol_e, err
+    assert err["max_abs_dVpsi_rel"] <= tol_v, err
+    plan.close()
