@@ -278,8 +278,10 @@ def fixed_blocks(plan, args):
         plan.set_batch(args.chain_batch)
     if args.band_block:
         plan.set_band_block(args.band_block)
-    return {"chain_batch": args.chain_batch, "band_block": args.band_block or 16, "tuned_on_bands": 0,
-            "candidates": 0}
+    if args.tiles:
+        plan.set_tiling([int(x) for x in args.tiles])
+    return {"chain_batch": args.chain_batch, "band_block": args.band_block or 16, "tiles": args.tiles,
+            "tuned_on_bands": 0, "candidates": 0}
 
 
 def tune_on_subset(plan, c, occ, nbands, reps=2):
@@ -289,8 +291,17 @@ def tune_on_subset(plan, c, occ, nbands, reps=2):
     sub = torch.from_numpy(np.ascontiguousarray(c[:nbands])).cuda()
     res = tune_apply(plan, sub, occ[:nbands], reps=reps, use_cache=False)
     del sub
-    return {"chain_batch": res["chain_batch"], "band_block": res["band_block"],
-            "tuned_on_bands": nbands, "candidates": len(res["table"])}
+    return {"chain_batch": res["chain_batch"], "band_block": res["band_block"], "tiles": res.get("tiles"),
+            "tiling": tiling_text(res.get("tiling")), "tuned_on_bands": nbands, "candidates": len(res["table"])}
+
+
+def tiling_text(tiling):
+    """'fwd 12x4x2/8 col 12x8/4 inv 12x8/4': radix plan / threads per line per pair pass."""
+    if not tiling:
+        return None
+    short = {"pair_fwd": "fwd", "pair_col": "col", "pair_inv": "inv"}
+    return " ".join("%s %s/%d" % (short[k], "x".join(str(r) for r in v["radices"]), v["threads_per_line"])
+                    for k, v in tiling.items())
 
 
 def run_batched(args, peaks, peak_src):
@@ -617,6 +628,8 @@ def main():
                     help="with --no-tune: chains per pair-pass launch of the Gamma-point forms")
     ap.add_argument("--band-block", type=int, default=0,
                     help="with --no-tune: band block of the Gamma-point pair schedule")
+    ap.add_argument("--tiles", default="",
+                    help="with --no-tune: FFT tiling of the forward, column and inverse passes, e.g. 100")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison line")
     ap.add_argument("--cufft-bands", type=int, default=128)
     ap.add_argument("--tune-bands", type=int, default=64,
@@ -650,7 +663,7 @@ def main():
     tuned = None
     if not args.no_tune:
         tuned = tune_on_subset(plan, c, occ, min(w["nb"], max(8, args.tune_bands // 2)), reps=1)
-    elif args.chain_batch or args.band_block:
+    elif args.chain_batch or args.band_block or args.tiles:
         tuned = fixed_blocks(plan, args)
     psi = torch.from_numpy(c).cuda()
     pairs = w["nb"] * (w["nb"] + 1) // 2
@@ -691,7 +704,7 @@ def main():
         tunedm = None
         if not args.no_tune:
             tunedm = tune_on_subset(planm, cm, occm, min(wm["nb"], args.tune_bands))
-        elif args.chain_batch or args.band_block:
+        elif args.chain_batch or args.band_block or args.tiles:
             tunedm = fixed_blocks(planm, args)
         psim = torch.from_numpy(cm).cuda()
         resm = time_form(planm, psim, occm, args.steps, args.warmup, rank=rank, world=world)
@@ -718,7 +731,7 @@ def main():
         tunedd = None
         if not args.no_tune:
             tunedd = tune_on_subset(pland, cd, occd, min(wd["nb"], args.tune_bands), reps=1)
-        elif args.chain_batch or args.band_block:
+        elif args.chain_batch or args.band_block or args.tiles:
             tunedd = fixed_blocks(pland, args)
         psid = torch.from_numpy(cd).cuda()
         resd = time_form(pland, psid, occd, args.steps, args.warmup, rank=rank, world=world)
@@ -761,7 +774,7 @@ def main():
         cpu = cpu_baseline(w, args.ref_bands)
         cpu.pop("seconds", None)
     def brief_tuned(t):
-        return None if t is None else {k: t[k] for k in ("chain_batch", "band_block")}
+        return None if t is None else {k: t.get(k) for k in ("chain_batch", "band_block", "tiling")}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -192,6 +192,29 @@ fock_status fock_plan_stats(fock_plan_t plan, fock_stats* stats);
  * accumulators in L2.  Takes effect at the next call.  Errors: INVALID_ARG. */
 fock_status fock_plan_set_band_block(fock_plan_t plan, int band_block);
 
+/*
+ * FFT tilings of the pair passes.  Each of the three pair passes (pass 0: the
+ * forward plane pass, 1: the column pass, 2: the inverse plane pass) has one
+ * or two compiled radix plans ("tilings"): tile 0 holds FftTraits' element
+ * budget per thread (24 complex values in the mixed form, 12 in FP64 and
+ * double-float), tile 1 the plan found with the other budget (12 in the mixed
+ * form, 24 in FP64; none in double-float).  When both budgets give the same
+ * plan for N, the pass has one tiling.  The results do not depend on the
+ * tiling beyond rounding; the speed does (the tuner in autotune.py times them).
+ *
+ * fock_plan_tiling_info: the plan of tile `tile` of pass `pass`: radices
+ *   (host int[8], stage order), nstages, threads per transformed line,
+ *   threads per CTA, and ntiles (1 or 2) for that pass.  INVALID_ARG for a
+ *   tile the pass does not have.
+ * fock_plan_set_tiling: tiles host int[3], the tile of each pass (each below
+ *   that pass's ntiles); takes effect at the next call (fock_apply,
+ *   fock_apply_shard, fock_apply_fixed, fock_pair_energies).  Default 0, 0, 0.
+ *   Errors: INVALID_ARG.
+ */
+fock_status fock_plan_tiling_info(fock_plan_t plan, int pass, int tile, int* radices, int* nstages,
+                                  int* threads_per_line, int* threads, int* ntiles);
+fock_status fock_plan_set_tiling(fock_plan_t plan, const int tiles[3]);
+
 /* Bytes of device memory the plan holds (tables + workspace).  bytes: host. */
 fock_status fock_plan_device_bytes(fock_plan_t plan, int64_t* bytes);
 

@@ -46,8 +46,10 @@ from ._lib import (  # noqa: F401
     fock_plan_reserve,
     fock_plan_set_band_block,
     fock_plan_set_batch,
+    fock_plan_set_tiling,
     fock_plan_set_timing,
     fock_plan_stats,
+    fock_plan_tiling_info,
     fock_status_string,
 )
 from .plan import FockBatch, FockKPlan, FockPlan  # noqa: F401

@@ -75,6 +75,8 @@ _SIGNATURES = {
     "fock_schedule": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_i32_p, ctypes.c_int64,
                       _c_i64_p],
     "fock_plan_set_band_block": [_vp, ctypes.c_int],
+    "fock_plan_tiling_info": [_vp, ctypes.c_int, ctypes.c_int, _c_int_p, _c_int_p, _c_int_p, _c_int_p, _c_int_p],
+    "fock_plan_set_tiling": [_vp, _c_int_p],
     "fock_plan_npw": [_vp, _c_i64_p],
     "fock_plan_gvectors": [_vp, _c_i32_p],
     "fock_plan_reserve": [_vp, ctypes.c_int],
@@ -267,6 +269,26 @@ def fock_plan_stats(plan):
         "chain_batch": s.chain_batch,
         "band_batch": s.band_batch,
     }
+
+
+PASSES = ("pair_fwd", "pair_col", "pair_inv")
+
+
+def fock_plan_tiling_info(plan, pass_, tile):
+    """Radix plan of tiling `tile` of pair pass `pass_` (0 fwd, 1 col, 2 inv):
+    dict(radices, threads_per_line, threads, ntiles)."""
+    r = (ctypes.c_int * 8)()
+    nst, tl, thr, nt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().fock_plan_tiling_info(plan, int(pass_), int(tile), r, ctypes.byref(nst), ctypes.byref(tl),
+                                        ctypes.byref(thr), ctypes.byref(nt)), plan)
+    return {"radices": list(r[:nst.value]), "threads_per_line": tl.value, "threads": thr.value,
+            "ntiles": nt.value}
+
+
+def fock_plan_set_tiling(plan, tiles):
+    """Tiling (0 or 1) of the forward plane, column and inverse plane passes."""
+    t = (ctypes.c_int * 3)(*[int(x) for x in tiles])
+    _check(load().fock_plan_set_tiling(plan, t), plan)
 
 
 def fock_plan_device_bytes(plan):

@@ -8,6 +8,9 @@ The knobs are the ones that decide how pair work maps onto the GPU:
 * ``band_block`` — bands per block of the pair schedule (pairs are visited in
   band_block x band_block blocks, so consecutive chains share orbitals and
   accumulators in L2);
+* ``tiling`` — the FFT tiling (radix plan and threads per line) of each of the
+  three pair passes, where the library compiled two (``FockPlan.tilings()``);
+  searched one pass at a time after the pair-block search;
 * for batches: ``persistent`` (one persistent launch for all systems, or
   size-specialised launches on one graph branch per system), ``slot_chains``
   (chains of the largest grid per transform-buffer slot of the persistent
@@ -76,29 +79,59 @@ def _time_ms(fn, reps):
     return statistics.median(out)
 
 
-def tune_apply(plan, psi, occ, chain_batches=(8, 17, 19, 32, 38), band_blocks=(8, 16, 32), reps=2,
-               use_cache=True):
-    """Fastest (chain_batch, band_block) for ``plan.apply(psi, occ)``; sets it on the plan.
+PASSES = ("pair_fwd", "pair_col", "pair_inv")
 
-    Returns ``{"chain_batch", "band_block", "ms", "table"}``.
+
+def tune_apply(plan, psi, occ, chain_batches=(8, 17, 19, 32, 38), band_blocks=(8, 16, 32), reps=2,
+               use_cache=True, tiling=True):
+    """Fastest (chain_batch, band_block) and FFT tiling for ``plan.apply(psi, occ)``;
+    sets them on the plan.
+
+    The pair-block grid is timed at the default tiling; then, one pair pass at a
+    time, the pass's other tiling is timed at the best setting so far and kept
+    if faster.  Returns ``{"chain_batch", "band_block", "tiles", "tiling", "ms",
+    "table"}``; ``tiling`` names each pass's chosen radix plan and threads per line.
     """
     key = "apply|%s|N%d|prec%d|nb%d" % (_gpu_name(), plan.grid[0], plan.precision, psi.shape[0])
+    has_tiling = tiling and hasattr(plan, "tilings")
     if use_cache:
         hit = _load_cache().get(key)
-        if hit:
+        if hit and ("tiles" in hit or not has_tiling):
             plan.set_batch(hit["chain_batch"])
             plan.set_band_block(hit["band_block"])
+            if has_tiling:
+                plan.set_tiling(hit["tiles"])
             return dict(hit, cached=True)
     table = []
+    tiles = [0, 0, 0]
+    if has_tiling:
+        plan.set_tiling(tiles)
     for cb, bb in itertools.product(chain_batches, band_blocks):
         plan.set_batch(cb)
         plan.set_band_block(bb)
         ms = _time_ms(lambda: plan.apply(psi, occ, want_ex=True), reps)
-        table.append({"chain_batch": cb, "band_block": bb, "ms": ms})
+        table.append({"chain_batch": cb, "band_block": bb, "tiles": list(tiles), "ms": ms})
     best = min(table, key=lambda r: r["ms"])
     plan.set_batch(best["chain_batch"])
     plan.set_band_block(best["band_block"])
-    res = {"chain_batch": best["chain_batch"], "band_block": best["band_block"], "ms": best["ms"],
+    best_ms = best["ms"]
+    options = plan.tilings() if has_tiling else {}
+    for p, name in enumerate(PASSES):
+        if len(options.get(name, ())) < 2:
+            continue
+        trial = list(tiles)
+        trial[p] = 1
+        plan.set_tiling(trial)
+        ms = _time_ms(lambda: plan.apply(psi, occ, want_ex=True), reps)
+        table.append({"chain_batch": best["chain_batch"], "band_block": best["band_block"], "tiles": trial,
+                      "ms": ms})
+        if ms < best_ms:
+            tiles, best_ms = trial, ms
+    if has_tiling:
+        plan.set_tiling(tiles)
+    res = {"chain_batch": best["chain_batch"], "band_block": best["band_block"], "tiles": tiles, "ms": best_ms,
+           "tiling": {name: dict(options[name][tiles[p]], tile=tiles[p])
+                      for p, name in enumerate(PASSES) if name in options},
            "table": table}
     if use_cache:
         _store_cache(key, res)
@@ -121,6 +154,9 @@ def tune_batch(plans, psi, occ, slot_chains=(4, 8, 16), rings=(3, 4), ctas_per_s
         if hit:
             for p in plans:
                 p.set_band_block(hit["band_block"])
+                if hit.get("tiles") and hasattr(p, "tilings"):
+                    t = p.tilings()
+                    p.set_tiling([hit["tiles"][j] if len(t[name]) > 1 else 0 for j, name in enumerate(PASSES)])
             return dict(hit, cached=True)
     table = []
     combos = []
@@ -142,7 +178,30 @@ def tune_batch(plans, psi, occ, slot_chains=(4, 8, 16), rings=(3, 4), ctas_per_s
     best = min(table, key=lambda r: r["ms"])
     for p in plans:
         p.set_band_block(best["band_block"])
-    res = {"options": best["options"], "band_block": best["band_block"], "ms": best["ms"], "table": table}
+    # graph branches run each plan's own size-specialised kernels: try the
+    # second FFT tiling of each pair pass on every plan that has one
+    tiles = [0, 0, 0]
+    best_ms = best["ms"]
+    if not best["options"].get("persistent", 1) and all(hasattr(p, "tilings") for p in plans):
+        two = [[len(p.tilings()[name]) > 1 for name in PASSES] for p in plans]
+        for k in range(3):
+            if not any(t[k] for t in two):
+                continue
+            trial = list(tiles)
+            trial[k] = 1
+            for p, t in zip(plans, two):
+                p.set_tiling([trial[j] if t[j] else 0 for j in range(3)])
+            b = FockBatch(plans, psi, occ, **best["options"])
+            ms = _time_ms(b.run, reps)
+            b.close()
+            torch.cuda.synchronize()
+            table.append({"band_block": best["band_block"], "options": best["options"], "tiles": trial, "ms": ms})
+            if ms < best_ms:
+                tiles, best_ms = trial, ms
+        for p, t in zip(plans, two):
+            p.set_tiling([tiles[j] if t[j] else 0 for j in range(3)])
+    res = {"options": best["options"], "band_block": best["band_block"], "tiles": tiles, "ms": best_ms,
+           "table": table}
     if use_cache:
         _store_cache(key, res)
     return res

@@ -27,7 +27,8 @@
 // of every stage, so it holds N / TL elements between the two barriers.
 //
 // Twiddles come from a table w[t] = exp(-2 pi i t / N), t < N, computed on the
-// host in FP64 and staged in shared memory; SIGN = +1 uses its conjugate.
+// host in FP64 and staged in shared memory together with its conjugate
+// (tw[N + t]), which the SIGN = +1 transforms read.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -43,6 +44,9 @@
 namespace fockx {
 
 constexpr int kMaxStages = 8;
+// The shared-memory twiddle table holds the forward table e^{-2 pi i t/N}
+// (t < N) followed by its conjugate for the inverse transforms.
+constexpr int kTwiddleTable = 2;
 constexpr int kMaxThreads = 1024;
 constexpr int kEmax = 24;  // elements a thread may hold across a stage
 
@@ -181,6 +185,12 @@ template <> struct FftTraits<df64> {
   static constexpr bool fused = false;
 };
 template <class T> using cplx = typename CplxOf<T>::type;
+
+// Elements a thread may hold across a stage for radix-plan variant EMAX (0:
+// the type's own, FftTraits<T>::emax).  A plan is named by (N, MAXT, EMAX).
+template <class T, int EMAX> __host__ __device__ constexpr int plan_emax() {
+  return EMAX > 0 ? EMAX : FftTraits<T>::emax;
+}
 
 // S * x for S = +1 or -1 (a sign flip, never a multiplication)
 template <int S, class T> FFT_HD T sgn(T x) {
@@ -449,6 +459,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* base, int t, bool active, con
   constexpr int NB = N / R;
   constexpr int PER = NB / TL;
   constexpr int TWS = N / (P * R);
+  const C* twt = SIGN > 0 ? tw + N : tw;  // the conjugate table for inverse transforms
   C x[PER][R];
   if (active) {
 #pragma unroll
@@ -467,20 +478,13 @@ __device__ __forceinline__ void fft_stage(cplx<T>* base, int t, bool active, con
       if constexpr (P > 1 && FftTraits<T>::fused) {
         C w[R];
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          w[r] = tw[r * kk * TWS];
-          if (SIGN > 0) w[r].y = -w[r].y;
-        }
+        for (int r = 1; r < R; ++r) w[r] = twt[r * kk * TWS];
         w[0] = w[1];  // not read: x_0 carries no twiddle
         Dft<SIGN, T>::template run_tw<R, false>(x[k], w);
       } else {
         if constexpr (P > 1) {
 #pragma unroll
-          for (int r = 1; r < R; ++r) {
-            C w = tw[r * kk * TWS];
-            if (SIGN > 0) w.y = -w.y;
-            x[k][r] = cmul(x[k][r], w);
-          }
+          for (int r = 1; r < R; ++r) x[k][r] = cmul(x[k][r], twt[r * kk * TWS]);
         }
         Dft<SIGN, T>::template run<R>(x[k]);
       }
@@ -500,14 +504,16 @@ __device__ __forceinline__ void fft_stage_first(cplx<T>* base, int t, bool activ
   using C = cplx<T>;
   constexpr int NB = N / R;
   constexpr int PER = NB / TL;
+  C x[PER][R];
   if (active) {
-    C x[PER][R];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const int b = t + TL * k;
 #pragma unroll
       for (int r = 0; r < R; ++r) x[k][r] = load(line, b + r * NB);
     }
+  }
+  if (active) {
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const int b = t + TL * k;
@@ -519,42 +525,72 @@ __device__ __forceinline__ void fft_stage_first(cplx<T>* base, int t, bool activ
   __syncthreads();
 }
 
-template <class T, int N, int SIGN, int TL, int ES, int S, int P, int MAXT>
+template <class T, int N, int SIGN, int TL, int ES, int S, int P, int MAXT, int EMAX = 0>
 __device__ __forceinline__ void fft_stages(cplx<T>* base, int t, bool active, const cplx<T>* tw) {
-  constexpr RadixPlan pl = make_radix_plan(N, MAXT, FftTraits<T>::emax);
+  constexpr RadixPlan pl = make_radix_plan(N, MAXT, plan_emax<T, EMAX>());
   if constexpr (S < pl.nst) {
     constexpr int R = pl.r[S];
     fft_stage<T, N, R, P, TL, ES, SIGN>(base, t, active, tw);
-    fft_stages<T, N, SIGN, TL, ES, S + 1, P * R, MAXT>(base, t, active, tw);
+    fft_stages<T, N, SIGN, TL, ES, S + 1, P * R, MAXT, EMAX>(base, t, active, tw);
   }
 }
 
 // FFT of NLINES lines of length N whose input comes from load(line, m) and
 // whose output lands in shared memory (line l at buf + l*LS, stride ES).
-template <class T, int N, int SIGN, int NLINES, int TL, int LS, int ES, int MAXT, class Load>
+template <class T, int N, int SIGN, int NLINES, int TL, int LS, int ES, int MAXT, int EMAX = 0, class Load>
 __device__ __forceinline__ void fft_lines_from(cplx<T>* buf, const cplx<T>* tw, const Load& load) {
-  constexpr RadixPlan pl = make_radix_plan(N, MAXT, FftTraits<T>::emax);
+  constexpr RadixPlan pl = make_radix_plan(N, MAXT, plan_emax<T, EMAX>());
   constexpr int R0 = pl.r[0];
   const int tid = threadIdx.x;
   const int line = tid % NLINES;
   const int t = tid / NLINES;
   const bool active = t < TL;
   fft_stage_first<T, N, R0, TL, ES, SIGN>(buf + line * LS, t, active, line, load);
-  fft_stages<T, N, SIGN, TL, ES, 1, R0, MAXT>(buf + line * LS, t, active, tw);
+  fft_stages<T, N, SIGN, TL, ES, 1, R0, MAXT, EMAX>(buf + line * LS, t, active, tw);
+}
+
+// FFT of `nlines` lines (a run-time count) whose input comes from
+// load(line, m) and whose output lands in shared memory at buf + off(line)
+// (elements ES apart).  Consecutive threads take consecutive lines, as in
+// fft_lines_from; threads beyond nlines * TL idle, so whole warps drop out when
+// fewer lines are transformed.
+template <class T, int N, int SIGN, int TL, int ES, int MAXT, int EMAX = 0, class Load, class Off>
+__device__ __forceinline__ void fft_lines_from_rt(cplx<T>* buf, const cplx<T>* tw, int nlines, const Load& load,
+                                                  const Off& off) {
+  constexpr RadixPlan pl = make_radix_plan(N, MAXT, plan_emax<T, EMAX>());
+  constexpr int R0 = pl.r[0];
+  const int tid = threadIdx.x;
+  const int line = tid % nlines;
+  const int t = tid / nlines;
+  const bool active = t < TL;
+  cplx<T>* base = buf + off(line);
+  fft_stage_first<T, N, R0, TL, ES, SIGN>(base, t, active, line, load);
+  fft_stages<T, N, SIGN, TL, ES, 1, R0, MAXT, EMAX>(base, t, active, tw);
+}
+
+// FFT in place of `nlines` lines (a run-time count) in shared memory, line l
+// at buf + off(l), elements ES apart; as fft_lines otherwise.
+template <class T, int N, int SIGN, int TL, int ES, int MAXT, int EMAX = 0, class Off>
+__device__ __forceinline__ void fft_lines_rt(cplx<T>* buf, const cplx<T>* tw, int nlines, const Off& off) {
+  const int tid = threadIdx.x;
+  const int line = tid % nlines;
+  const int t = tid / nlines;
+  const bool active = t < TL;
+  fft_stages<T, N, SIGN, TL, ES, 0, 1, MAXT, EMAX>(buf + off(line), t, active, tw);
 }
 
 // FFT of NLINES lines of length N in shared memory: line l starts at buf + l*LS,
 // its elements are ES apart.  Every thread of the CTA must call this (it
 // synchronises); threads with tid >= NLINES*TL idle.
-// MAXT names the radix plan (make_radix_plan(N, MAXT, FftTraits<T>::emax)) that
-// TL was chosen for.
-template <class T, int N, int SIGN, int NLINES, int TL, int LS, int ES, int MAXT = kMaxThreads>
+// MAXT and EMAX name the radix plan (make_radix_plan(N, MAXT, plan_emax<T,
+// EMAX>())) that TL was chosen for.
+template <class T, int N, int SIGN, int NLINES, int TL, int LS, int ES, int MAXT = kMaxThreads, int EMAX = 0>
 __device__ __forceinline__ void fft_lines(cplx<T>* buf, const cplx<T>* tw) {
   const int tid = threadIdx.x;
   const int line = tid % NLINES;
   const int t = tid / NLINES;
   const bool active = t < TL;
-  fft_stages<T, N, SIGN, TL, ES, 0, 1, MAXT>(buf + line * LS, t, active, tw);
+  fft_stages<T, N, SIGN, TL, ES, 0, 1, MAXT, EMAX>(buf + line * LS, t, active, tw);
 }
 
 }  // namespace fockx

@@ -47,6 +47,16 @@ struct DevPlan {
   const int* ncol;
   const int* colmap;
   int ncta_col;
+  // rows k2 that have kept columns are [0, row_lo) and [N - row_hi, N) (a
+  // ball centred on G = 0 reaches a symmetric range of m2; row_lo = N,
+  // row_hi = 0 when every row is kept); col_max = the largest ncol[k2]
+  int row_lo, row_hi, col_max;
+  // the kept columns (k2 << 16) | k3 in row order (nkept entries)
+  const int* kept;
+  int nkept;
+  // radix-plan variant ("tiling", 0 or 1) of the forward plane, column and
+  // inverse plane passes
+  int tile[3];
   // deterministic accumulation: W holds 64-bit fixed point scaled by det_scale[0]
   // (= 2^s), the column pass stores per-CTA energy partials at [pair * ncta_col + cta]
   int det;
@@ -77,6 +87,10 @@ struct KernelOps {
   // W(r) of bands [band0, band0 + nbat) to (V_x psi)(G) on the sphere.
   cudaError_t (*to_sphere)(const DevPlan&, const void* W, int nb, int band0, int nbat, void* X,
                            double2* vpsiG, cudaStream_t);
+  // radix plan of a tiling of a pair pass (pass 0 fwd, 1 col, 2 inv; tile 0/1):
+  // radices[nst], threads per line, threads per CTA; returns the number of
+  // distinct tilings (1 or 2)
+  int (*tile_plan)(int pass, int tile, int* radices, int* nst, int* threads_per_line, int* threads);
 };
 
 // Kernels for grid size n and precision (0: FP64, 1: mixed); NULL if not built.

@@ -60,6 +60,40 @@ template <> __device__ __forceinline__ cdf64 ldcg_c<cdf64>(const cdf64* p) {
   return r;
 }
 
+// L2 eviction priorities (createpolicy): evict_first for data read for the last
+// time (the transform buffer in the inverse pass), evict_last for data the next
+// chains of a band block read again (orbital and accumulator planes).
+__device__ __forceinline__ unsigned long long l2_policy_evict_first() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_policy_evict_last() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// ld.global.cg of one complex value with an L2 eviction policy.
+template <class C> __device__ __forceinline__ C ldcg_hint(const C* p, unsigned long long pol);
+template <> __device__ __forceinline__ float2 ldcg_hint<float2>(const float2* p, unsigned long long pol) {
+  float2 v;
+  asm volatile("ld.global.cg.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+template <> __device__ __forceinline__ double2 ldcg_hint<double2>(const double2* p, unsigned long long pol) {
+  double2 v;
+  asm volatile("ld.global.cg.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+// Four floats with an L2 eviction policy (16-byte aligned).
+__device__ __forceinline__ float4 ld_f4_hint(const float* p, unsigned long long pol) {
+  float4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+
 template <class T> __device__ __forceinline__ void atomic_add_real(T* p, T v) { atomicAdd(p, v); }
 // df64 into an FP64 accumulator: both parts become doubles by integer
 // instructions, one FP64 add joins them (exact to the rounding of that add).
@@ -125,11 +159,12 @@ __device__ inline void block_sum4_df(df64 v[4], float* red) {
   }
 }
 
-// Compile-time geometry of the passes for grid size N.
-template <class T, int N, int MAXT = kMaxThreads>
+// Compile-time geometry of the passes for grid size N and radix-plan variant
+// EMAX (elements a thread holds across a stage; 0: the type's own).
+template <class T, int N, int MAXT = kMaxThreads, int EMAX = 0>
 struct Geo {
   using C = cplx<T>;
-  static constexpr RadixPlan pl = make_radix_plan(N, MAXT, FftTraits<T>::emax);
+  static constexpr RadixPlan pl = make_radix_plan(N, MAXT, plan_emax<T, EMAX>());
   static_assert(pl.nst > 0, "grid size must be 2^a 3^b and fit the FFT kernels");
   static constexpr int KH = N / 2 + 1;                    // stored half of the last axis
   static constexpr int NC = 2 * KH;                       // stored columns per row (A and B)
@@ -142,23 +177,26 @@ struct Geo {
   static constexpr int THR_COLH = (NC * TLC + 31) / 32 * 32;
   static constexpr int THR_COLF = (N * TLP + 31) / 32 * 32;
   static_assert(THR_PLANE <= 1024 && THR_COLH <= 1024, "CTA too large");
-  // CTAs per SM the column pass is register-budgeted for (shared memory allows
-  // two in FP32 up to N = 96, one in FP64)
-  static constexpr int MIN_CTAS = (sizeof(T) == 4) ? 2 : 1;
+  // CTAs per SM the column and inverse passes are register-budgeted for
+  // (shared memory allows two in FP32 up to N = 96, one in FP64): two when two
+  // CTAs of 72 registers a thread fit the register file
+  static constexpr int MIN_CTAS = (sizeof(T) == 4 && 2 * 72 * THR_COLH <= 65536) ? 2 : 1;
   // CTAs per SM the k-point inverse plane pass is register-budgeted for: in
   // FP32, eight where eight CTAs of 40 registers a thread fit the register file
   // (its shared memory allows that many up to N = 48); 0 leaves the choice to
   // the compiler, as a bound without a minimum does (a minimum of 1 changes
   // its register allocation: 89 instead of 78 registers at 96^3 in FP32)
   static constexpr int MIN_CTAS_KINV = (sizeof(T) == 4 && 8 * 40 * THR_PLANE <= 65536) ? 8 : 0;
-  static constexpr size_t SMEM_PLANE = sizeof(C) * (size_t)(N * RP + N);
+  // twiddle table in shared memory: e^{-2 pi i t/N} and its conjugate (2N values)
+  static constexpr int TWN = kTwiddleTable * N;
+  static constexpr size_t SMEM_PLANE = sizeof(C) * (size_t)(N * RP + TWN);
   static constexpr size_t SMEM_COLH =
-      sizeof(C) * (size_t)(N * NC + N) + 32 * 4 * sizeof(double) + NC * sizeof(int);
-  static constexpr size_t SMEM_COLF = sizeof(C) * (size_t)(N * N + N);
+      sizeof(C) * (size_t)(N * NC + TWN) + 32 * 4 * sizeof(double) + NC * sizeof(int);
+  static constexpr size_t SMEM_COLF = sizeof(C) * (size_t)(N * N + TWN);
   // inverse plane pass: the stored half plane with an odd row stride NC + 1,
   // the twiddles and the column map's row lengths
   static constexpr int NCP = NC + 1;
-  static constexpr size_t SMEM_INV = sizeof(C) * (size_t)(N * NCP + N) + N * sizeof(int);
+  static constexpr size_t SMEM_INV = sizeof(C) * (size_t)(N * NCP + TWN) + N * sizeof(int);
 };
 
 // Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
@@ -241,10 +279,17 @@ __device__ __noinline__ void small_g_term_fp64(const DevPlan& g, cplx<T>* S, int
   S[e] = z;
 }
 
+// Stage the twiddle table in shared memory: tw[t] = e^{-2 pi i t/N} for the
+// forward transforms, tw[N + t] = its conjugate for the inverse ones, so no
+// transform negates a twiddle where it uses it.
 template <class T>
 __device__ __forceinline__ void load_twiddles(cplx<T>* tw, const DevPlan& g) {
   const cplx<T>* src = static_cast<const cplx<T>*>(g.tw);
-  for (int t = threadIdx.x; t < g.n; t += blockDim.x) tw[t] = src[t];
+  for (int t = threadIdx.x; t < g.n; t += blockDim.x) {
+    const cplx<T> w = src[t];
+    tw[t] = w;
+    tw[g.n + t] = cmake<T>(w.x, -w.y);
+  }
 }
 
 // ---------------------------------------------------------------- O(nb) passes
@@ -354,12 +399,12 @@ __global__ void k_gather(DevPlan g, const cplx<T>* __restrict__ X, int nb, int b
 
 // One task of the forward plane pass: plane i1 of chain `ch`, whose transform
 // buffer is Hc.  Shared memory: Geo::SMEM_PLANE bytes at smem_raw.
-template <class T, int N, int MAXT>
+template <class T, int N, int MAXT, int EMAX = 0>
 __device__ __forceinline__ void pair_fwd_task(const DevPlan& g, const T* __restrict__ psi,
                                               const Chain& ch, cplx<T>* __restrict__ Hc, int i1,
                                               unsigned char* smem_raw) {
   using C = cplx<T>;
-  using G = Geo<T, N, MAXT>;
+  using G = Geo<T, N, MAXT, EMAX>;
   constexpr int RP = G::RP, KH = G::KH, NC = G::NC;
   C* P = reinterpret_cast<C*>(smem_raw);
   C* tw = P + N * RP;
@@ -373,16 +418,27 @@ __device__ __forceinline__ void pair_fwd_task(const DevPlan& g, const T* __restr
   // Columns first: the first stage along i2 reads the pair product straight
   // from the orbital planes (a warp's lines are consecutive columns i3, so the
   // loads coalesce) and leaves its outputs in shared memory; then the rows.
-  const auto product = [&](int i3, int i2) {
-    const int e = i2 * N + i3;
-    return cmake<T>(pai[e] * paj[e], hb ? pbi[e] * pbj[e] : T(0));
+  // this thread's column i3 (line-fast mapping of the transform along i2)
+  const int c3 = threadIdx.x % N;
+  const T* qai = pai + c3;
+  const T* qaj = paj + c3;
+  const T* qbi = pbi + c3;
+  const T* qbj = pbj + c3;
+  const auto product = [&](int, int i2) {
+    return cmake<T>(qai[i2 * N] * qaj[i2 * N], hb ? qbi[i2 * N] * qbj[i2 * N] : T(0));
   };
-  fft_lines_from<T, N, -1, N, G::TLP, 1, RP, MAXT>(P, tw, product);  // along i2
-  fft_lines<T, N, -1, N, G::TLP, RP, 1, MAXT>(P, tw);                // along i3
+  fft_lines_from<T, N, -1, N, G::TLP, 1, RP, MAXT, EMAX>(P, tw, product);  // along i2
+  // along i3: only the rows k2 that hold kept columns, [0, row_lo) and
+  // [N - row_hi, N) (the split below reads row k2 and its mirror N - k2, both in)
+  const int rlo = g.row_lo, nrows = g.row_lo + g.row_hi;
+  const auto row_off = [&](int l) { return (l < rlo ? l : l + (N - nrows)) * RP; };
+  fft_lines_rt<T, N, -1, G::TLP, 1, MAXT, EMAX>(P, tw, nrows, row_off);
   C* Hp = Hc + (int64_t)i1 * N * NC;
-  for (int e = threadIdx.x; e < N * KH; e += blockDim.x) {
-    const int k2 = e / KH, k3 = e - k2 * KH;
-    if (k3 >= __ldg(g.ncol + k2)) continue;  // a column no pair density reaches
+  // split by Hermitian symmetry over the list of kept columns (k2, k3): every
+  // lane busy, consecutive threads on consecutive k3 of a row
+  for (int e = threadIdx.x; e < g.nkept; e += blockDim.x) {
+    const int code = __ldg(g.kept + e);
+    const int k2 = code >> 16, k3 = code & 0xffff;
     const int m2 = k2 == 0 ? 0 : N - k2, m3 = k3 == 0 ? 0 : N - k3;
     const C z = P[k2 * RP + k3], zm = P[m2 * RP + m3];
     Hp[k2 * NC + k3] = cmake<T>(half_of(z.x + zm.x), half_of(z.y - zm.y));
@@ -390,13 +446,13 @@ __device__ __forceinline__ void pair_fwd_task(const DevPlan& g, const T* __restr
   }
 }
 
-template <class T, int N>
-__global__ void __launch_bounds__(Geo<T, N>::THR_PLANE)
+template <class T, int N, int EMAX = 0>
+__global__ void __launch_bounds__(Geo<T, N, kMaxThreads, EMAX>::THR_PLANE)
     k_pair_fwd(DevPlan g, const T* __restrict__ psi, const Chain* __restrict__ chains,
                cplx<T>* __restrict__ H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Chain ch = chains[blockIdx.y];
-  pair_fwd_task<T, N, kMaxThreads>(g, psi, ch, H + (int64_t)blockIdx.y * g.hsize, blockIdx.x, smem_raw);
+  pair_fwd_task<T, N, kMaxThreads, EMAX>(g, psi, ch, H + (int64_t)blockIdx.y * g.hsize, blockIdx.x, smem_raw);
 }
 
 // Publish a CTA's energy partials (thread 0): atomically into the pair slots,
@@ -439,12 +495,11 @@ __device__ __forceinline__ int line_k2(int code) { return code >> 16; }
 __device__ __forceinline__ int line_s(int code) { return (code >> 15) & 1; }
 __device__ __forceinline__ int line_k3(int code) { return code & 0x7fff; }
 
-// Stage the CTA's line codes in shared memory, then its lines of the transform
-// buffer (all i1) into S[i1][l]; lines without a code are zero.
-// Asynchronous global-to-shared copies (cp.async) for the column-pass loads of
-// the stand-alone kernels: every element of a thread is in flight at once, no
-// register holds it.  Inside the persistent kernel the loads stay ld.global.cg
-// (the buffer was written earlier by the same launch, so L1 must not serve it).
+// Asynchronous global-to-shared copies (cp.async) for the double-float
+// inverse plane pass of the stand-alone kernels: every element of a thread is
+// in flight at once, no register holds it.  Inside the persistent kernel the
+// loads stay ld.global.cg (the buffer was written earlier by the same launch,
+// so L1 must not serve it).
 constexpr bool kColAsync = true;
 // The column and inverse passes read their first transform stage straight from
 // the transform buffer (no staging pass through shared memory).  Measured at
@@ -462,103 +517,60 @@ __device__ __forceinline__ void col_codes(const DevPlan& g, int cta, int* codes)
   __syncthreads();
 }
 
-// Element i1 of column-pass line l (zero for a line without a code).
+// The column of Hc that this thread's line of the column pass reads and
+// writes (the line-fast thread mapping of the transforms: line tid mod NC),
+// or NULL for a line without a code.  codes must be staged.
 template <class C, int N, int NC>
-__device__ __forceinline__ C col_value(const C* __restrict__ Hc, const int* codes, int l, int i1) {
-  const int code = codes[l];
-  C v;
-  if (code >= 0) {
-    v = ldcg_c(Hc + ((int64_t)i1 * N + line_k2(code)) * NC + line_s(code) * (NC / 2) + line_k3(code));
-  } else {
-    v.x = 0;
-    v.y = 0;
-  }
-  return v;
+__device__ __forceinline__ C* col_line_ptr(C* Hc, const int* codes) {
+  constexpr int KH = NC / 2;
+  const int code = codes[threadIdx.x % NC];
+  return code >= 0 ? Hc + line_k2(code) * NC + line_s(code) * KH + line_k3(code) : nullptr;
 }
 
-template <class C, int N, int NC, bool ASYNC>
-__device__ __forceinline__ void col_load(const DevPlan& g, const C* __restrict__ Hc, int cta, int* codes,
-                                         C* S) {
-  constexpr int KH = NC / 2;
-  for (int l = threadIdx.x; l < NC; l += blockDim.x) codes[l] = __ldg(g.colmap + cta * NC + l);
-  __syncthreads();
-  if constexpr (ASYNC) {
-    static_assert(sizeof(C) == 8 || sizeof(C) == 16, "cp.async copies 8 or 16 bytes");
-    for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
-      const int i1 = e / NC, l = e - i1 * NC;
-      const int code = codes[l];
-      // a line without a code copies zero bytes: the destination is zero-filled
-      const C* src = code >= 0 ? Hc + ((int64_t)i1 * N + line_k2(code)) * NC + line_s(code) * KH + line_k3(code)
-                               : Hc;
-      const unsigned dst = (unsigned)__cvta_generic_to_shared(S + e);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst), "l"(src), "n"((int)sizeof(C)),
-                   "r"(code >= 0 ? (int)sizeof(C) : 0)
-                   : "memory");
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
-    return;
-  }
-  for (int e0 = threadIdx.x; e0 < N * NC; e0 += kLoadUnroll * blockDim.x) {
-    C v[kLoadUnroll];
-#pragma unroll
-    for (int u = 0; u < kLoadUnroll; ++u) {
-      const int e = e0 + u * blockDim.x;
-      if (e < N * NC) {
-        const int i1 = e / NC, l = e - i1 * NC;
-        const int code = codes[l];
-        if (code >= 0) {
-          v[u] = ldcg_c(Hc + ((int64_t)i1 * N + line_k2(code)) * NC + line_s(code) * KH + line_k3(code));
-        } else {
-          v[u].x = 0;
-          v[u].y = 0;
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kLoadUnroll; ++u) {
-      const int e = e0 + u * blockDim.x;
-      if (e < N * NC) S[e] = v[u];
-    }
-  }
-  __syncthreads();
-}
-
-template <class C, int N, int NC>
-__device__ __forceinline__ void col_store(C* __restrict__ Hc, const int* codes, const C* S) {
-  constexpr int KH = NC / 2;
-  for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
-    const int i1 = e / NC, l = e - i1 * NC;
-    const int code = codes[l];
-    if (code >= 0) Hc[((int64_t)i1 * N + line_k2(code)) * NC + line_s(code) * KH + line_k3(code)] = S[e];
+// Store the transformed lines: thread (line l, sub-thread t) writes elements
+// i1 = t, t + TL, ... of its own line (consecutive lanes hold consecutive
+// lines, so both the shared reads and the global writes are contiguous).
+template <class C, int N, int NC, int TL>
+__device__ __forceinline__ void col_store_lines(C* lp, const C* S) {
+  const int l = threadIdx.x % NC, t = threadIdx.x / NC;
+  if (lp != nullptr && t < TL) {
+#pragma unroll 4
+    for (int i1 = t; i1 < N; i1 += TL) lp[(int64_t)i1 * N * NC] = S[i1 * NC + l];
   }
 }
 
 // The column pass in double-float arithmetic: the df64 tables of v / Ntot and
 // dv/domega, per-thread double-float energy sums that are reduced (in FP64)
 // before the inverse transform, so they hold no registers across it.
-template <int N, int MAXT>
+template <int N, int MAXT, int EMAX = 0>
 __device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __restrict__ Hc, const Chain& ch,
                                                  int cta, double* __restrict__ epair, double* __restrict__ dpair,
                                                  unsigned char* smem_raw) {
   using C = cdf64;
-  using G = Geo<df64, N, MAXT>;
+  using G = Geo<df64, N, MAXT, EMAX>;
   constexpr int KH = G::KH, NC = G::NC;
   C* S = reinterpret_cast<C*>(smem_raw);
   C* tw = S + N * NC;
-  double* red = reinterpret_cast<double*>(tw + N);
+  double* red = reinterpret_cast<double*>(tw + G::TWN);
   int* codes = reinterpret_cast<int*>(red + 32 * 4);
   load_twiddles<df64>(tw, g);
   const bool want_d = g.dvtab64 != nullptr;
   const df64* vt = static_cast<const df64*>(g.vtab);    // v / Ntot
   const df64* dvt = static_cast<const df64*>(g.dvtab);  // dv/domega
-  if constexpr (kFirstStageDirect) {
-    col_codes<NC>(g, cta, codes);
-    const auto val = [&](int l, int i1) { return col_value<C, N, NC>(Hc, codes, l, i1); };
-    fft_lines_from<df64, N, -1, NC, G::TLC, 1, NC, MAXT>(S, tw, val);  // along i1
-  } else {
-    col_load<C, N, NC, kColAsync && MAXT == kMaxThreads>(g, Hc, cta, codes, S);
-    fft_lines<df64, N, -1, NC, G::TLC, 1, NC, MAXT>(S, tw);  // along i1
+  col_codes<NC>(g, cta, codes);
+  {
+    const C* lp = col_line_ptr<C, N, NC>(Hc, codes);
+    const auto val = [&](int, int i1) {
+      C v;
+      if (lp != nullptr) {
+        v = ldcg_c(lp + (int64_t)i1 * N * NC);
+      } else {
+        v.x = df64(0.f);
+        v.y = df64(0.f);
+      }
+      return v;
+    };
+    fft_lines_from<df64, N, -1, NC, G::TLC, 1, NC, MAXT, EMAX>(S, tw, val);  // along i1
   }
   {
     df64 accd[4] = {df64(0.f), df64(0.f), df64(0.f), df64(0.f)};
@@ -599,30 +611,39 @@ __device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __rest
       put_energies(g, ch, cta, acc, want_d, epair, dpair);
     }
   }
-  fft_lines<df64, N, +1, NC, G::TLC, 1, NC, MAXT>(S, tw);  // inverse along k1
-  col_store<C, N, NC>(Hc, codes, S);
+  fft_lines<df64, N, +1, NC, G::TLC, 1, NC, MAXT, EMAX>(S, tw);  // inverse along k1
+  col_store_lines<C, N, NC, G::TLC>(col_line_ptr<C, N, NC>(Hc, codes), S);
 }
 
 // The column pass in FP64 or in the mixed form.
-template <class T, int N, int MAXT>
+template <class T, int N, int MAXT, int EMAX = 0>
 __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __restrict__ Hc,
                                                   const Chain& ch, int cta, double* __restrict__ epair,
                                                   double* __restrict__ dpair, unsigned char* smem_raw) {
   using C = cplx<T>;
-  using G = Geo<T, N, MAXT>;
+  using G = Geo<T, N, MAXT, EMAX>;
   constexpr int KH = G::KH, NC = G::NC;
   C* S = reinterpret_cast<C*>(smem_raw);
   C* tw = S + N * NC;
-  double* red = reinterpret_cast<double*>(tw + N);
+  double* red = reinterpret_cast<double*>(tw + G::TWN);
   int* codes = reinterpret_cast<int*>(red + 32 * 4);
   load_twiddles<T>(tw, g);
-  if constexpr (kFirstStageDirect) {
-    col_codes<NC>(g, cta, codes);
-    const auto val = [&](int l, int i1) { return col_value<C, N, NC>(Hc, codes, l, i1); };
-    fft_lines_from<T, N, -1, NC, G::TLC, 1, NC, MAXT>(S, tw, val);  // along i1
-  } else {
-    col_load<C, N, NC, kColAsync && MAXT == kMaxThreads>(g, Hc, cta, codes, S);
-    fft_lines<T, N, -1, NC, G::TLC, 1, NC, MAXT>(S, tw);  // along i1
+  col_codes<NC>(g, cta, codes);
+  {
+    // the first stage reads this thread's line straight from the transform
+    // buffer: one base pointer per thread, compile-time offsets per element
+    const C* lp = col_line_ptr<C, N, NC>(Hc, codes);
+    const auto val = [&](int, int i1) {
+      C v;
+      if (lp != nullptr) {
+        v = ldcg_c(lp + (int64_t)i1 * N * NC);
+      } else {
+        v.x = 0;
+        v.y = 0;
+      }
+      return v;
+    };
+    fft_lines_from<T, N, -1, NC, G::TLC, 1, NC, MAXT, EMAX>(S, tw, val);  // along i1
   }
 
   // kernel multiply and energy partials
@@ -672,22 +693,39 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
       const T* vl = vt + k2 * KH + k3;
       const T* dvl = dvt + k2 * KH + k3;
       T e_sum = T(0), d_sum = T(0);
-      for (int k1 = threadIdx.x / NC; k1 < N; k1 += kstep) {
-        const int e = k1 * NC + l;
-        const int m1 = freq_of(k1, N);
-        if (m1 * m1 + r23 <= g.msmall2) {
-          if (s == 0 || ch.bi >= 0) small_g_term_fp64<T, N>(g, S, e, k1, k2, k3, s, ch, epair, dpair);
-          continue;
+      if (r23 > g.msmall2) {  // no term of this line is a small-|G| one
+        const int k10 = threadIdx.x / NC;
+        const T* vp = vl + k10 * N * KH;
+        const T* dvp = dvl + k10 * N * KH;
+        C* sp = S + k10 * NC + l;
+        for (int k1 = k10; k1 < N; k1 += kstep, vp += kstep * N * KH, dvp += kstep * N * KH, sp += kstep * NC) {
+          C z = *sp;
+          const T a2 = z.x * z.x + z.y * z.y;
+          const T v = *vp;
+          e_sum += v * a2;
+          if (want_d) d_sum += *dvp * a2;
+          z.x *= v;
+          z.y *= v;
+          *sp = z;
         }
-        const int vo = k1 * N * KH;
-        C z = S[e];
-        const T a2 = z.x * z.x + z.y * z.y;
-        const T v = vl[vo];
-        e_sum += v * a2;
-        if (want_d) d_sum += dvl[vo] * a2;
-        z.x *= v;
-        z.y *= v;
-        S[e] = z;
+      } else {
+        for (int k1 = threadIdx.x / NC; k1 < N; k1 += kstep) {
+          const int e = k1 * NC + l;
+          const int m1 = freq_of(k1, N);
+          if (m1 * m1 + r23 <= g.msmall2) {
+            if (s == 0 || ch.bi >= 0) small_g_term_fp64<T, N>(g, S, e, k1, k2, k3, s, ch, epair, dpair);
+            continue;
+          }
+          const int vo = k1 * N * KH;
+          C z = S[e];
+          const T a2 = z.x * z.x + z.y * z.y;
+          const T v = vl[vo];
+          e_sum += v * a2;
+          if (want_d) d_sum += dvl[vo] * a2;
+          z.x *= v;
+          z.y *= v;
+          S[e] = z;
+        }
       }
       if (s) {
         accf[1] = wgt * e_sum;
@@ -705,8 +743,8 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
     acc_f32[3] = accf[3];
   }
   __syncthreads();
-  fft_lines<T, N, +1, NC, G::TLC, 1, NC, MAXT>(S, tw);  // inverse along k1
-  col_store<C, N, NC>(Hc, codes, S);
+  fft_lines<T, N, +1, NC, G::TLC, 1, NC, MAXT, EMAX>(S, tw);  // inverse along k1
+  col_store_lines<C, N, NC, G::TLC>(col_line_ptr<C, N, NC>(Hc, codes), S);
   if constexpr (RealTraits<T>::prec != 1) {
     block_sum4(acc, red);
   } else {
@@ -722,59 +760,64 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
 
 // One task of the column pass: the NC lines `cta` of the column map for chain
 // `ch` (transform buffer Hc).  Shared memory: Geo::SMEM_COLH bytes at smem_raw.
-template <class T, int N, int MAXT>
+template <class T, int N, int MAXT, int EMAX = 0>
 __device__ __forceinline__ void pair_col_task(const DevPlan& g, cplx<T>* __restrict__ Hc,
                                               const Chain& ch, int cta, double* __restrict__ epair,
                                               double* __restrict__ dpair, unsigned char* smem_raw) {
   if constexpr (RealTraits<T>::prec == 2) {
-    pair_col_task_df<N, MAXT>(g, Hc, ch, cta, epair, dpair, smem_raw);
+    pair_col_task_df<N, MAXT, EMAX>(g, Hc, ch, cta, epair, dpair, smem_raw);
   } else {
-    pair_col_task_std<T, N, MAXT>(g, Hc, ch, cta, epair, dpair, smem_raw);
+    pair_col_task_std<T, N, MAXT, EMAX>(g, Hc, ch, cta, epair, dpair, smem_raw);
   }
 }
 
-template <class T, int N>
-__global__ void __launch_bounds__(Geo<T, N>::THR_COLH, Geo<T, N>::MIN_CTAS)
+template <class T, int N, int EMAX = 0>
+__global__ void __launch_bounds__(Geo<T, N, kMaxThreads, EMAX>::THR_COLH, Geo<T, N, kMaxThreads, EMAX>::MIN_CTAS)
     k_pair_col(DevPlan g, cplx<T>* __restrict__ H, const Chain* __restrict__ chains,
                double* __restrict__ epair, double* __restrict__ dpair) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Chain ch = chains[blockIdx.y];
-  pair_col_task<T, N, kMaxThreads>(g, H + (int64_t)blockIdx.y * g.hsize, ch, blockIdx.x, epair, dpair,
-                                   smem_raw);
+  pair_col_task<T, N, kMaxThreads, EMAX>(g, H + (int64_t)blockIdx.y * g.hsize, ch, blockIdx.x, epair, dpair,
+                                         smem_raw);
 }
 
 // One task of the inverse plane pass: plane i1 of chain `ch` (transform buffer
 // Hc), accumulating into W.  Shared memory: Geo::SMEM_PLANE bytes at smem_raw.
-template <class T, int N, int MAXT>
+template <class T, int N, int MAXT, int EMAX = 0>
 __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restrict__ psi,
                                               acc_t<T>* __restrict__ W, const T* __restrict__ occ,
                                               const Chain& ch, const cplx<T>* __restrict__ Hc, int i1,
                                               unsigned char* smem_raw) {
   using C = cplx<T>;
-  using G = Geo<T, N, MAXT>;
+  using G = Geo<T, N, MAXT, EMAX>;
   constexpr int KH = G::KH, NC = G::NC, NCP = G::NCP;
   C* Q = reinterpret_cast<C*>(smem_raw);
   C* tw = Q + N * NCP;
-  int* ncol = reinterpret_cast<int*>(tw + N);
+  int* ncol = reinterpret_cast<int*>(tw + G::TWN);
   load_twiddles<T>(tw, g);
   for (int r = threadIdx.x; r < N; r += blockDim.x) ncol[r] = __ldg(g.ncol + r);
   __syncthreads();
   const C* Hp = Hc + (int64_t)i1 * N * NC;
   // 1-2. the stored half plane, row k2 = [A(k2, 0..N/2) | B(k2, 0..N/2)],
   //    columns no pair density reaches (never written) read as zero, and its
-  //    inverse transform along k2 into Q[k2][c] (odd row stride NCP)
+  //    inverse transform along k2 into Q[k2][c] (odd row stride NCP).  Only
+  //    the columns k3 < col_max of A and B hold anything: 2 col_max lines are
+  //    transformed, line l being column l (A) or KH + l - col_max (B).
+  const int cm = g.col_max;
+  const auto col_of = [&](int l) { return l < cm ? l : KH + (l - cm); };
   if constexpr (inv_first_stage_direct<T>()) {
-    const auto val = [&](int c, int k2) {
+    const unsigned long long last_use = l2_policy_evict_first();  // H is dead after this read
+    const auto val = [&](int l, int k2) {
       C v;
-      if ((c < KH ? c : c - KH) < ncol[k2]) {
-        v = ldcg_c(Hp + k2 * NC + c);
+      if ((l < cm ? l : l - cm) < ncol[k2]) {
+        v = ldcg_hint(Hp + k2 * NC + col_of(l), last_use);
       } else {
         v.x = 0;
         v.y = 0;
       }
       return v;
     };
-    fft_lines_from<T, N, +1, NC, G::TLC, 1, NCP, MAXT>(Q, tw, val);
+    fft_lines_from_rt<T, N, +1, G::TLC, NCP, MAXT, EMAX>(Q, tw, 2 * cm, val, col_of);
   } else {
   if constexpr (kColAsync && MAXT == kMaxThreads) {
     for (int e = threadIdx.x; e < N * NC; e += blockDim.x) {
@@ -809,11 +852,12 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
     }
   }
   __syncthreads();
-  fft_lines<T, N, +1, NC, G::TLC, 1, NCP, MAXT>(Q, tw);  // inverse transform along k2
+  fft_lines_rt<T, N, +1, G::TLC, NCP, MAXT, EMAX>(Q, tw, 2 * cm, col_of);  // inverse transform along k2
   }
   // 3. rows: z(k3) = A^(k3) + i B^(k3) for k3 <= N/2 and, from the Hermitian
   //    symmetry of the transforms of the real planes, z(N - k3) =
-  //    conj(A^(k3)) + i conj(B^(k3)); one warp per row (reads, then writes)
+  //    conj(A^(k3)) + i conj(B^(k3)); one warp per row (reads, then writes);
+  //    columns k3 >= col_max were not transformed and hold nothing
   {
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     static_assert(N / 2 + 1 <= 64, "two stored columns per lane");
@@ -823,9 +867,12 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const int k = lane + 32 * t;
-        if (k < KH) {
+        if (k < cm) {
           av[t] = row[k];
           bv[t] = row[KH + k];
+        } else {
+          av[t] = cmake<T>(T(0), T(0));
+          bv[t] = av[t];
         }
       }
       __syncwarp();
@@ -842,7 +889,7 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
   }
   __syncthreads();
   // 4. inverse transform along k3 of the N rows: Q[i2][i3] = phi_a + i phi_b
-  fft_lines<T, N, +1, N, G::TLP, NCP, 1, MAXT>(Q, tw);
+  fft_lines<T, N, +1, N, G::TLP, NCP, 1, MAXT, EMAX>(Q, tw);
   const int64_t plane0 = (int64_t)i1 * N * N;
   const bool hb = ch.bi >= 0;
   // Up to four updates k, W[tgt_k] -= f[src_k] psi[src_k] phi:
@@ -868,14 +915,17 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
     wt[k] = W + (int64_t)(tgt[k] >= 0 ? tgt[k] : 0) * g.ntot + plane0;
   }
   if constexpr (RealTraits<T>::prec == 1) {
+    // four consecutive points per thread: 16-byte loads of the orbitals and
+    // one red.global.add.v4.f32 per target
     static_assert(N % 4 == 0, "vector updates need N divisible by 4");
+    const unsigned long long keep = l2_policy_evict_last();  // orbitals and accumulators of the band block
     for (int e4 = threadIdx.x; e4 < N * N / 4; e4 += blockDim.x) {
       const int e = 4 * e4;
       const int i2 = e / N, i3 = e - i2 * N;
       float4 phia, phib;
       {
-        const C z0 = Q[i2 * NCP + i3], z1 = Q[i2 * NCP + i3 + 1], z2 = Q[i2 * NCP + i3 + 2],
-                z3 = Q[i2 * NCP + i3 + 3];
+        const C* q = Q + i2 * NCP + i3;
+        const C z0 = q[0], z1 = q[1], z2 = q[2], z3 = q[3];
         phia = make_float4(z0.x, z1.x, z2.x, z3.x);
         phib = make_float4(z0.y, z1.y, z2.y, z3.y);
       }
@@ -884,7 +934,7 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
       for (int k = 0; k < 4; ++k) {
         c[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (tgt[k] < 0) continue;
-        const float4 p = *reinterpret_cast<const float4*>(ps[k] + e);
+        const float4 p = ld_f4_hint(ps[k] + e, keep);
         const float4 ph = k < 2 ? phia : phib;
         const float m = -f[k];
         c[k] = make_float4(m * p.x * ph.x, m * p.y * ph.y, m * p.z * ph.z, m * p.w * ph.w);
@@ -903,8 +953,8 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
           }
         }
         float* dst = wt[r] + e;
-        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(a.x), "f"(a.y),
-                     "f"(a.z), "f"(a.w)
+        asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(dst), "f"(a.x),
+                     "f"(a.y), "f"(a.z), "f"(a.w), "l"(keep)
                      : "memory");
       }
     }
@@ -940,14 +990,37 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
   }
 }
 
-template <class T, int N>
-__global__ void __launch_bounds__(Geo<T, N>::THR_COLH, Geo<T, N>::MIN_CTAS)
+template <class T, int N, int EMAX = 0>
+__global__ void __launch_bounds__(Geo<T, N, kMaxThreads, EMAX>::THR_COLH, Geo<T, N, kMaxThreads, EMAX>::MIN_CTAS)
     k_pair_inv(DevPlan g, const T* __restrict__ psi, acc_t<T>* __restrict__ W, const T* __restrict__ occ,
                const Chain* __restrict__ chains, const cplx<T>* __restrict__ H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Chain ch = chains[blockIdx.y];
-  pair_inv_task<T, N, kMaxThreads>(g, psi, W, occ, ch, H + (int64_t)blockIdx.y * g.hsize, blockIdx.x,
-                                   smem_raw);
+  pair_inv_task<T, N, kMaxThreads, EMAX>(g, psi, W, occ, ch, H + (int64_t)blockIdx.y * g.hsize, blockIdx.x,
+                                         smem_raw);
+}
+
+// ------------------------------------------------------------ FFT tilings
+//
+// Each pair pass can run one of two radix plans ("tilings"): tile 0 is the
+// type's own (FftTraits::emax elements per thread), tile 1 the plan found
+// with the other element budget (12 for FP32, 24 for FP64; none for the
+// double-float form).  When both budgets give the same plan for N, tile 1 is
+// tile 0 and no second kernel is compiled.
+template <class T> constexpr int alt_emax() {
+  return RealTraits<T>::prec == 1 ? 12 : (RealTraits<T>::prec == 0 ? 24 : 0);
+}
+constexpr bool same_plan(const RadixPlan& a, const RadixPlan& b) {
+  if (a.nst != b.nst || a.tl_plane != b.tl_plane || a.tl_colh != b.tl_colh) return false;
+  for (int k = 0; k < a.nst; ++k)
+    if (a.r[k] != b.r[k]) return false;
+  return true;
+}
+template <class T, int N> constexpr int tile1_emax() {
+  return (alt_emax<T>() == 0 ||
+          same_plan(Geo<T, N>::pl, Geo<T, N, kMaxThreads, alt_emax<T>()>::pl))
+             ? 0
+             : alt_emax<T>();
 }
 
 // ------------------------------------------------------------------ launchers
@@ -958,21 +1031,41 @@ template <class T, int N>
 struct Launch {
   using C = cplx<T>;
   using G = Geo<T, N>;
+  static constexpr int E1 = tile1_emax<T, N>();  // EMAX of tile 1 (0: tile 1 is tile 0)
+  using G1 = Geo<T, N, kMaxThreads, E1>;
 
   static cudaError_t configure(const DevPlan&) {
     const void* fns[] = {(const void*)k_col_full<T, N, +1>, (const void*)k_col_full<T, N, -1>,
                          (const void*)k_plane_full<T, N, +1, 0, 1>,
-                         (const void*)k_plane_full<T, N, -1, 1, 0>, (const void*)k_pair_fwd<T, N>};
+                         (const void*)k_plane_full<T, N, -1, 1, 0>, (const void*)k_pair_fwd<T, N>,
+                         (const void*)k_pair_fwd<T, N, E1>};
     for (const void* f : fns) {
       cudaError_t err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)G::SMEM_PLANE);
       if (err != cudaSuccess) return err;
     }
-    cudaError_t err = cudaFuncSetAttribute((const void*)k_pair_inv<T, N>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_INV);
-    if (err != cudaSuccess) return err;
-    return cudaFuncSetAttribute((const void*)k_pair_col<T, N>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_COLH);
+    for (const void* f : {(const void*)k_pair_inv<T, N>, (const void*)k_pair_inv<T, N, E1>}) {
+      cudaError_t err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_INV);
+      if (err != cudaSuccess) return err;
+    }
+    for (const void* f : {(const void*)k_pair_col<T, N>, (const void*)k_pair_col<T, N, E1>}) {
+      cudaError_t err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM_COLH);
+      if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+  }
+
+  // Radix plan of tile `tile` (0 or 1) of pass `pass` (0 forward plane, 1
+  // column, 2 inverse plane): stage radices, stage count, threads per line of
+  // the pass's first transform and threads per CTA.
+  static int tile_plan(int pass, int tile, int* radices, int* nst, int* threads_per_line, int* threads) {
+    const RadixPlan pl = tile == 1 ? G1::pl : G::pl;
+    *nst = pl.nst;
+    for (int k = 0; k < pl.nst; ++k) radices[k] = pl.r[k];
+    const bool plane = pass == 0;
+    *threads_per_line = plane ? pl.tl_plane : pl.tl_colh;
+    *threads = tile == 1 ? (plane ? G1::THR_PLANE : G1::THR_COLH) : (plane ? G::THR_PLANE : G::THR_COLH);
+    return E1 != 0 ? 2 : 1;
   }
 
   static cudaError_t to_real(const DevPlan& g, const double2* psiG, int nb, int band0, int nbat,
@@ -990,23 +1083,36 @@ struct Launch {
 
   static cudaError_t pair_fwd(const DevPlan& g, const void* psi, const Chain* ch, int nch, void* H,
                               cudaStream_t s) {
-    k_pair_fwd<T, N><<<dim3(N, nch), G::THR_PLANE, G::SMEM_PLANE, s>>>(
-        g, static_cast<const T*>(psi), ch, static_cast<C*>(H));
+    if (E1 != 0 && g.tile[0] == 1)
+      k_pair_fwd<T, N, E1><<<dim3(N, nch), G1::THR_PLANE, G::SMEM_PLANE, s>>>(
+          g, static_cast<const T*>(psi), ch, static_cast<C*>(H));
+    else
+      k_pair_fwd<T, N><<<dim3(N, nch), G::THR_PLANE, G::SMEM_PLANE, s>>>(
+          g, static_cast<const T*>(psi), ch, static_cast<C*>(H));
     return cudaGetLastError();
   }
 
   static cudaError_t pair_col(const DevPlan& g, void* H, const Chain* ch, int nch, double* ep,
                               double* dp, cudaStream_t s) {
-    k_pair_col<T, N><<<dim3(g.ncta_col, nch), G::THR_COLH, G::SMEM_COLH, s>>>(g, static_cast<C*>(H), ch,
-                                                                       ep, dp);
+    if (E1 != 0 && g.tile[1] == 1)
+      k_pair_col<T, N, E1><<<dim3(g.ncta_col, nch), G1::THR_COLH, G::SMEM_COLH, s>>>(
+          g, static_cast<C*>(H), ch, ep, dp);
+    else
+      k_pair_col<T, N><<<dim3(g.ncta_col, nch), G::THR_COLH, G::SMEM_COLH, s>>>(
+          g, static_cast<C*>(H), ch, ep, dp);
     return cudaGetLastError();
   }
 
   static cudaError_t pair_inv(const DevPlan& g, const void* psi, void* W, const void* occ,
                               const Chain* ch, int nch, const void* H, cudaStream_t s) {
-    k_pair_inv<T, N><<<dim3(N, nch), G::THR_COLH, G::SMEM_INV, s>>>(
-        g, static_cast<const T*>(psi), static_cast<acc_t<T>*>(W), static_cast<const T*>(occ), ch,
-        static_cast<const C*>(H));
+    if (E1 != 0 && g.tile[2] == 1)
+      k_pair_inv<T, N, E1><<<dim3(N, nch), G1::THR_COLH, G::SMEM_INV, s>>>(
+          g, static_cast<const T*>(psi), static_cast<acc_t<T>*>(W), static_cast<const T*>(occ), ch,
+          static_cast<const C*>(H));
+    else
+      k_pair_inv<T, N><<<dim3(N, nch), G::THR_COLH, G::SMEM_INV, s>>>(
+          g, static_cast<const T*>(psi), static_cast<acc_t<T>*>(W), static_cast<const T*>(occ), ch,
+          static_cast<const C*>(H));
     return cudaGetLastError();
   }
 
@@ -1024,7 +1130,7 @@ struct Launch {
   static constexpr KernelOps ops() {
     return KernelOps{(int)sizeof(T), RealTraits<T>::prec, N,
                      smem_max(smem_max(G::SMEM_COLH, G::SMEM_PLANE), G::SMEM_INV),
-                     configure, to_real, pair_fwd, pair_col, pair_inv, to_sphere};
+                     configure, to_real, pair_fwd, pair_col, pair_inv, to_sphere, tile_plan};
   }
 };
 

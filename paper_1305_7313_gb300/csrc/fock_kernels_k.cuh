@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_COLF, Geo<T, N>::MIN_CTAS)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* S = reinterpret_cast<C*>(smem_raw);
   C* tw = S + N * N;
-  double* red = reinterpret_cast<double*>(tw + N);
+  double* red = reinterpret_cast<double*>(tw + G::TWN);
   const int k2 = blockIdx.x;
   const Chain ch = chains[blockIdx.y];
   C* Hc = H + (int64_t)blockIdx.y * g.ntot;
@@ -261,7 +261,7 @@ struct LaunchK {
                                 (int)smem_colk());
   }
 
-  static constexpr size_t smem_colk() { return sizeof(C) * (size_t)(N * N + N) + 32 * 4 * sizeof(double); }
+  static constexpr size_t smem_colk() { return sizeof(C) * (size_t)(N * N + G::TWN) + 32 * 4 * sizeof(double); }
 
   static cudaError_t to_real(const DevPlan& g, const double2* psiG, int npw, const int* gidx, int band0,
                              int nbat, void* Xv, void* u, cudaStream_t s) {

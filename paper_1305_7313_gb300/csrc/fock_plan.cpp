@@ -87,6 +87,7 @@ struct fock_plan {
   double* d_dvtab64 = nullptr;
   int* d_ncol = nullptr;
   int* d_colmap = nullptr;
+  int* d_kept = nullptr;
   // deterministic accumulation (fock_plan_set_deterministic)
   bool det = false;
   double vnorm = 0.0;          // ||v||_2 over the whole grid
@@ -707,10 +708,12 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
       for (int k3 = 0; k3 < kh; ++k3)
         if (mark[(size_t)k2 * n + k3]) ncol[k2] = k3 + 1;
   }
-  std::vector<int> colmap;
+  std::vector<int> colmap, kept;
   for (int k2 = 0; k2 < n; ++k2)
     for (int s = 0; s < 2; ++s)
       for (int k3 = 0; k3 < ncol[k2]; ++k3) colmap.push_back((k2 << 16) | (s << 15) | k3);
+  for (int k2 = 0; k2 < n; ++k2)
+    for (int k3 = 0; k3 < ncol[k2]; ++k3) kept.push_back((k2 << 16) | k3);
   const int nlines = 2 * kh;
   p->kept_columns = (int64_t)colmap.size();
   const int ncta_col = std::max(1, (int)((colmap.size() + nlines - 1) / nlines));
@@ -747,7 +750,8 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
   if (ok && kind == FOCK_KERNEL_ERFC) ok = upload((void**)&p->d_dvtab64, dv64.data(), sizeof(double) * nhalf);
   if (ok)
     ok = upload((void**)&p->d_ncol, ncol.data(), sizeof(int) * ncol.size()) &&
-         upload((void**)&p->d_colmap, colmap.data(), sizeof(int) * colmap.size());
+         upload((void**)&p->d_colmap, colmap.data(), sizeof(int) * colmap.size()) &&
+         upload((void**)&p->d_kept, kept.data(), sizeof(int) * kept.size());
   if (ok) {
     if (fp64) {
       std::vector<double> vs(nhalf);
@@ -811,7 +815,26 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
   d.ncol = p->d_ncol;
   d.colmap = p->d_colmap;
   d.ncta_col = ncta_col;
+  d.kept = p->d_kept;
+  d.nkept = (int)kept.size();
+  {
+    // kept rows as two runs [0, lo) and [n - hi, n); any other pattern keeps all rows
+    int lo = 0, hi = 0, cmax = 0;
+    while (lo < n && ncol[lo] > 0) ++lo;
+    while (hi < n - lo && ncol[n - 1 - hi] > 0) ++hi;
+    bool runs = true;
+    for (int k2 = lo; k2 < n - hi; ++k2) runs = runs && ncol[k2] == 0;
+    if (!runs) {
+      lo = n;
+      hi = 0;
+    }
+    for (int k2 = 0; k2 < n; ++k2) cmax = std::max(cmax, ncol[k2]);
+    d.row_lo = lo;
+    d.row_hi = hi;
+    d.col_max = std::max(1, cmax);
+  }
   d.det = 0;  // set per call on a copy when the plan is deterministic
+  d.tile[0] = d.tile[1] = d.tile[2] = 0;
   d.det_scale = nullptr;
 
   int optin = 0, sms = 0;
@@ -909,6 +932,36 @@ fock_status fock_plan_set_band_block(fock_plan_t plan, int band_block) {
     plan->band_block = band_block;
     plan->sched_nb = -1;  // rebuilt at the next call
   }
+  return FOCK_OK;
+}
+
+fock_status fock_plan_tiling_info(fock_plan_t plan, int pass, int tile, int* radices, int* nstages,
+                                  int* threads_per_line, int* threads, int* ntiles) {
+  if (!plan) return fail(nullptr, FOCK_ERR_INVALID_ARG, "plan is NULL");
+  if (!radices || !nstages || !threads_per_line || !threads || !ntiles)
+    return fail(plan, FOCK_ERR_INVALID_ARG, "NULL output");
+  if (pass < 0 || pass > 2 || tile < 0 || tile > 1) return fail(plan, FOCK_ERR_INVALID_ARG, "pass or tile out of range");
+  int r[8], nst = 0, tl = 0, thr = 0;
+  const int nt = plan->ops->tile_plan(pass, tile, r, &nst, &tl, &thr);
+  if (tile >= nt) return fail(plan, FOCK_ERR_INVALID_ARG, "this plan has one tiling for that pass");
+  for (int k = 0; k < nst; ++k) radices[k] = r[k];
+  *nstages = nst;
+  *threads_per_line = tl;
+  *threads = thr;
+  *ntiles = nt;
+  return FOCK_OK;
+}
+
+fock_status fock_plan_set_tiling(fock_plan_t plan, const int tiles[3]) {
+  if (!plan) return fail(nullptr, FOCK_ERR_INVALID_ARG, "plan is NULL");
+  if (!tiles) return fail(plan, FOCK_ERR_INVALID_ARG, "tiles is NULL");
+  for (int pass = 0; pass < 3; ++pass) {
+    int r[8], nst = 0, tl = 0, thr = 0;
+    const int nt = plan->ops->tile_plan(pass, 0, r, &nst, &tl, &thr);
+    if (tiles[pass] < 0 || tiles[pass] >= nt)
+      return fail(plan, FOCK_ERR_INVALID_ARG, "a tile index is not below the pass's number of tilings");
+  }
+  for (int pass = 0; pass < 3; ++pass) plan->dp.tile[pass] = tiles[pass];
   return FOCK_OK;
 }
 
@@ -1177,6 +1230,7 @@ fock_status fock_destroy(fock_plan_t plan) {
   cudaFree(plan->d_dvtab64);
   cudaFree(plan->d_ncol);
   cudaFree(plan->d_colmap);
+  cudaFree(plan->d_kept);
   cudaFree(plan->d_stats);
   cudaFree(plan->d_scale);
   cudaFree(plan->d_epart);

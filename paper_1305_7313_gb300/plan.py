@@ -53,6 +53,18 @@ class FockPlan:
     def reserve(self, nb_max):
         _lib.fock_plan_reserve(self.handle, nb_max)
 
+    def tilings(self):
+        """Per pair pass, the list of its FFT tilings (radix plans) as dicts."""
+        out = {}
+        for p, name in enumerate(_lib.PASSES):
+            first = _lib.fock_plan_tiling_info(self.handle, p, 0)
+            out[name] = [first] + [_lib.fock_plan_tiling_info(self.handle, p, t) for t in range(1, first["ntiles"])]
+        return out
+
+    def set_tiling(self, tiles):
+        """Tiling index (0 or 1) of the forward plane, column and inverse plane passes."""
+        _lib.fock_plan_set_tiling(self.handle, tiles)
+
     def device_bytes(self):
         return _lib.fock_plan_device_bytes(self.handle)
 

@@ -27,6 +27,24 @@ class FakePlan:
         self.applies += 1
 
 
+class FakeTiledPlan(FakePlan):
+    """A plan whose forward and inverse plane passes have two FFT tilings and
+    whose column pass has one, as the library reports them."""
+
+    def __init__(self):
+        super().__init__()
+        self.tiles = None
+
+    def tilings(self):
+        t0 = {"radices": [12, 8], "threads_per_line": 4, "threads": 384, "ntiles": 2}
+        t1 = {"radices": [12, 4, 2], "threads_per_line": 8, "threads": 768, "ntiles": 2}
+        one = {"radices": [12, 8], "threads_per_line": 4, "threads": 416, "ntiles": 1}
+        return {"pair_fwd": [t0, t1], "pair_col": [one], "pair_inv": [t0, t1]}
+
+    def set_tiling(self, tiles):
+        self.tiles = list(tiles)
+
+
 class FakePsi:
     def __init__(self, nb):
         self.shape = (nb, 100)
@@ -126,3 +144,30 @@ def test_batch_tuner_candidates_and_choice(clock, monkeypatch):
     assert autotune.tune_batch(plans, [FakePsi(10), FakePsi(20)], None, persistent=(1, 0),
                                band_blocks=(16,)).get("cached")
     assert len(built) == n
+
+
+def test_apply_tuner_searches_the_fft_tilings_one_pass_at_a_time(clock):
+    # pair-block grid at the default tiling, then each pass that has a second
+    # tiling tried at the best block (the column pass has one: not tried);
+    # the forward pass's second tiling is faster, the inverse pass's is not
+    plan = FakeTiledPlan()
+    def cost(s):
+        cb, bb, tiles = s
+        c = 100.0 + abs(cb - 19) + abs(bb - 16)
+        if tiles[0] == 1:
+            c -= 10.0
+        if tiles[2] == 1:
+            c += 5.0
+        return c
+    clock["cost"] = cost
+    clock["probe"] = lambda: (plan.chain_batch, plan.band_block, tuple(plan.tiles))
+    res = autotune.tune_apply(plan, FakePsi(512), None)
+    assert (res["chain_batch"], res["band_block"], res["tiles"]) == (19, 16, [1, 0, 0])
+    assert res["ms"] == 90.0 and plan.tiles == [1, 0, 0]
+    assert clock["calls"] == 15 + 2  # 5 x 3 pair-block candidates, then two tilings
+    assert res["tiling"]["pair_fwd"]["radices"] == [12, 4, 2] and res["tiling"]["pair_fwd"]["tile"] == 1
+    assert res["tiling"]["pair_col"]["tile"] == 0 and res["tiling"]["pair_inv"]["tile"] == 0
+    # a second process takes the choice from the cache without timing
+    plan2 = FakeTiledPlan()
+    res2 = autotune.tune_apply(plan2, FakePsi(512), None)
+    assert res2["cached"] and plan2.tiles == [1, 0, 0] and clock["calls"] == 17

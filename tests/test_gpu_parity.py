@@ -184,3 +184,41 @@ def test_orbitals_of_another_sphere_are_refused_before_any_device_work():
         case["plan"].apply(wrong, case["occ"])
     vpsi, ex, _ = case["plan"].apply(case["psi"], case["occ"])  # the plan still works
     assert np.isfinite(ex)
+
+
+@pytest.mark.parametrize("prec,kind,omega,tol_v,tol_e", [
+    (_lib.PREC_FP64, _lib.SPENCER_ALAVI, None, TOL64, TOL64),
+    (_lib.PREC_MIXED32, _lib.ERFC, 0.106, TOL32_V, TOL32_E),
+], ids=["fp64", "mixed32"])
+def test_every_fft_tiling_matches_the_oracle(prec, kind, omega, tol_v, tol_e):
+    # 96^3 at L = 27, Ecut = 12 (the grid with two compiled tilings), 6 bands:
+    # every combination of the passes' tilings against the oracle, and the
+    # tuner's choice list as the library describes it
+    import itertools
+    case = setup_case(96, 27.0, 12.0, 6, 4096, kind=kind, omega=omega, prec=prec)
+    plan = case["plan"]
+    tilings = plan.tilings()
+    assert [len(tilings[p]) for p in _lib.PASSES] == [2, 2, 2]
+    for p in _lib.PASSES:
+        t0, t1 = tilings[p]
+        assert t0["radices"] != t1["radices"] and t0["threads_per_line"] != t1["threads_per_line"]
+        assert int(np.prod(t0["radices"])) == int(np.prod(t1["radices"])) == 96
+    vref, eref, _ = oracle_of(case)
+    for tiles in itertools.product((0, 1), repeat=3):
+        plan.set_tiling(tiles)
+        vpsi, ex, _ = plan.apply(case["psi"], case["occ"])
+        assert rel_inf(vpsi.cpu().numpy(), vref) <= tol_v, tiles
+        assert abs(ex - eref) <= tol_e * abs(eref), tiles
+    with pytest.raises(_lib.FockError):
+        plan.set_tiling((2, 0, 0))
+    plan.close()
+
+
+def test_a_grid_with_one_tiling_refuses_the_second():
+    case = setup_case(24, 10.0, 10.0, 4, 17, prec=_lib.PREC_MIXED32, kind=_lib.ERFC, omega=0.5)
+    plan = case["plan"]
+    assert all(len(v) == 1 for v in plan.tilings().values())
+    with pytest.raises(_lib.FockError):
+        plan.set_tiling((1, 0, 0))
+    plan.set_tiling((0, 0, 0))
+    plan.close()
