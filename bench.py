@@ -325,7 +325,7 @@ def run_batched(args, peaks, peak_src):
     tuned = {"options": {}, "band_block": 16}
     if not args.no_tune:
         tuned = tune_batch(plans, psis, occs, slot_chains=(4, 8, 16), rings=(3,), ctas_per_sm=(0,),
-                           persistent=(1, 0), reps=1, use_cache=False)
+                           persistent=(1, 2, 0), reps=1, use_cache=False)
     batch = FockBatch(plans, psis, occs, **tuned["options"])
     for _ in range(args.warmup):
         batch.run()
@@ -354,14 +354,12 @@ def run_batched(args, peaks, peak_src):
     batch.close()
     for p in plans:
         p.close()
-    persistent = bool(tuned["options"].get("persistent", 1))
-    if not persistent:
-        # the pair passes ran as size-specialised launches: time them as a whole
-        nbytes_kernel = "pair passes (graph branches)"
-    else:
-        nbytes_kernel = "k_pair_persistent"
-    return {"workload": "batched16_mixed32_sa_N48-96_L13.5-27", "mode": "persistent" if persistent else
-            "graph branches of size-specialised launches",
+    mode = int(tuned["options"].get("persistent", 1))
+    nbytes_kernel = {0: "pair passes (graph branches)", 1: "k_pair_persistent", 2: "k_pair_dataflow"}[mode]
+    persistent = mode != 0
+    return {"workload": "batched16_mixed32_sa_N48-96_L13.5-27",
+            "mode": {0: "graph branches of size-specialised launches", 1: "persistent launch",
+                     2: "dataflow launch (one CTA per task)"}[mode],
             "value": pairs * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
             "pairs": pairs, "dtype": "f32", "graph": True, "persistent_launches_per_step": 1 if persistent else 0,
             "gpu_launches_per_step": info["launches"], "persistent_grid": info["grid"],
@@ -379,7 +377,7 @@ def best_by_mode(table):
     """Fastest tuner candidate per pair-pass mode (persistent launch vs graph branches)."""
     out = {}
     for r in table:
-        key = "persistent" if r["options"].get("persistent", 1) else "branches"
+        key = {0: "branches", 1: "persistent", 2: "dataflow"}[int(r["options"].get("persistent", 1))]
         if key not in out or r["ms"] < out[key]:
             out[key] = r["ms"]
     return out

@@ -353,9 +353,14 @@ typedef struct {
   int stall_segment;    /* TEST ONLY (leave at -1): >= 0 makes that segment wait for itself,
                            which can never finish, so that tests can drive the bounded-wait
                            path (FOCK_ERR_TIMEOUT) without a GPU fault */
-  int persistent;       /* 1: the pair passes of all systems in one persistent launch (default);
+  int persistent;       /* pair passes of the systems:
+                           1: one persistent launch of resident CTAs that take (system, pass,
+                              chain, plane/column) tasks in dependency order (default);
+                           2: one dataflow launch with one CTA per task: each CTA takes a ticket
+                              when it starts, waits (bounded) for the tasks its own depends on,
+                              then runs it;
                            0: each system's pair passes as size-specialised launches on its own
-                           branch of the graph (branches run concurrently) */
+                              branch of the graph (branches run concurrently) */
 } fock_batch_options;
 
 /* Fill `opt` with the defaults above. */

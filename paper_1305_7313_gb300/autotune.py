@@ -11,8 +11,9 @@ The knobs are the ones that decide how pair work maps onto the GPU:
 * ``tiling`` — the FFT tiling (radix plan and threads per line) of each of the
   three pair passes, where the library compiled two (``FockPlan.tilings()``);
   searched one pass at a time after the pair-block search;
-* for batches: ``persistent`` (one persistent launch for all systems, or
-  size-specialised launches on one graph branch per system), ``slot_chains``
+* for batches: ``persistent`` (1: one persistent launch for all systems; 2:
+  one dataflow launch with a CTA per task; 0: size-specialised launches on
+  one graph branch per system), ``slot_chains``
   (chains of the largest grid per transform-buffer slot of the persistent
   launch), ``ring`` (slots in flight) and ``ctas_per_sm`` (resident CTAs per
   SM of the persistent launch).
@@ -161,9 +162,11 @@ def tune_batch(plans, psi, occ, slot_chains=(4, 8, 16), rings=(3, 4), ctas_per_s
     table = []
     combos = []
     for pers in persistent:
-        if pers:
+        if pers == 1:
             combos += [(bb, sc, ring, cps, 1) for bb, sc, ring, cps in
                        itertools.product(band_blocks, slot_chains, rings, ctas_per_sm)]
+        elif pers == 2:  # dataflow launch: one CTA per task, no residency knob
+            combos += [(bb, sc, ring, 0, 2) for bb, sc, ring in itertools.product(band_blocks, slot_chains, rings)]
         else:  # the persistent-launch knobs do not apply
             combos += [(bb, slot_chains[0], rings[0], 0, 0) for bb in band_blocks]
     for bb, sc, ring, cps, pers in combos:

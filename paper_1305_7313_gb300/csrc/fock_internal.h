@@ -145,6 +145,10 @@ struct PersistOps {
   cudaError_t (*launch)(int grid, const SysDesc* sys, const Segment* seg, int nseg, int ntasks,
                         unsigned* counters, unsigned char* hring, size_t slot_bytes,
                         unsigned long long limit_ns, cudaStream_t s);
+  // one CTA per task, inlined bodies, dependency waits (grid = ntasks)
+  cudaError_t (*launch_dataflow)(const SysDesc* sys, const Segment* seg, int nseg, int ntasks,
+                                 unsigned* counters, unsigned char* hring, size_t slot_bytes,
+                                 unsigned long long limit_ns, cudaStream_t s);
 };
 
 // Persistent pair kernel of a precision (0: FP64, 1: mixed).

@@ -152,11 +152,99 @@ __global__ void __launch_bounds__(kPersistMaxT<T>, PersistGeo<T>::MIN_CTAS)
   }
 }
 
+// ---------------------------------------------------------------- dataflow launch
+//
+// The same segments and dependencies as the persistent kernel, but one CTA per
+// task and no loop: the grid has one CTA per ticket.  A CTA takes its ticket
+// from the global counter when it starts (so tickets follow the order in which
+// CTAs become resident, whatever the hardware's dispatch order), waits for the
+// segments its task depends on (all of smaller tickets, held by CTAs that have
+// already started: the lowest unfinished ticket can always run), runs the task
+// body inlined (the register allocation of a stand-alone kernel, no call
+// boundary) and publishes it.  Waits are bounded as in the persistent kernel.
+
+// The task body, inlined, for grid size N.
+template <class T, int N>
+__device__ __forceinline__ void dataflow_task(const SysDesc* __restrict__ sys, const Segment& sg, int local,
+                                              cplx<T>* hslot, unsigned char* smem) {
+  const SysDesc& sd = sys[sg.sys];
+  const int per = sg.kind == 1 ? sd.g.ncta_col : N;
+  const int c = local / per, idx = local - c * per;
+  cplx<T>* Hc = hslot + (int64_t)c * sd.g.hsize;
+  const Chain ch = sd.chains[sg.chain0 + c];
+  if (sg.kind == 0) {
+    pair_fwd_task<T, N, kPersistMaxT<T>>(sd.g, static_cast<const T*>(sd.psi), ch, Hc, idx, smem);
+  } else if (sg.kind == 1) {
+    pair_col_task<T, N, kPersistMaxT<T>>(sd.g, Hc, ch, idx, sd.epair, sd.dpair, smem);
+  } else {
+    pair_inv_task<T, N, kPersistMaxT<T>>(sd.g, static_cast<const T*>(sd.psi), static_cast<T*>(sd.W),
+                                         static_cast<const T*>(sd.occT), ch, Hc, idx, smem);
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kPersistMaxT<T>, PersistGeo<T>::MIN_CTAS)
+    k_pair_dataflow(const SysDesc* __restrict__ sys, const Segment* __restrict__ seg, int nseg, int ntasks,
+                    unsigned* counters, unsigned char* hring, size_t slot_bytes, unsigned long long limit_ns) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_ticket, s_seg;
+  unsigned* err = counters + 1;
+  unsigned* done = counters + 2;
+  if (threadIdx.x == 0) {
+    int t = ntasks, cur = -1;
+    if (ld_acquire(err) == 0u) {
+      t = (int)atomicAdd(counters, 1u);
+      if (t < ntasks) {  // the segment of ticket t: the last with task0 <= t
+        int lo = 0, hi = nseg - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) / 2;
+          if (seg[mid].task0 <= t) lo = mid;
+          else hi = mid - 1;
+        }
+        cur = lo;
+        const Segment& sg = seg[cur];
+        bool ok = true;
+        if (sg.dep >= 0) ok = bounded_wait(done + sg.dep, (unsigned)seg[sg.dep].ntasks, err, limit_ns);
+        if (ok && sg.dep2 >= 0) ok = bounded_wait(done + sg.dep2, (unsigned)seg[sg.dep2].ntasks, err, limit_ns);
+        if (!ok) {
+          atomicCAS(err, 0u, (unsigned)cur + 1u);
+          t = ntasks;
+        }
+      }
+    }
+    s_ticket = t;
+    s_seg = cur;
+  }
+  __syncthreads();
+  const int t = s_ticket;
+  if (t >= ntasks) return;
+  const Segment sg = seg[s_seg];
+  cplx<T>* hslot = reinterpret_cast<cplx<T>*>(hring + (size_t)sg.slot * slot_bytes);
+  const int local = t - sg.task0;
+  switch (sys[sg.sys].g.n) {
+    case 24: dataflow_task<T, 24>(sys, sg, local, hslot, smem_raw); break;
+    case 32: dataflow_task<T, 32>(sys, sg, local, hslot, smem_raw); break;
+    case 48: dataflow_task<T, 48>(sys, sg, local, hslot, smem_raw); break;
+    case 64: dataflow_task<T, 64>(sys, sg, local, hslot, smem_raw); break;
+    case 72: dataflow_task<T, 72>(sys, sg, local, hslot, smem_raw); break;
+    case 96: dataflow_task<T, 96>(sys, sg, local, hslot, smem_raw); break;
+    default: break;  // the host admits only the sizes above
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(done + s_seg, 1u);
+  }
+}
+
 template <class T>
 struct PersistLaunch {
   static cudaError_t configure() {
-    return cudaFuncSetAttribute((const void*)k_pair_persistent<T>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PersistGeo<T>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_pair_persistent<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PersistGeo<T>::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void*)k_pair_dataflow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PersistGeo<T>::SMEM);
   }
   static cudaError_t occupancy(int* ctas_per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_pair_persistent<T>, kPersistMaxT<T>,
@@ -169,8 +257,15 @@ struct PersistLaunch {
                                                                       hring, slot_bytes, limit_ns);
     return cudaGetLastError();
   }
+  static cudaError_t launch_dataflow(const SysDesc* sys, const Segment* seg, int nseg, int ntasks,
+                                     unsigned* counters, unsigned char* hring, size_t slot_bytes,
+                                     unsigned long long limit_ns, cudaStream_t s) {
+    k_pair_dataflow<T><<<ntasks, kPersistMaxT<T>, PersistGeo<T>::SMEM, s>>>(sys, seg, nseg, ntasks, counters,
+                                                                          hring, slot_bytes, limit_ns);
+    return cudaGetLastError();
+  }
   static constexpr PersistOps ops() {
-    return PersistOps{(int)sizeof(T), PersistGeo<T>::SMEM, configure, occupancy, launch};
+    return PersistOps{(int)sizeof(T), PersistGeo<T>::SMEM, configure, occupancy, launch, launch_dataflow};
   }
 };
 

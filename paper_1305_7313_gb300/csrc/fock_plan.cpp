@@ -1339,7 +1339,11 @@ fock_status batch_enqueue(fock_batch* b, cudaStream_t s) {
   FOCK_BCUDA(b, cudaStreamIsCapturing(s, &cap));
   const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
   FOCK_BCUDA(b, cudaEventRecordWithFlags(b->ev0, s, ev_flags));
-  if (b->opt.persistent) {
+  if (b->opt.persistent == 2) {
+    FOCK_BCUDA(b, b->pops->launch_dataflow(b->d_sys, b->d_seg, nseg, b->ntasks, b->d_counters, b->d_ring,
+                                           b->slot_bytes, limit_ns, s));
+    b->launches += 1;
+  } else if (b->opt.persistent) {
     FOCK_BCUDA(b, b->pops->launch(b->grid, b->d_sys, b->d_seg, nseg, b->ntasks, b->d_counters,
                                   b->d_ring, b->slot_bytes, limit_ns, s));
     b->launches += 1;
@@ -1417,7 +1421,8 @@ fock_status fock_batch_create(fock_batch_t* out, int nsys, const fock_plan_t* pl
   fock_batch_options o;
   fock_batch_default_options(&o);
   if (opt) o = *opt;
-  if (o.slot_chains < 1 || o.ring < 3 || o.ctas_per_sm < 0 || !(o.wait_limit_s > 0.0))
+  if (o.slot_chains < 1 || o.ring < 3 || o.ctas_per_sm < 0 || !(o.wait_limit_s > 0.0) || o.persistent < 0 ||
+      o.persistent > 2)
     return bfail(nullptr, FOCK_ERR_INVALID_ARG, "bad batch options");
   int dev = -1;
   cudaError_t ge = cudaGetDevice(&dev);
@@ -1568,6 +1573,7 @@ fock_status fock_batch_create(fock_batch_t* out, int nsys, const fock_plan_t* pl
   if (o.ctas_per_sm > 0) per_sm = std::min(per_sm, o.ctas_per_sm);
   // every CTA of the grid must be resident at once: the waits rely on it
   b->grid = std::min(b->ntasks, per_sm * nsm);
+  if (o.persistent == 2) b->grid = b->ntasks;  // the dataflow launch: one CTA per task
 
   if (o.use_graph) {
     if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)

@@ -133,15 +133,18 @@ def test_batch_tuner_candidates_and_choice(clock, monkeypatch):
     clock["cost"] = lambda o: 5.0 if (o["persistent"], o["slot_chains"], o["ring"], o["ctas_per_sm"]) == (1, 8, 4, 1) \
         else 9.0
     plans = [FakePlan(48), FakePlan(96)]
-    res = autotune.tune_batch(plans, [FakePsi(10), FakePsi(20)], None, persistent=(1, 0), band_blocks=(16,))
-    # persistent candidates: every slot_chains x ring x ctas_per_sm; non-persistent: one per band block
-    assert len(built) == 3 * 2 * 2 + 1
+    res = autotune.tune_batch(plans, [FakePsi(10), FakePsi(20)], None, persistent=(1, 0, 2), band_blocks=(16,))
+    # persistent candidates: every slot_chains x ring x ctas_per_sm; dataflow:
+    # every slot_chains x ring; graph branches: one per band block
+    assert len(built) == 3 * 2 * 2 + 1 + 3 * 2
     assert sum(1 for o in built if o["persistent"] == 0) == 1
+    assert sum(1 for o in built if o["persistent"] == 2) == 6
+    assert all(o["ctas_per_sm"] == 0 for o in built if o["persistent"] == 2)
     assert res["options"]["persistent"] == 1 and res["options"]["slot_chains"] == 8
     assert res["options"]["ring"] == 4 and res["options"]["ctas_per_sm"] == 1 and res["ms"] == 5.0
     assert all(p.band_block == 16 for p in plans)
     n = len(built)
-    assert autotune.tune_batch(plans, [FakePsi(10), FakePsi(20)], None, persistent=(1, 0),
+    assert autotune.tune_batch(plans, [FakePsi(10), FakePsi(20)], None, persistent=(1, 0, 2),
                                band_blocks=(16,)).get("cached")
     assert len(built) == n
 

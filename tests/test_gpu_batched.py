@@ -30,7 +30,7 @@ def make_systems(prec, kind=_lib.SPENCER_ALAVI, omega=None, seed=50):
 
 @pytest.mark.parametrize("prec,tol_v,tol_e", [(_lib.PREC_FP64, 1e-10, 1e-10),
                                               (_lib.PREC_MIXED32, 2e-5, 5e-6)])
-@pytest.mark.parametrize("use_graph,persistent", [(1, 1), (0, 1), (1, 0)])
+@pytest.mark.parametrize("use_graph,persistent", [(1, 1), (0, 1), (1, 0), (1, 2), (0, 2)])
 def test_batch_matches_single_applies_and_oracle(prec, tol_v, tol_e, use_graph, persistent):
     torch, plans, psis, occs, cs = make_systems(prec, _lib.ERFC, 0.3)
     singles = []
@@ -75,16 +75,17 @@ def test_batch_input_update_between_replays():
     batch.close()
 
 
-def test_a_wait_that_never_ends_times_out_and_the_device_stays_usable():
+@pytest.mark.parametrize("persistent", [1, 2])
+def test_a_wait_that_never_ends_times_out_and_the_device_stays_usable(persistent):
     torch, plans, psis, occs, cs = make_systems(_lib.PREC_MIXED32)
     # segment 4 waits for its own completion: nothing will ever set that counter
-    stalled = FockBatch(plans, psis, occs, slot_chains=2, wait_limit_s=0.5, stall_segment=4)
+    stalled = FockBatch(plans, psis, occs, slot_chains=2, wait_limit_s=0.5, stall_segment=4, persistent=persistent)
     with pytest.raises(_lib.FockError) as err:
         stalled.run()
     assert err.value.status == 6  # FOCK_ERR_TIMEOUT
     stalled.close()
     torch.cuda.synchronize()
-    ok = FockBatch(plans, psis, occs, slot_chains=2)
+    ok = FockBatch(plans, psis, occs, slot_chains=2, persistent=persistent)
     ex, _ = ok.run()
     e0 = plans[0].apply(psis[0], occs[0])[1]
     assert abs(ex[0] - e0) <= 5e-6 * abs(e0)
