@@ -23,12 +23,20 @@ Everything is evaluated one pair at a time, in FP64, with ``numpy.fft`` as the
 only library primitive: no packing of two pairs into one transform, no fusion,
 no blocking.
 
+``oracle.sternheimer`` adds the linear-response solve of §3.1 (the Sternheimer
+equation (H - eps_n + alpha P) g_n = -Q w_n by CG, with the paper's regrouping
+of converged and unconverged bands) for a model Hamiltonian, kinetic energy
+plus a local potential on the same plane-wave sphere.
+
 Parity pins (see ``tests/test_oracle_*.py``): a direct O(N^2) DFT on tiny
 grids, closed-form Gaussian self-energies for both kernels, Hermiticity and
 negative semidefiniteness of <psi_a|V_x|psi_b>, E_x = 1/2 sum_j f_j
 <psi_j|V_x psi_j>, finite differences of E_x in psi and in omega, unitary,
 translation, permutation and partition invariances, and brute-force counts of
-the G-sphere.  No function here is "parity unpinned".
+the G-sphere; for the Sternheimer solve, the model H's FFT route against the
+dense matrix of the potential's Fourier coefficients (itself checked against
+closed forms) and the CG solution against a direct dense solve.  No function
+here is "parity unpinned".
 """
 
 from .lattice import reciprocal_lattice, cell_volume, gsphere, gsphere_k, grid_miller, grid_g2
