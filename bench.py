@@ -342,18 +342,29 @@ def run_batched(args, peaks, peak_src):
         torch.cuda.synchronize()
     ms = start.elapsed_time(end)
     info = batch.info()
-    # algorithmic bytes of the persistent launch: per chain the complex64 half
-    # spectrum is written (fwd), read and written (col) and read (inv)
+    # algorithmic bytes of the pair passes, per chain of each system: the kept
+    # columns of the complex64 half spectrum are written (fwd), read and
+    # written (col) and read (inv); the forward pass reads four orbital planes
+    # and the inverse pass reads four and read-modify-writes four accumulator
+    # planes, each counted once per band block
+    bb = tuned.get("band_block", 16)
     nbytes = 0.0
-    for sy in systems:
+    for sy, p in zip(systems, plans):
         n = sy["N"]
+        kept, total = p.columns()
         chains = (sy["nb"] * (sy["nb"] + 1) // 2 + 1) // 2
-        nbytes += chains * 4 * n * n * 2 * (n // 2 + 1) * 8.0
+        hbytes = n * n * 2 * (n // 2 + 1) * 8.0 * kept / total
+        nbytes += chains * (4 * hbytes + 16 * n ** 3 * 4.0 / max(1, min(bb, sy["nb"])))
     pm = statistics.median(pms)
     achieved = nbytes / (pm * 1e-3) / 1e9
     batch.close()
     for p in plans:
         p.close()
+    traffic = None
+    if args.nb is None:  # DRAM bytes per chain of the pair passes (ncu, 64-band systems), scaled by chains
+        traffic = sum(((sy["nb"] * (sy["nb"] + 1) // 2 + 1) // 2) * BATCH_DRAM_PER_CHAIN.get(sy["N"], float("nan"))
+                      for sy in systems)
+        traffic = None if traffic != traffic else traffic
     mode = int(tuned["options"].get("persistent", 1))
     nbytes_kernel = {0: "pair passes (graph branches)", 1: "k_pair_persistent", 2: "k_pair_dataflow"}[mode]
     persistent = mode != 0
@@ -366,11 +377,17 @@ def run_batched(args, peaks, peak_src):
             "segments": info["segments"], "tasks": info["tasks"],
             "roofline": {"bound": "hbm", "kernel": nbytes_kernel, "achieved": achieved,
                          "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                         "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
-                         "peak_src": peak_src + " (hbm copy)", "ms_per_launch": pm},
+                         "frac": achieved / float(peaks["hbm_gbs"]), "traffic": traffic,
+                         "algorithmic_bytes": nbytes, "peak_src": peak_src + " (hbm copy)", "ms_pair_passes": pm},
             "tuned": {"options": tuned["options"], "band_block": tuned["band_block"],
                       "best_ms_by_mode": best_by_mode(tuned.get("table", []))},
             "clocks": clk.summary()}
+
+
+# DRAM bytes (read + write) per chain of the three pair passes of the batch's
+# systems, by grid size (filled from an ncu capture of the pair kernels of the
+# 64-band version of the batch); empty: not captured for these kernels
+BATCH_DRAM_PER_CHAIN = {}
 
 
 def best_by_mode(table):

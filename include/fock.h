@@ -330,6 +330,43 @@ fock_status fock_pair_energies_static(fock_plan_t plan, const void* psi_G, int n
                                       const int32_t* pairs, int npairs, double* e, double* d,
                                       fock_stream_t stream);
 
+/*
+ * fock_sternheimer_solve — the linear-response step of the paper's GIPAW code
+ * (§3.1, the Sternheimer equation and the CG paragraph after it): for each
+ * right-hand ket w_n, solve
+ *     (H - eps_n + alpha P) g_n = -Q w_n,   P = sum_i |u_i><u_i|,  Q = 1 - P,
+ * by conjugate gradients, for the model Gamma-point Hamiltonian
+ * H = -1/2 nabla^2 + V(r) on the plan's plane-wave sphere:
+ *     (H c)(G) = |G|^2/2 c(G) + (sqrt(Omega)/Ntot) FFT[V(r) psi(r)](G),
+ *     psi(r) = Omega^-1/2 sum_{G in S} c(G) exp(iG.r) on the plan's grid.
+ * The first CG iteration updates every band; from then on the bands are kept
+ * in two contiguous groups, not converged and converged, and only the first is
+ * updated (a band converges when its residual norm ||-Q w_n - A_n g_n|| falls
+ * below tol); the result is returned in the original band order.  Plain CG
+ * from g = 0, no preconditioner.  alpha should exceed the occupied bandwidth
+ * (the paper takes twice it) so that every A_n is positive definite.
+ *   plan     an FP64 plan (INVALID_ARG otherwise): sphere, grid, transforms.
+ *   vloc     device double [N^3]: V(r) on the grid, index (i1 N + i2) N + i3.
+ *   u_G      device complex128 [nocc][npw]: the occupied states (orthonormal,
+ *            Gamma-point real: c(-G) = c(G)*).
+ *   eps      host double [nrhs]: eps_n.
+ *   w_G      device complex128 [nrhs][npw]: the kets w_n (Gamma-point real).
+ *   alpha, tol, maxiter   projector shift, residual threshold (> 0), CG
+ *            iteration limit (>= 1).
+ *   g_G      device complex128 [nrhs][npw]: receives g_n; must not overlap
+ *            u_G or w_G.
+ *   iters    host int [nrhs] or NULL: CG updates each band received.
+ *   resid    host double [nrhs] or NULL: final residual norms (a band that
+ *            did not reach tol within maxiter keeps its last iterate).
+ * Uses the plan's real-space workspace (any fixed operator set by
+ * fock_set_occupied is dropped) and allocates its own CG vectors for the
+ * call.  Synchronises the stream once per CG iteration.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+fock_status fock_sternheimer_solve(fock_plan_t plan, const double* vloc, const void* u_G, int nocc,
+                                   const double* eps, const void* w_G, int nrhs, double alpha, double tol,
+                                   int maxiter, void* g_G, int* iters, double* resid, fock_stream_t stream);
+
 /* ---------------------------------------------------------------- batches
  *
  * Many independent systems (uneven grids and band counts) in one batched

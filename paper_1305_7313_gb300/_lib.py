@@ -94,6 +94,8 @@ _SIGNATURES = {
     "fock_apply_fixed": [_vp, _vp, ctypes.c_int, _vp, _vp],
     "fock_pair_energies_static": [_vp, _vp, ctypes.c_int, _c_i32_p, ctypes.c_int, _c_dbl_p, _c_dbl_p,
                                   _vp],
+    "fock_sternheimer_solve": [_vp, _vp, _vp, ctypes.c_int, _c_dbl_p, _vp, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_int, _vp, _c_int_p, _c_dbl_p, _vp],
     "fock_batch_default_options": [ctypes.POINTER(BatchOptions)],
     "fock_batch_create": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), _c_int_p,
                           ctypes.POINTER(_vp), ctypes.POINTER(_c_dbl_p), ctypes.POINTER(_vp),
@@ -387,6 +389,35 @@ def fock_pair_energies_static(plan, psi_G, pairs, want_d=False, stream=None):
                                             d.ctypes.data_as(_c_dbl_p) if want_d else None,
                                             _stream(stream)), plan)
     return (e, d) if want_d else e
+
+
+def fock_sternheimer_solve(plan, ntot, vloc, u_G, eps, w_G, alpha, tol, maxiter=1000, g_G=None, stream=None):
+    """(g, iters, resid): CG solution of (H - eps_n + alpha P) g_n = -Q w_n for
+    H = kinetic + V(r) on the plan's sphere.  ``ntot``: the plan's grid points
+    N^3; ``vloc``: contiguous CUDA float64 tensor with ntot elements;
+    ``u_G`` / ``w_G``: CUDA complex128 [nocc / nrhs, npw]; ``eps``: host [nrhs]."""
+    import torch
+    npw = fock_plan_npw(plan)
+    nocc = _rows(u_G, "u_G", npw)
+    nrhs = _rows(w_G, "w_G", npw)
+    if not (isinstance(vloc, torch.Tensor) and vloc.is_cuda and vloc.dtype == torch.float64
+            and vloc.is_contiguous()):
+        raise TypeError("vloc must be a contiguous CUDA float64 tensor")
+    if vloc.numel() != int(ntot):
+        raise ValueError("vloc has %d values, the plan's grid %d" % (vloc.numel(), int(ntot)))
+    eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64).ravel())
+    if eps.shape != (nrhs,):
+        raise ValueError("eps must hold one value per right-hand ket (%d)" % nrhs)
+    if g_G is None:
+        g_G = torch.empty_like(w_G)
+    iters = (ctypes.c_int * nrhs)()
+    resid = (ctypes.c_double * nrhs)()
+    _check(load().fock_sternheimer_solve(plan, ctypes.c_void_p(vloc.data_ptr()), _dev_ptr(u_G, "u_G"), nocc,
+                                         eps.ctypes.data_as(_c_dbl_p), _dev_ptr(w_G, "w_G"), nrhs,
+                                         float(alpha), float(tol), int(maxiter),
+                                         _dev_ptr(g_G, "g_G", tuple(w_G.shape)), iters, resid,
+                                         _stream(stream)), plan)
+    return g_G, np.array(iters[:], dtype=np.int64), np.array(resid[:])
 
 
 def _check_batch(status, batch=None):

@@ -62,6 +62,7 @@ def _jobs():
                  ["-c", os.path.join(CSRC, "fock_kpoints.cpp")]))
     jobs.append(("fock_common.o", nv + ["-c", os.path.join(CSRC, "fock_common.cu")]))
     jobs.append(("fock_static.o", nv + ["-c", os.path.join(CSRC, "fock_static.cu")]))
+    jobs.append(("fock_sternheimer.o", nv + ["-c", os.path.join(CSRC, "fock_sternheimer.cu")]))
     for tag, t in (("f64", "double"), ("f32", "float")):
         jobs.append(("fock_persist_%s.o" % tag,
                      nv + ["-DFOCK_T=" + t, "-DFOCK_OPS_NAME=kPersist_%s" % tag,

@@ -177,6 +177,21 @@ cudaError_t launch_det_scale(const double* stats, int nbands, const double* occ,
 cudaError_t launch_det_to_double(void* w, int64_t n, const double* scale, cudaStream_t s);
 cudaError_t launch_det_pair_sums(const double* part, int npairs, int ncta, double* out, cudaStream_t s);
 
+// Sternheimer CG (fock_sternheimer.cu): kets are complex128 [m][npw], FP64.
+cudaError_t st_vmul(const double* v, const double* psi, double* w, int m, int64_t ntot, cudaStream_t s);
+cudaError_t st_dots(const double2* a, const double2* b, int m, int npw, double* out, cudaStream_t s);
+cudaError_t st_proj_coef(const double2* u, int nocc, const double2* x, int m, int npw, double* c, cudaStream_t s);
+cudaError_t st_rhs(const double2* w, const double2* u, const double* c, int nocc, int m, int npw, double2* b,
+                   cudaStream_t s);
+cudaError_t st_finish(double2* ap, const double2* p, const double* kin, const double* eps, const double2* u,
+                      const double* c, int nocc, double alpha, int m, int npw, cudaStream_t s);
+cudaError_t st_step(double2* x, double2* r, const double2* p, const double2* ap, const double* rr, const double* pap,
+                    int m, int npw, cudaStream_t s);
+cudaError_t st_dir(double2* p, const double2* r, const double* rr_new, const double* rr, int m, int npw,
+                   cudaStream_t s);
+cudaError_t st_gather_rows(const double2* src, double2* dst, const int* perm, int m, int npw, cudaStream_t s);
+cudaError_t st_gather_scalars(const double* src, double* dst, const int* perm, int m, cudaStream_t s);
+
 // E = scale * sum_p f_i f_j (1 or 2) e_p over the pairs; out[0] = E, out[1] = dE.
 cudaError_t launch_energy_reduce(const int2* pairs, int npairs, const double* occ,
                                  const double* epair, const double* dpair, double scale,

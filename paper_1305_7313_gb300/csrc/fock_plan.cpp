@@ -571,6 +571,26 @@ void plan_set_error(fock_plan* plan, const char* msg) {
 
 }  // namespace fockx
 
+namespace {
+
+// Device buffers of one Sternheimer solve, freed on every exit path.
+struct StBuffers {
+  std::vector<void*> ptrs;
+  ~StBuffers() {
+    for (void* q : ptrs) cudaFree(q);
+  }
+  template <class P>
+  cudaError_t alloc(P** out, size_t bytes) {
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, bytes < 16 ? 16 : bytes);
+    if (e == cudaSuccess) ptrs.push_back(q);
+    *out = static_cast<P*>(q);
+    return e;
+  }
+};
+
+}  // namespace
+
 extern "C" {
 
 const char* fock_status_string(fock_status s) {
@@ -962,6 +982,145 @@ fock_status fock_plan_set_tiling(fock_plan_t plan, const int tiles[3]) {
       return fail(plan, FOCK_ERR_INVALID_ARG, "a tile index is not below the pass's number of tilings");
   }
   for (int pass = 0; pass < 3; ++pass) plan->dp.tile[pass] = tiles[pass];
+  return FOCK_OK;
+}
+
+fock_status fock_sternheimer_solve(fock_plan_t p, const double* vloc, const void* u_G, int nocc,
+                                   const double* eps, const void* w_G, int nrhs, double alpha, double tol,
+                                   int maxiter, void* g_G, int* iters, double* resid, fock_stream_t stream) {
+  if (!p) return fail(nullptr, FOCK_ERR_INVALID_ARG, "plan is NULL");
+  if (p->prec != FOCK_PREC_FP64) return fail(p, FOCK_ERR_INVALID_ARG, "the Sternheimer solve needs an FP64 plan");
+  if (!vloc || !u_G || !eps || !w_G || !g_G) return fail(p, FOCK_ERR_INVALID_ARG, "NULL argument");
+  if (nocc < 1 || nrhs < 1 || nocc > (1 << 15) || nrhs > (1 << 15) || maxiter < 1)
+    return fail(p, FOCK_ERR_INVALID_ARG, "nocc, nrhs and maxiter must be >= 1 (nocc, nrhs <= 32768)");
+  if (!std::isfinite(alpha) || !(tol > 0.0) || !std::isfinite(tol))
+    return fail(p, FOCK_ERR_INVALID_ARG, "alpha must be finite and tol positive");
+  for (int n = 0; n < nrhs; ++n)
+    if (!std::isfinite(eps[n])) return fail(p, FOCK_ERR_INVALID_ARG, "eps must be finite");
+  const size_t npw = (size_t)p->npw;
+  const size_t kb = npw * nrhs * sizeof(double2);
+  {
+    const char* g = static_cast<const char*>(g_G);
+    const char* w = static_cast<const char*>(w_G);
+    const char* u = static_cast<const char*>(u_G);
+    const size_t ub = npw * nocc * sizeof(double2);
+    if ((g < w + kb && w < g + kb) || (g < u + ub && u < g + kb))
+      return fail(p, FOCK_ERR_INVALID_ARG, "g_G overlaps w_G or u_G");
+  }
+  fock_status st = check_device(p);
+  if (st != FOCK_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = ensure_workspace(p, nrhs, 1);
+  if (st != FOCK_OK) return st;
+  p->fixed_nb = 0;  // the real-space workspace is overwritten
+  const double2* u = static_cast<const double2*>(u_G);
+  StBuffers buf;
+  double2 *x, *r, *pk, *ap, *tmp;
+  double *kin, *d_eps, *c, *rr, *rrn, *pap, *sc;
+  int* perm;
+  const size_t nb8 = sizeof(double) * nrhs;
+  FOCK_CUDA(p, buf.alloc(&x, kb));
+  FOCK_CUDA(p, buf.alloc(&r, kb));
+  FOCK_CUDA(p, buf.alloc(&pk, kb));
+  FOCK_CUDA(p, buf.alloc(&ap, kb));
+  FOCK_CUDA(p, buf.alloc(&tmp, kb));
+  FOCK_CUDA(p, buf.alloc(&kin, sizeof(double) * npw));
+  FOCK_CUDA(p, buf.alloc(&d_eps, nb8));
+  FOCK_CUDA(p, buf.alloc(&c, sizeof(double) * nocc * nrhs));
+  FOCK_CUDA(p, buf.alloc(&rr, nb8));
+  FOCK_CUDA(p, buf.alloc(&rrn, nb8));
+  FOCK_CUDA(p, buf.alloc(&pap, nb8));
+  FOCK_CUDA(p, buf.alloc(&sc, nb8));
+  FOCK_CUDA(p, buf.alloc(&perm, sizeof(int) * nrhs));
+  // |G|^2 / 2 on the sphere, in the plan's canonical order
+  std::vector<double> kin_h(npw);
+  for (size_t g = 0; g < npw; ++g)
+    kin_h[g] = 0.5 * fockx::lattice::g2_of(p->recip, p->miller[3 * g], p->miller[3 * g + 1], p->miller[3 * g + 2]);
+  std::vector<double> eps_h(eps, eps + nrhs);
+  FOCK_CUDA(p, cudaMemcpyAsync(kin, kin_h.data(), sizeof(double) * npw, cudaMemcpyHostToDevice, s));
+  FOCK_CUDA(p, cudaMemcpyAsync(d_eps, eps_h.data(), nb8, cudaMemcpyHostToDevice, s));
+
+  const int ip = (int)npw;
+  const int nbat = bands_per_grid_batch(p);
+  // (H - eps_n + alpha P) on the kets q at positions [0, m) into out
+  auto apply_a = [&](const double2* q, int m, double2* out) -> fock_status {
+    for (int b0 = 0; b0 < m; b0 += nbat)
+      FOCK_CUDA(p, p->ops->to_real(p->dp, q, m, b0, std::min(nbat, m - b0), p->ws.h, p->ws.psi, s));
+    FOCK_CUDA(p, fockx::st_vmul(vloc, static_cast<const double*>(p->ws.psi), static_cast<double*>(p->ws.w), m,
+                                p->dp.ntot, s));
+    for (int b0 = 0; b0 < m; b0 += nbat)
+      FOCK_CUDA(p, p->ops->to_sphere(p->dp, p->ws.w, m, b0, std::min(nbat, m - b0), p->ws.h, out, s));
+    FOCK_CUDA(p, fockx::st_proj_coef(u, nocc, q, m, ip, c, s));
+    FOCK_CUDA(p, fockx::st_finish(out, q, kin, d_eps, u, c, nocc, alpha, m, ip, s));
+    return FOCK_OK;
+  };
+
+  // b = -Q w into r; x = 0; p = r; rr = <r|r>
+  FOCK_CUDA(p, fockx::st_proj_coef(u, nocc, static_cast<const double2*>(w_G), nrhs, ip, c, s));
+  FOCK_CUDA(p, fockx::st_rhs(static_cast<const double2*>(w_G), u, c, nocc, nrhs, ip, r, s));
+  FOCK_CUDA(p, cudaMemsetAsync(x, 0, kb, s));
+  FOCK_CUDA(p, cudaMemcpyAsync(pk, r, kb, cudaMemcpyDeviceToDevice, s));
+  FOCK_CUDA(p, fockx::st_dots(r, r, nrhs, ip, rr, s));
+
+  // order[k]: the band at position k; positions [0, m) are not converged
+  std::vector<int> order(nrhs), it_h(nrhs, 0), keep;
+  for (int n = 0; n < nrhs; ++n) order[n] = n;
+  std::vector<double> rr_h(nrhs);
+  int m = nrhs;
+  for (int it = 0; it < maxiter && m > 0; ++it) {
+    st = apply_a(pk, m, ap);
+    if (st != FOCK_OK) return st;
+    FOCK_CUDA(p, fockx::st_dots(pk, ap, m, ip, pap, s));
+    FOCK_CUDA(p, fockx::st_step(x, r, pk, ap, rr, pap, m, ip, s));
+    FOCK_CUDA(p, fockx::st_dots(r, r, m, ip, rrn, s));
+    FOCK_CUDA(p, fockx::st_dir(pk, r, rrn, rr, m, ip, s));
+    FOCK_CUDA(p, cudaMemcpyAsync(rr, rrn, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    FOCK_CUDA(p, cudaMemcpyAsync(rr_h.data(), rrn, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    FOCK_CUDA(p, cudaStreamSynchronize(s));
+    for (int k = 0; k < m; ++k) ++it_h[order[k]];
+    // regroup: not converged first, then converged, each in their order
+    keep.clear();
+    for (int k = 0; k < m; ++k)
+      if (!(std::sqrt(rr_h[k]) < tol)) keep.push_back(k);
+    const int m_new = (int)keep.size();
+    for (int k = 0; k < m; ++k)
+      if (std::sqrt(rr_h[k]) < tol) keep.push_back(k);
+    bool moved = false;
+    for (int k = 0; k < m; ++k) moved = moved || keep[k] != k;
+    if (moved) {
+      FOCK_CUDA(p, cudaMemcpyAsync(perm, keep.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+      double2* rows[3] = {x, r, pk};
+      for (double2* a : rows) {
+        FOCK_CUDA(p, fockx::st_gather_rows(a, tmp, perm, m, ip, s));
+        FOCK_CUDA(p, cudaMemcpyAsync(a, tmp, npw * m * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+      }
+      double* scal[2] = {rr, d_eps};
+      for (double* a : scal) {
+        FOCK_CUDA(p, fockx::st_gather_scalars(a, sc, perm, m, s));
+        FOCK_CUDA(p, cudaMemcpyAsync(a, sc, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+      }
+      std::vector<int> o2(order);
+      std::vector<double> r2(rr_h);
+      for (int k = 0; k < m; ++k) {
+        o2[k] = order[keep[k]];
+        r2[k] = rr_h[keep[k]];
+      }
+      order.swap(o2);
+      rr_h.swap(r2);
+    }
+    m = m_new;
+  }
+  // back to the original band order: g[order[k]] = x[k]
+  std::vector<int> inv(nrhs);
+  for (int k = 0; k < nrhs; ++k) inv[order[k]] = k;
+  FOCK_CUDA(p, cudaMemcpyAsync(perm, inv.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+  FOCK_CUDA(p, fockx::st_gather_rows(x, static_cast<double2*>(g_G), perm, nrhs, ip, s));
+  FOCK_CUDA(p, cudaMemcpyAsync(rr_h.data(), rr, nb8, cudaMemcpyDeviceToHost, s));
+  FOCK_CUDA(p, cudaStreamSynchronize(s));
+  for (int k = 0; k < nrhs; ++k) {
+    if (iters) iters[order[k]] = it_h[order[k]];
+    if (resid) resid[order[k]] = std::sqrt(rr_h[k]);
+  }
   return FOCK_OK;
 }
 

@@ -127,6 +127,15 @@ class FockPlan:
     def pair_energies(self, psi_G, pairs, want_d=False, stream=None):
         return _lib.fock_pair_energies(self.handle, psi_G, pairs, want_d, stream)
 
+    def sternheimer(self, vloc, u_G, eps, w_G, alpha, tol, maxiter=1000, g_G=None, stream=None):
+        """(g, iters, resid) solving (H - eps_n + alpha P) g_n = -Q w_n for the
+        model H = kinetic + V(r) on this plan's sphere (FP64 plans): the
+        Sternheimer equation of §3.1 by CG with converged/unconverged band
+        regrouping.  ``vloc``: CUDA float64 [N, N, N]; ``u_G``: occupied
+        states, ``w_G``: right-hand kets, CUDA complex128 [*, npw]."""
+        ntot = self.grid[0] * self.grid[1] * self.grid[2]
+        return _lib.fock_sternheimer_solve(self.handle, ntot, vloc, u_G, eps, w_G, alpha, tol, maxiter, g_G, stream)
+
     def close(self):
         if self.handle is not None:
             _lib.fock_destroy(self.handle)

@@ -124,3 +124,38 @@ def test_autotuner_picks_a_candidate_and_keeps_results(tmp_path, monkeypatch):
     ex, _ = b.run()
     assert abs(ex[2] - e0) <= 5e-6 * abs(e0)
     b.close()
+
+
+@pytest.mark.parametrize("persistent", [0, 2])
+def test_the_full_sixteen_system_batch_matches_single_applies(persistent):
+    # the benchmark's batch: 16 systems on 48^3, 64^3, 72^3 and 96^3 grids
+    # (L = 27 N / 96, Ecut 12 Ha, 32-384 bands, 298,602 pairs), mixed form:
+    # E_x of every system and V_x psi of the last band of one system per grid
+    # size against the same systems applied one at a time
+    from paper_1305_7313_gb300.workloads import batched_systems, cubic_cell
+    torch = require_gpu()
+    systems = batched_systems()
+    plans, psis, occs = [], [], []
+    for sy in systems:
+        p = FockPlan(sy["N"], cubic_cell(sy["L"]), sy["ecut"], sy["kernel"], sy["omega"], sy["prec"])
+        c = synth.orbitals(p.miller, cubic_cell(sy["L"]), sy["nb"], sy["seed"])
+        plans.append(p)
+        psis.append(torch.from_numpy(c).cuda())
+        occs.append(np.full(sy["nb"], 2.0))
+    assert sum(sy["nb"] * (sy["nb"] + 1) // 2 for sy in systems) == 298602
+    batch = FockBatch(plans, psis, occs, persistent=persistent, slot_chains=16)
+    ex, _ = batch.run()
+    first_of_size = {}
+    for k, sy in enumerate(systems):
+        first_of_size.setdefault(sy["N"], k)
+    for k, sy in enumerate(systems):
+        v, e, _ = plans[k].apply(psis[k], occs[k])
+        assert abs(ex[k] - e) <= 5e-6 * abs(e), (k, sy["N"])
+        if first_of_size[sy["N"]] == k:
+            last = sy["nb"] - 1
+            assert rel_inf(batch.vpsi[k][last].cpu().numpy(), v[last].cpu().numpy()) <= 2e-5, (k, sy["N"])
+        del v
+    batch.close()
+    for p in plans:
+        p.close()
+    torch.cuda.empty_cache()
