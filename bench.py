@@ -178,9 +178,17 @@ MEASURED_TRAFFIC_PER_CHAIN = {
 }
 
 
+def pair_loop_ms(res, steps):
+    """Device time per step of the pair passes (forward, column, inverse): the
+    step time minus the phases around them, which run on the call's stream
+    alone (the pair passes' launches may overlap on several streams)."""
+    other = sum(res["phase_ms"].get(k, 0.0) for k in ("to_real", "to_sphere", "energy")) / steps
+    return res["ms"] / steps - other
+
+
 def pair_loop_rate(pairs, res, steps):
-    """Pairs per second of the pair passes alone (forward, column, inverse; device time)."""
-    ms = sum(res["phase_ms"].get(k, 0.0) for k in ("pair_fwd", "pair_col", "pair_inv")) / steps
+    """Pairs per second of the pair passes alone."""
+    ms = pair_loop_ms(res, steps)
     return pairs / (ms * 1e-3) if ms > 0 else None
 
 
@@ -191,8 +199,12 @@ def measured_traffic(form, n, kernel, band_block, chains_per_launch):
     return per * chains_per_launch
 
 
-def roofline(form, plan, res, steps, peaks, peak_src, band_block=16):
-    """Roofline of the dominant pair kernel (the phase with the largest device time)."""
+def roofline(form, plan, res, steps, peaks, peak_src, band_block=16, streams=1):
+    """Roofline of the dominant pair kernel (the phase with the largest device
+    time), or of the three pair passes together when their launches overlap
+    on several streams (a launch's duration then includes its neighbours')."""
+    if streams > 1:
+        return loop_roofline(form, plan, res, steps, peaks, peak_src, band_block, streams)
     n = plan.grid[0]
     ntot = float(n) ** 3
     nc = 2 * (n // 2 + 1)
@@ -272,6 +284,49 @@ def form_summary(res_line, roof, err):
     return out
 
 
+def loop_roofline(form, plan, res, steps, peaks, peak_src, band_block, streams):
+    """Achieved rate of the three pair passes together: their algorithmic flops
+    (FP64, double-float) or bytes (mixed) per step over the pair loop's device
+    time per step."""
+    n = plan.grid[0]
+    ntot = float(n) ** 3
+    nc = 2 * (n // 2 + 1)
+    chains = res["stats"]["chains"]
+    ms = pair_loop_ms(res, steps)
+    label = "pair passes (fwd + col + inv, launches on %d streams)" % streams
+    if form in ("fp64", "df64"):
+        log2n = np.log2(n)
+        per_chain = 5 * ntot * 2 * log2n * 2 + 2 * 5 * ntot * log2n * nc / n
+        achieved = per_chain * chains / (ms * 1e-3) / 1e12
+        per_clk = FP64_FLOPS_PER_CLK if form == "fp64" else DF64_FLOPS_PER_CLK
+        peak = per_clk * 2070.0e6 / 1e12
+        mhz = res["clocks"].get("sm_mhz") or 2070.0
+        src = ("measured DFMA loop, 2070 MHz" if form == "fp64" else
+               "measured FP32 FMA loop / 9.4 FP32 instructions per double-float flop, 2070 MHz")
+        out = {"bound": "alu", "kernel": label, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+               "frac": achieved / peak, "peak_src": src,
+               "frac_at_sampled_clock": achieved / (per_clk * mhz * 1e6 / 1e12)}
+    else:
+        kept, total = plan.columns()
+        hbytes = n * n * nc * 8.0 * kept / total
+        plane = ntot * 4.0 / max(1, band_block)
+        per_chain = 4 * hbytes + 16 * plane
+        achieved = per_chain * chains / (ms * 1e-3) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        out = {"bound": "hbm", "kernel": label, "achieved": achieved, "peak": peak, "unit": "GB/s",
+               "frac": achieved / peak, "peak_src": peak_src + " (hbm copy)", "bytes_per_chain": per_chain}
+    per = MEASURED_LOOP_TRAFFIC_PER_CHAIN.get((form, n, band_block))
+    out.update({"traffic": per * chains if per else None, "traffic_unit": "DRAM bytes per step (ncu, all three kernels)",
+                "ms_pair_loop": ms, "chains_per_step": chains})
+    return out
+
+
+# DRAM bytes (read + write) per chain of the three pair kernels together, from
+# ncu captures of the 96^3 pair passes (profiles/pair_passes_*_96.md), by form
+# and band block; scaled to a step by its chains
+MEASURED_LOOP_TRAFFIC_PER_CHAIN = {}
+
+
 def fixed_blocks(plan, args):
     """--chain-batch / --band-block given: set them and report them as the choice."""
     if args.chain_batch:
@@ -280,8 +335,9 @@ def fixed_blocks(plan, args):
         plan.set_band_block(args.band_block)
     if args.tiles:
         plan.set_tiling([int(x) for x in args.tiles])
+    plan.set_streams(args.streams)
     return {"chain_batch": args.chain_batch, "band_block": args.band_block or 16, "tiles": args.tiles,
-            "tuned_on_bands": 0, "candidates": 0}
+            "streams": args.streams, "tuned_on_bands": 0, "candidates": 0}
 
 
 def tune_on_subset(plan, c, occ, nbands, reps=2):
@@ -291,7 +347,8 @@ def tune_on_subset(plan, c, occ, nbands, reps=2):
     sub = torch.from_numpy(np.ascontiguousarray(c[:nbands])).cuda()
     res = tune_apply(plan, sub, occ[:nbands], reps=reps, use_cache=False)
     del sub
-    return {"chain_batch": res["chain_batch"], "band_block": res["band_block"], "tiles": res.get("tiles"),
+    return {"chain_batch": res["chain_batch"], "band_block": res["band_block"], "streams": res.get("streams", 1),
+            "tiles": res.get("tiles"),
             "tiling": tiling_text(res.get("tiling")), "tuned_on_bands": nbands, "candidates": len(res["table"])}
 
 
@@ -643,6 +700,8 @@ def main():
                     help="with --no-tune: chains per pair-pass launch of the Gamma-point forms")
     ap.add_argument("--band-block", type=int, default=0,
                     help="with --no-tune: band block of the Gamma-point pair schedule")
+    ap.add_argument("--streams", type=int, default=1,
+                    help="with --no-tune: streams the pair-pass launches rotate over (1-4)")
     ap.add_argument("--tiles", default="",
                     help="with --no-tune: FFT tiling of the forward, column and inverse passes, e.g. 100")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison line")
@@ -678,7 +737,7 @@ def main():
     tuned = None
     if not args.no_tune:
         tuned = tune_on_subset(plan, c, occ, min(w["nb"], max(8, args.tune_bands // 2)), reps=1)
-    elif args.chain_batch or args.band_block or args.tiles:
+    elif args.chain_batch or args.band_block or args.tiles or args.streams > 1:
         tuned = fixed_blocks(plan, args)
     psi = torch.from_numpy(c).cuda()
     pairs = w["nb"] * (w["nb"] + 1) // 2
@@ -686,7 +745,8 @@ def main():
     ms_step = res["ms"] / args.steps
     value = pairs * args.steps / (res["ms"] * 1e-3)
     form = {PREC_FP64: "fp64", PREC_MIXED32: "mixed32"}.get(w["prec"], "df64")
-    roof = roofline(form, plan, res, args.steps, peaks, peak_src, tuned["band_block"] if tuned else 16)
+    roof = roofline(form, plan, res, args.steps, peaks, peak_src, tuned["band_block"] if tuned else 16,
+                    tuned.get("streams", 1) if tuned else 1)
     err = golden_errors(plan, c, w) if world == 1 else None
 
     # ---- end to end through the public API from pinned host memory
@@ -719,7 +779,7 @@ def main():
         tunedm = None
         if not args.no_tune:
             tunedm = tune_on_subset(planm, cm, occm, min(wm["nb"], args.tune_bands))
-        elif args.chain_batch or args.band_block or args.tiles:
+        elif args.chain_batch or args.band_block or args.tiles or args.streams > 1:
             tunedm = fixed_blocks(planm, args)
         psim = torch.from_numpy(cm).cuda()
         resm = time_form(planm, psim, occm, args.steps, args.warmup, rank=rank, world=world)
@@ -727,7 +787,7 @@ def main():
         mixed = {"workload": wm["name"], "value": pm * args.steps / (resm["ms"] * 1e-3), "unit": UNIT,
                  "ms_per_step": resm["ms"] / args.steps, "dtype": "f32",
                  "roofline": roofline("mixed32", planm, resm, args.steps, peaks, peak_src,
-                                      tunedm["band_block"] if tunedm else 16),
+                                      tunedm["band_block"] if tunedm else 16, tunedm.get("streams", 1) if tunedm else 1),
                  "pair_loop_pairs_per_s": pair_loop_rate(pm, resm, args.steps),
                  "gpu_launches": resm["launches"], "clocks": resm["clocks"], "tuned": tunedm}
         mixed["summary"] = form_summary(mixed, mixed["roofline"], golden_errors(planm, cm, wm) if world == 1 else None)
@@ -746,7 +806,7 @@ def main():
         tunedd = None
         if not args.no_tune:
             tunedd = tune_on_subset(pland, cd, occd, min(wd["nb"], args.tune_bands), reps=1)
-        elif args.chain_batch or args.band_block or args.tiles:
+        elif args.chain_batch or args.band_block or args.tiles or args.streams > 1:
             tunedd = fixed_blocks(pland, args)
         psid = torch.from_numpy(cd).cuda()
         resd = time_form(pland, psid, occd, args.steps, args.warmup, rank=rank, world=world)
@@ -754,7 +814,7 @@ def main():
         df = {"workload": wd["name"], "value": pd * args.steps / (resd["ms"] * 1e-3), "unit": UNIT,
               "ms_per_step": resd["ms"] / args.steps, "dtype": "f32x2 (double-float)",
               "roofline": roofline("df64", pland, resd, args.steps, peaks, peak_src,
-                                   tunedd["band_block"] if tunedd else 16),
+                                   tunedd["band_block"] if tunedd else 16, tunedd.get("streams", 1) if tunedd else 1),
               "pair_loop_pairs_per_s": pair_loop_rate(pd, resd, args.steps),
               "gpu_launches": resd["launches"], "clocks": resd["clocks"], "tuned": tunedd}
         df["summary"] = form_summary(df, df["roofline"], golden_errors(pland, cd, wd) if world == 1 else None)
@@ -789,7 +849,7 @@ def main():
         cpu = cpu_baseline(w, args.ref_bands)
         cpu.pop("seconds", None)
     def brief_tuned(t):
-        return None if t is None else {k: t.get(k) for k in ("chain_batch", "band_block", "tiling")}
+        return None if t is None else {k: t.get(k) for k in ("chain_batch", "band_block", "streams", "tiling")}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -158,6 +158,16 @@ fock_status fock_plan_reserve(fock_plan_t plan, int nb_max);
  * Takes effect at the next call.  Errors: INVALID_ARG. */
 fock_status fock_plan_set_batch(fock_plan_t plan, int chain_batch);
 
+/* Streams of the pair loop of fock_apply and fock_apply_shard (1 to 4, default
+ * 1).  With S > 1, launch k of the pair passes runs on stream k mod S: the
+ * call's stream or one of S - 1 streams the plan owns, each with its own
+ * transform buffer (S times the buffer memory), so that the kernels of
+ * neighbouring launches run side by side; the call's stream waits for all of
+ * them before the energies are reduced, and results agree up to the order of
+ * the floating-point accumulations.  Takes effect at the next call.
+ * Errors: INVALID_ARG. */
+fock_status fock_plan_set_streams(fock_plan_t plan, int streams);
+
 /* Phases of a call, for fock_plan_stats. */
 enum {
   FOCK_PHASE_TO_REAL = 0,   /* G-sphere scatter + inverse 3D FFT of the orbitals */

@@ -46,6 +46,7 @@ from ._lib import (  # noqa: F401
     fock_plan_reserve,
     fock_plan_set_band_block,
     fock_plan_set_batch,
+    fock_plan_set_streams,
     fock_plan_set_tiling,
     fock_plan_set_timing,
     fock_plan_stats,

@@ -85,6 +85,7 @@ _SIGNATURES = {
     "fock_plan_columns": [_vp, _c_i64_p, _c_i64_p],
     "fock_plan_set_deterministic": [_vp, ctypes.c_int],
     "fock_plan_set_timing": [_vp, ctypes.c_int],
+    "fock_plan_set_streams": [_vp, ctypes.c_int],
     "fock_plan_stats": [_vp, ctypes.POINTER(FockStats)],
     "fock_apply": [_vp, _vp, ctypes.c_int, _c_dbl_p, _vp, _c_dbl_p, _c_dbl_p, _vp],
     "fock_apply_shard": [_vp, _vp, ctypes.c_int, _c_dbl_p, ctypes.c_int, ctypes.c_int, _vp,
@@ -291,6 +292,11 @@ def fock_plan_set_tiling(plan, tiles):
     """Tiling (0 or 1) of the forward plane, column and inverse plane passes."""
     t = (ctypes.c_int * 3)(*[int(x) for x in tiles])
     _check(load().fock_plan_set_tiling(plan, t), plan)
+
+
+def fock_plan_set_streams(plan, streams):
+    """Streams (1 to 4) the pair-pass launches of an apply rotate over."""
+    _check(load().fock_plan_set_streams(plan, int(streams)), plan)
 
 
 def fock_plan_device_bytes(plan):

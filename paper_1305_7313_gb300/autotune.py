@@ -8,6 +8,8 @@ The knobs are the ones that decide how pair work maps onto the GPU:
 * ``band_block`` — bands per block of the pair schedule (pairs are visited in
   band_block x band_block blocks, so consecutive chains share orbitals and
   accumulators in L2);
+* ``streams`` — how many streams the launches of the pair passes rotate over
+  (neighbouring launches overlap on the GPU);
 * ``tiling`` — the FFT tiling (radix plan and threads per line) of each of the
   three pair passes, where the library compiled two (``FockPlan.tilings()``);
   searched one pass at a time after the pair-block search;
@@ -84,37 +86,57 @@ PASSES = ("pair_fwd", "pair_col", "pair_inv")
 
 
 def tune_apply(plan, psi, occ, chain_batches=(8, 17, 19, 32, 38), band_blocks=(8, 16, 32), reps=2,
-               use_cache=True, tiling=True):
-    """Fastest (chain_batch, band_block) and FFT tiling for ``plan.apply(psi, occ)``;
-    sets them on the plan.
+               use_cache=True, tiling=True, streams=(2, 3, 4)):
+    """Fastest (chain_batch, band_block), stream count and FFT tiling for
+    ``plan.apply(psi, occ)``; sets them on the plan.
 
-    The pair-block grid is timed at the default tiling; then, one pair pass at a
-    time, the pass's other tiling is timed at the best setting so far and kept
-    if faster.  Returns ``{"chain_batch", "band_block", "tiles", "tiling", "ms",
-    "table"}``; ``tiling`` names each pass's chosen radix plan and threads per line.
+    The pair-block grid is timed on one stream at the default tiling; then
+    each stream count of ``streams`` with the best chain batch and with twice
+    it (launches on several streams overlap, and larger ones fill the GPU
+    better side by side); then, one pair pass at a time, the pass's other
+    tiling is timed at the best setting so far and kept if faster.  Returns
+    ``{"chain_batch", "band_block", "streams", "tiles", "tiling", "ms",
+    "table"}``; ``tiling`` names each pass's chosen radix plan and threads per
+    line.
     """
     key = "apply|%s|N%d|prec%d|nb%d" % (_gpu_name(), plan.grid[0], plan.precision, psi.shape[0])
     has_tiling = tiling and hasattr(plan, "tilings")
+    has_streams = bool(streams) and hasattr(plan, "set_streams")
     if use_cache:
         hit = _load_cache().get(key)
-        if hit and ("tiles" in hit or not has_tiling):
+        if hit and ("tiles" in hit or not has_tiling) and ("streams" in hit or not has_streams):
             plan.set_batch(hit["chain_batch"])
             plan.set_band_block(hit["band_block"])
             if has_tiling:
                 plan.set_tiling(hit["tiles"])
+            if has_streams:
+                plan.set_streams(hit["streams"])
             return dict(hit, cached=True)
     table = []
     tiles = [0, 0, 0]
     if has_tiling:
         plan.set_tiling(tiles)
+    if has_streams:
+        plan.set_streams(1)
     for cb, bb in itertools.product(chain_batches, band_blocks):
         plan.set_batch(cb)
         plan.set_band_block(bb)
         ms = _time_ms(lambda: plan.apply(psi, occ, want_ex=True), reps)
-        table.append({"chain_batch": cb, "band_block": bb, "tiles": list(tiles), "ms": ms})
+        table.append({"chain_batch": cb, "band_block": bb, "streams": 1, "tiles": list(tiles), "ms": ms})
     best = min(table, key=lambda r: r["ms"])
-    plan.set_batch(best["chain_batch"])
     plan.set_band_block(best["band_block"])
+    best_streams = 1
+    if has_streams:
+        for ns, cb in itertools.product(streams, (best["chain_batch"], 2 * best["chain_batch"])):
+            plan.set_streams(ns)
+            plan.set_batch(cb)
+            ms = _time_ms(lambda: plan.apply(psi, occ, want_ex=True), reps)
+            row = {"chain_batch": cb, "band_block": best["band_block"], "streams": ns, "tiles": list(tiles), "ms": ms}
+            table.append(row)
+            if ms < best["ms"]:
+                best, best_streams = row, ns
+        plan.set_streams(best_streams)
+    plan.set_batch(best["chain_batch"])
     best_ms = best["ms"]
     options = plan.tilings() if has_tiling else {}
     for p, name in enumerate(PASSES):
@@ -124,13 +146,14 @@ def tune_apply(plan, psi, occ, chain_batches=(8, 17, 19, 32, 38), band_blocks=(8
         trial[p] = 1
         plan.set_tiling(trial)
         ms = _time_ms(lambda: plan.apply(psi, occ, want_ex=True), reps)
-        table.append({"chain_batch": best["chain_batch"], "band_block": best["band_block"], "tiles": trial,
-                      "ms": ms})
+        table.append({"chain_batch": best["chain_batch"], "band_block": best["band_block"], "streams": best_streams,
+                      "tiles": trial, "ms": ms})
         if ms < best_ms:
             tiles, best_ms = trial, ms
     if has_tiling:
         plan.set_tiling(tiles)
-    res = {"chain_batch": best["chain_batch"], "band_block": best["band_block"], "tiles": tiles, "ms": best_ms,
+    res = {"chain_batch": best["chain_batch"], "band_block": best["band_block"], "streams": best_streams,
+           "tiles": tiles, "ms": best_ms,
            "tiling": {name: dict(options[name][tiles[p]], tile=tiles[p])
                       for p, name in enumerate(PASSES) if name in options},
            "table": table}

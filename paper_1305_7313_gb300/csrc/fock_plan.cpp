@@ -49,6 +49,7 @@ struct Workspace {
   void* psi = nullptr;
   void* w = nullptr;
   void* h = nullptr;
+  void* hx[3] = {nullptr, nullptr, nullptr};  // transform buffers of the other pair-loop streams
   size_t h_bytes = 0;
   int npair_cap = 0;
   double* epair = nullptr;
@@ -112,6 +113,11 @@ struct fock_plan {
   int fixed_nb = 0;
   int fixed_sched_nt = -1;
   int fixed_sched_bb = 0;
+  // pair-loop launches rotate over the caller's stream and streams - 1
+  // plan-owned ones, each with its own transform buffer
+  int streams = 1;
+  cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
   // launch accounting and optional per-launch event timing
   fock_stats stats{};
   bool timing = false;
@@ -151,6 +157,7 @@ void free_ws(Workspace& w) {
   cudaFree(w.psi);
   cudaFree(w.w);
   cudaFree(w.h);
+  for (void* x : w.hx) cudaFree(x);
   cudaFree(w.epair);
   cudaFree(w.dpair);
   cudaFree(w.pairs);
@@ -436,6 +443,18 @@ fock_status det_prepare(fock_plan* p, int nbands, int nsrc, DevPlan* dp, cudaStr
   return FOCK_OK;
 }
 
+// The plan-owned streams of the pair loop, their fork/join events and
+// transform buffers.
+fock_status pipeline_resources(fock_plan* p) {
+  if (!p->ev_fork) FOCK_CUDA(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+  for (int k = 0; k + 1 < p->streams; ++k) {
+    if (!p->aux[k]) FOCK_CUDA(p, cudaStreamCreateWithFlags(&p->aux[k], cudaStreamNonBlocking));
+    if (!p->ev_join[k]) FOCK_CUDA(p, cudaEventCreateWithFlags(&p->ev_join[k], cudaEventDisableTiming));
+    if (!p->ws.hx[k]) FOCK_CUDA(p, dev_alloc(&p->ws.hx[k], p->ws.h_bytes));
+  }
+  return FOCK_OK;
+}
+
 fock_status apply_impl(fock_plan* p, const void* psiG, int nb, const double* occ, int shard,
                        int nshards, void* vpsiG, double* ex, double* dex, fock_stream_t stream) {
   fock_status st = validate_apply(p, psiG, nb, vpsiG);
@@ -493,21 +512,39 @@ fock_status apply_impl(fock_plan* p, const void* psiG, int nb, const double* occ
   p->stats.chain_batch = p->chain_batch;
   p->stats.chains = c1 - c0;
   p->stats.pairs = std::min(npairs, 2 * c1) - std::min(npairs, 2 * c0);
-  for (int c = c0; c < c1; c += p->chain_batch) {
+  // several streams: launch k runs on stream k mod S (stream 0 = the call's)
+  // with that stream's transform buffer, so neighbouring launches' kernels
+  // share the GPU; W and the pair energies take atomic (or exact integer)
+  // updates, which commute
+  const int nst = std::max(1, std::min(p->streams, (c1 - c0 + p->chain_batch - 1) / p->chain_batch));
+  if (nst > 1) {
+    st = pipeline_resources(p);
+    if (st != FOCK_OK) return st;
+    FOCK_CUDA(p, cudaEventRecord(p->ev_fork, s));
+    for (int k = 0; k + 1 < nst; ++k) FOCK_CUDA(p, cudaStreamWaitEvent(p->aux[k], p->ev_fork, 0));
+  }
+  for (int c = c0, k = 0; c < c1; c += p->chain_batch, ++k) {
     const int cnt = std::min(p->chain_batch, c1 - c);
     const Chain* ch = p->ws.chains + c;
+    const int j = k % nst;
+    cudaStream_t sk = j == 0 ? s : p->aux[j - 1];
+    void* hk = j == 0 ? p->ws.h : p->ws.hx[j - 1];
     {
-      PhaseScope ps(p, FOCK_PHASE_PAIR_FWD, 1, s);
-      FOCK_CUDA(p, p->ops->pair_fwd(dp, p->ws.psi, ch, cnt, p->ws.h, s));
+      PhaseScope ps(p, FOCK_PHASE_PAIR_FWD, 1, sk);
+      FOCK_CUDA(p, p->ops->pair_fwd(dp, p->ws.psi, ch, cnt, hk, sk));
     }
     {
-      PhaseScope ps(p, FOCK_PHASE_PAIR_COL, 1, s);
-      FOCK_CUDA(p, p->ops->pair_col(dp, p->ws.h, ch, cnt, ep, dpp, s));
+      PhaseScope ps(p, FOCK_PHASE_PAIR_COL, 1, sk);
+      FOCK_CUDA(p, p->ops->pair_col(dp, hk, ch, cnt, ep, dpp, sk));
     }
     {
-      PhaseScope ps(p, FOCK_PHASE_PAIR_INV, 1, s);
-      FOCK_CUDA(p, p->ops->pair_inv(dp, p->ws.psi, p->ws.w, p->ws.occT, ch, cnt, p->ws.h, s));
+      PhaseScope ps(p, FOCK_PHASE_PAIR_INV, 1, sk);
+      FOCK_CUDA(p, p->ops->pair_inv(dp, p->ws.psi, p->ws.w, p->ws.occT, ch, cnt, hk, sk));
     }
+  }
+  for (int k = 0; k + 1 < nst; ++k) {
+    FOCK_CUDA(p, cudaEventRecord(p->ev_join[k], p->aux[k]));
+    FOCK_CUDA(p, cudaStreamWaitEvent(s, p->ev_join[k], 0));
   }
   const int p0 = std::min(npairs, 2 * c0), p1 = std::min(npairs, 2 * c1);
   if (p->det) {
@@ -1131,9 +1168,20 @@ fock_status fock_plan_set_batch(fock_plan_t plan, int chain_batch) {
   if (chain_batch != plan->chain_batch) {
     cudaFree(plan->ws.h);  // stream-ordered work using it has been queued by earlier calls;
     plan->ws.h = nullptr;  // cudaFree waits for the device to finish with it
+    for (void*& x : plan->ws.hx) {
+      cudaFree(x);
+      x = nullptr;
+    }
     plan->ws.h_bytes = 0;
     plan->chain_batch = chain_batch;
   }
+  return FOCK_OK;
+}
+
+fock_status fock_plan_set_streams(fock_plan_t plan, int streams) {
+  if (!plan) return fail(nullptr, FOCK_ERR_INVALID_ARG, "plan is NULL");
+  if (streams < 1 || streams > 4) return fail(plan, FOCK_ERR_INVALID_ARG, "streams must be 1 to 4");
+  plan->streams = streams;
   return FOCK_OK;
 }
 
@@ -1379,6 +1427,11 @@ fock_status fock_pair_energies(fock_plan_t plan, const void* psi_G, int nb, cons
 fock_status fock_destroy(fock_plan_t plan) {
   if (!plan) return FOCK_OK;
   for (cudaEvent_t e : plan->events) cudaEventDestroy(e);
+  if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+  for (int k = 0; k < 3; ++k) {
+    if (plan->ev_join[k]) cudaEventDestroy(plan->ev_join[k]);
+    if (plan->aux[k]) cudaStreamDestroy(plan->aux[k]);
+  }
   free_ws(plan->ws);
   cudaFree(plan->d_gidx);
   cudaFree(plan->d_gidxneg);

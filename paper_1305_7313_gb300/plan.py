@@ -44,6 +44,10 @@ class FockPlan:
     def set_band_block(self, band_block):
         _lib.fock_plan_set_band_block(self.handle, band_block)
 
+    def set_streams(self, streams):
+        """1 to 4 streams for the pair-pass launches (more than 1: neighbouring launches overlap)."""
+        _lib.fock_plan_set_streams(self.handle, streams)
+
     def set_timing(self, enable):
         _lib.fock_plan_set_timing(self.handle, enable)
 

@@ -27,6 +27,17 @@ class FakePlan:
         self.applies += 1
 
 
+class FakeStreamPlan(FakePlan):
+    """A plan that also takes a stream count."""
+
+    def __init__(self, n=96, precision=0):
+        super().__init__(n, precision)
+        self.streams = None
+
+    def set_streams(self, ns):
+        self.streams = ns
+
+
 class FakeTiledPlan(FakePlan):
     """A plan whose forward and inverse plane passes have two FFT tilings and
     whose column pass has one, as the library reports them."""
@@ -174,3 +185,23 @@ def test_apply_tuner_searches_the_fft_tilings_one_pass_at_a_time(clock):
     plan2 = FakeTiledPlan()
     res2 = autotune.tune_apply(plan2, FakePsi(512), None)
     assert res2["cached"] and plan2.tiles == [1, 0, 0] and clock["calls"] == 17
+
+
+def test_apply_tuner_tries_stream_counts_with_the_best_and_twice_the_best_chain_batch(clock):
+    plan = FakeStreamPlan()
+    def cost(st):
+        cb, bb, ns = st
+        c = 100.0 + abs(cb - 19) + abs(bb - 16)
+        if ns == 3 and cb == 38:
+            c = 60.0  # three streams with twice the best single-stream batch
+        elif ns > 1:
+            c -= 5.0
+        return c
+    clock["cost"] = cost
+    clock["probe"] = lambda: (plan.chain_batch, plan.band_block, plan.streams)
+    res = autotune.tune_apply(plan, FakePsi(512), None)
+    assert (res["chain_batch"], res["band_block"], res["streams"], res["ms"]) == (38, 16, 3, 60.0)
+    assert (plan.chain_batch, plan.band_block, plan.streams) == (38, 16, 3)
+    assert clock["calls"] == 15 + 3 * 2
+    assert {(r["streams"], r["chain_batch"]) for r in res["table"] if r["streams"] > 1} == \
+        {(ns, cb) for ns in (2, 3, 4) for cb in (19, 38)}

@@ -99,3 +99,22 @@ def test_roofline_arithmetic_matches_the_documented_figures():
     assert abs(hbytes / 1e6 - 4.34) < 0.01
     assert abs(rm["bytes_per_chain"] / 1e6 - 9.65) < 0.01 and rm["bound"] == "hbm"
     assert abs(rm["traffic"] / 1e6 - 15.35 * 38) < 1e-6
+
+
+def test_loop_roofline_counts_all_three_pair_passes():
+    # launches on several streams: the three passes' work over the pair loop's
+    # time (the step minus the phases on the call's stream)
+    b = _bench_module()
+    peaks = {"hbm_gbs": 6688.8}
+    res = {"ms": 1000.0, "phase_ms": {"to_real": 10.0, "to_sphere": 20.0, "energy": 0.0, "pair_fwd": 500.0,
+                                      "pair_col": 600.0, "pair_inv": 700.0},
+           "clocks": {"sm_mhz": 2070.0}, "stats": {"chains": 1000, "phase_launches": {}}}
+    r = b.roofline("fp64", _Plan(), res, 1, peaks, "measured", 8, streams=3)
+    assert r["ms_pair_loop"] == 970.0 and "3 streams" in r["kernel"]
+    n3 = 96.0 ** 3
+    per_chain = 5 * n3 * 2 * 6.584962500721156 * 2 + 2 * 5 * n3 * 6.584962500721156 * 98 / 96
+    assert abs(per_chain / 1e6 - 175.9) < 0.1  # 88.0 MFLOP per pair
+    assert abs(r["achieved"] - per_chain * 1000 / 0.97 / 1e12) < 1e-9
+    rm = b.roofline("mixed32", _Plan(), res, 1, peaks, "measured", 8, streams=2)
+    assert abs(rm["bytes_per_chain"] / 1e6 - 24.44) < 0.05  # 4 x 4.34 MB of kept columns + 16 planes / 8
+    assert abs(rm["achieved"] - rm["bytes_per_chain"] * 1000 / 0.97 / 1e9) < 1e-6

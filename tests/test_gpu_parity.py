@@ -222,3 +222,31 @@ def test_a_grid_with_one_tiling_refuses_the_second():
         plan.set_tiling((1, 0, 0))
     plan.set_tiling((0, 0, 0))
     plan.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(_lib.PREC_FP64, TOL64), (_lib.PREC_MIXED32, TOL32_V),
+                                      (_lib.PREC_DF64, TOL64)], ids=["fp64", "mixed32", "df64"])
+def test_pair_launches_on_several_streams_match_the_oracle(prec, tol):
+    # small launches (5 chains of 36 pairs' 18 chains) rotated over 1-4 streams,
+    # each with its own transform buffer; deterministic accumulation too (FP64
+    # forms): the same bits on every stream count
+    case = setup_case(24, 10.0, 10.0, 8, 1305, prec=prec)
+    plan = case["plan"]
+    plan.set_batch(5)
+    vref, eref, _ = oracle_of(case)
+    for streams in (1, 2, 3, 4):
+        plan.set_streams(streams)
+        vpsi, ex, _ = plan.apply(case["psi"], case["occ"])
+        assert rel_inf(vpsi.cpu().numpy(), vref) <= tol, streams
+        assert abs(ex - eref) <= (TOL64 if prec != _lib.PREC_MIXED32 else TOL32_E) * abs(eref), streams
+    if prec != _lib.PREC_MIXED32:
+        plan.set_deterministic(True)
+        bits = []
+        for streams in (1, 3):
+            plan.set_streams(streams)
+            vpsi, ex, _ = plan.apply(case["psi"], case["occ"])
+            bits.append((vpsi.cpu().numpy().tobytes(), ex))
+        assert bits[0] == bits[1]
+    with pytest.raises(_lib.FockError):
+        plan.set_streams(5)
+    plan.close()
