@@ -919,6 +919,44 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
     // one red.global.add.v4.f32 per target
     static_assert(N % 4 == 0, "vector updates need N divisible by 4");
     const unsigned long long keep = l2_policy_evict_last();  // orbitals and accumulators of the band block
+    // The usual chain of the band-blocked schedule: pairs (i, j) and (i, j')
+    // with i, j, j' distinct and both updates wanted.  Three orbitals, three
+    // targets: W_j -= f_i psi_i phi_a, W_j' -= f_i psi_i phi_b and
+    // W_i -= f_j psi_j phi_a + f_j' psi_j' phi_b, without per-point bookkeeping.
+    const bool shared_i = hb && ch.ai == ch.bi && ch.ai != ch.aj && ch.ai != ch.bj && ch.aj != ch.bj &&
+                          !(ch.flags & (kChainOneSidedA | kChainOneSidedB));
+    if (shared_i) {
+      const float mi = -f[0], mj = -f[1], mj2 = -f[3];
+      const float* pi = ps[0];
+      const float* pj = ps[1];
+      const float* pj2 = ps[3];
+      float* wj = wt[0];
+      float* wj2 = wt[2];
+      float* wi = wt[1];
+      for (int e4 = threadIdx.x; e4 < N * N / 4; e4 += blockDim.x) {
+        const int e = 4 * e4;
+        const int i2 = e / N, i3 = e - i2 * N;
+        const C* q = Q + i2 * NCP + i3;
+        const C z0 = q[0], z1 = q[1], z2 = q[2], z3 = q[3];
+        const float4 vi = ld_f4_hint(pi + e, keep);
+        const float4 vj = ld_f4_hint(pj + e, keep);
+        const float4 vj2 = ld_f4_hint(pj2 + e, keep);
+        const float4 a = make_float4(mi * vi.x * z0.x, mi * vi.y * z1.x, mi * vi.z * z2.x, mi * vi.w * z3.x);
+        const float4 b = make_float4(mi * vi.x * z0.y, mi * vi.y * z1.y, mi * vi.z * z2.y, mi * vi.w * z3.y);
+        const float4 ci = make_float4(mj * vj.x * z0.x + mj2 * vj2.x * z0.y, mj * vj.y * z1.x + mj2 * vj2.y * z1.y,
+                                      mj * vj.z * z2.x + mj2 * vj2.z * z2.y, mj * vj.w * z3.x + mj2 * vj2.w * z3.y);
+        asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(wj + e), "f"(a.x),
+                     "f"(a.y), "f"(a.z), "f"(a.w), "l"(keep)
+                     : "memory");
+        asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(wj2 + e), "f"(b.x),
+                     "f"(b.y), "f"(b.z), "f"(b.w), "l"(keep)
+                     : "memory");
+        asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(wi + e), "f"(ci.x),
+                     "f"(ci.y), "f"(ci.z), "f"(ci.w), "l"(keep)
+                     : "memory");
+      }
+      return;
+    }
     for (int e4 = threadIdx.x; e4 < N * N / 4; e4 += blockDim.x) {
       const int e = 4 * e4;
       const int i2 = e / N, i3 = e - i2 * N;
