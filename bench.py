@@ -172,9 +172,8 @@ def time_form(plan, psi, occ, steps, warmup, want_dex=False, rank=0, world=1):
 # (profiles/pair_passes_*_96.md); scaled to a launch by its chains, reported
 # only for a captured band block (the orbital re-reads depend on it).
 MEASURED_TRAFFIC_PER_CHAIN = {
-    ("fp64", 96, "pair_inv", 8): 57.6e6, ("fp64", 96, "pair_inv", 32): 53.3e6,
-    ("df64", 96, "pair_inv", 8): 57.5e6, ("df64", 96, "pair_inv", 32): 53.3e6,
-    ("mixed32", 96, "pair_inv", 8): 15.35e6, ("mixed32", 96, "pair_inv", 32): 26.3e6,
+    ("fp64", 96, "pair_inv", 8): 54.51e6, ("df64", 96, "pair_inv", 8): 57.47e6,
+    ("mixed32", 96, "pair_inv", 8): 12.61e6,
 }
 
 
@@ -272,13 +271,21 @@ def golden_errors(plan, c, w):
     return err
 
 
+def phase_share(res):
+    """Shares of the three pair passes in their summed device time (rounded)."""
+    ph = {k: res["phase_ms"].get("pair_" + k, 0.0) for k in ("fwd", "col", "inv")}
+    tot = sum(ph.values())
+    return {k: round(v / tot, 3) for k, v in ph.items()} if tot > 0 else None
+
+
 def form_summary(res_line, roof, err):
     """The compact record of one form printed at the end of the JSON line."""
     out = {"workload": res_line["workload"], "value": res_line["value"], "unit": UNIT,
            "ms_per_step": res_line["ms_per_step"], "dtype": res_line["dtype"],
            "frac": roof["frac"], "bound": roof["bound"], "achieved": roof["achieved"],
            "peak": roof["peak"], "roof_unit": roof["unit"], "dominant": roof["kernel"],
-           "traffic": roof["traffic"], "pair_loop_pairs_per_s": res_line["pair_loop_pairs_per_s"]}
+           "traffic": roof["traffic"], "pair_loop_pairs_per_s": res_line["pair_loop_pairs_per_s"],
+           "pass_share": res_line.get("pass_share")}
     if err:
         out.update({k: err[k] for k in ("max_abs_dVpsi_rel", "rel_dEx", "rel_ddEx_domega")})
     return out
@@ -322,9 +329,12 @@ def loop_roofline(form, plan, res, steps, peaks, peak_src, band_block, streams):
 
 
 # DRAM bytes (read + write) per chain of the three pair kernels together, from
-# ncu captures of the 96^3 pair passes (profiles/pair_passes_*_96.md), by form
-# and band block; scaled to a step by its chains
-MEASURED_LOOP_TRAFFIC_PER_CHAIN = {}
+# ncu captures of the 96^3 pair passes on one stream at 38 chains per launch
+# (profiles/pair_passes_*_96.md), by form and band block; scaled to a step by
+# its chains
+MEASURED_LOOP_TRAFFIC_PER_CHAIN = {
+    ("fp64", 96, 8): 96.47e6, ("df64", 96, 8): 98.72e6, ("mixed32", 96, 8): 29.03e6,
+}
 
 
 def fixed_blocks(plan, args):
@@ -788,7 +798,7 @@ def main():
                  "ms_per_step": resm["ms"] / args.steps, "dtype": "f32",
                  "roofline": roofline("mixed32", planm, resm, args.steps, peaks, peak_src,
                                       tunedm["band_block"] if tunedm else 16, tunedm.get("streams", 1) if tunedm else 1),
-                 "pair_loop_pairs_per_s": pair_loop_rate(pm, resm, args.steps),
+                 "pair_loop_pairs_per_s": pair_loop_rate(pm, resm, args.steps), "pass_share": phase_share(resm),
                  "gpu_launches": resm["launches"], "clocks": resm["clocks"], "tuned": tunedm}
         mixed["summary"] = form_summary(mixed, mixed["roofline"], golden_errors(planm, cm, wm) if world == 1 else None)
         planm.close()
@@ -815,7 +825,7 @@ def main():
               "ms_per_step": resd["ms"] / args.steps, "dtype": "f32x2 (double-float)",
               "roofline": roofline("df64", pland, resd, args.steps, peaks, peak_src,
                                    tunedd["band_block"] if tunedd else 16, tunedd.get("streams", 1) if tunedd else 1),
-              "pair_loop_pairs_per_s": pair_loop_rate(pd, resd, args.steps),
+              "pair_loop_pairs_per_s": pair_loop_rate(pd, resd, args.steps), "pass_share": phase_share(resd),
               "gpu_launches": resd["launches"], "clocks": resd["clocks"], "tuned": tunedd}
         df["summary"] = form_summary(df, df["roofline"], golden_errors(pland, cd, wd) if world == 1 else None)
         pland.close()
@@ -869,6 +879,7 @@ def main():
         "clocks": res["clocks"],
         "errors": err,
         "pair_loop_pairs_per_s": pair_loop_rate(pairs, res, args.steps),
+        "pass_share": phase_share(res),
         "tuned": brief_tuned(tuned),
         "batched": batched,
         "kpoints": kpoints,
