@@ -260,7 +260,7 @@ def golden_errors(plan, c, w):
     rec_mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(rec_mod)
     case = rec_mod.CASE_OF_SEED.get(w["seed"])
-    if case is None or plan.grid[0] != 96 or w["nb"] < rec_mod.NB or not os.path.exists(rec_mod.FILE):
+    if case is None or plan.grid[0] != 96 or w["nb"] != rec_mod.NB_ALL or not os.path.exists(rec_mod.FILE):
         return None
     rec = rec_mod.load()
     sub = torch.from_numpy(np.ascontiguousarray(c[:rec_mod.NB])).cuda()
@@ -389,7 +389,7 @@ def run_batched(args, peaks, peak_src):
         psis.append(torch.from_numpy(c).cuda())
         occs.append(occ)
     pairs = sum(sy["nb"] * (sy["nb"] + 1) // 2 for sy in systems)
-    tuned = {"options": {}, "band_block": 16}
+    tuned = {"options": {"persistent": args.batch_mode}, "band_block": 16}
     if not args.no_tune:
         tuned = tune_batch(plans, psis, occs, slot_chains=(4, 8, 16), rings=(3,), ctas_per_sm=(0,),
                            persistent=(1, 2, 0), reps=1, use_cache=False)
@@ -714,6 +714,9 @@ def main():
                     help="with --no-tune: streams the pair-pass launches rotate over (1-4)")
     ap.add_argument("--tiles", default="",
                     help="with --no-tune: FFT tiling of the forward, column and inverse passes, e.g. 100")
+    ap.add_argument("--batch-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="with --no-tune: pair passes of the batch as graph branches (0), one persistent "
+                         "launch (1) or one dataflow launch (2)")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison line")
     ap.add_argument("--cufft-bands", type=int, default=128)
     ap.add_argument("--tune-bands", type=int, default=64,
@@ -886,7 +889,7 @@ def main():
         "autograd": autograd,
         "cufft_comparison": cufft,
         # the two other forms of the metric last, compact
-        "df64_summary": df["summary"] if df else None,
+        "df64_summary": dict(df["summary"], tuned=brief_tuned(df["tuned"])) if df else None,
         "mixed32_summary": dict(mixed["summary"], tuned=brief_tuned(mixed["tuned"])) if mixed else None,
     }
     print(json.dumps(line), flush=True)

@@ -159,8 +159,9 @@ class FockPlan:
 
 
 class FockBatch:
-    """Many systems in one batched apply (one persistent pair launch, replayed
-    as a CUDA graph).  ``plans``: distinct :class:`FockPlan` objects of one
+    """Many systems in one batched apply, replayed as one CUDA graph; the pair
+    passes run as one graph branch per system, one persistent launch or one
+    dataflow launch (option ``persistent`` = 0, 1, 2).  ``plans``: distinct :class:`FockPlan` objects of one
     precision; ``psi``: device complex128 tensors [nb_s, npw_s]; ``occ``: host
     occupations.  Output tensors are allocated here and kept: every
     :meth:`run` overwrites ``self.vpsi``.  Options as in ``fock_batch_options``.

@@ -8,6 +8,9 @@ import os
 
 FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_fullsize_N96_nb64.txt")
 NB = 64
+# the set the 64 bands come from: the seeded 512-band set, orthonormalised as a
+# whole (a 64-band set drawn with the same seed is a different set)
+NB_ALL = 512
 # the cases of the file: (workload seed, kernel) -> case name
 CASE_OF_SEED = {1306: "spencer_alavi_seed1306", 1307: "erfc_seed1307"}
 

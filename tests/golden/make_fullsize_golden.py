@@ -35,8 +35,8 @@ _spec = importlib.util.spec_from_file_location("synth", os.path.join(ROOT, "pape
 synth = importlib.util.module_from_spec(_spec)
 _spec.loader.exec_module(synth)
 
-from tests.golden.fullsize_record import FILE  # noqa: E402  (the reader of the same file)
-N, L, ECUT, NB_ALL, NB = 96, 27.0, 12.0, 512, 64
+from tests.golden.fullsize_record import FILE, NB, NB_ALL  # noqa: E402  (the reader of the same file)
+N, L, ECUT = 96, 27.0, 12.0
 # (name, kernel, omega, seed): the seeds of the 96^3 workloads
 CASES = (("spencer_alavi_seed1306", "spencer_alavi", None, 1306), ("erfc_seed1307", "erfc", 0.106, 1307))
 BANDS = (0, 31, 63)           # bands whose V_x psi is sampled

@@ -118,3 +118,17 @@ def test_loop_roofline_counts_all_three_pair_passes():
     rm = b.roofline("mixed32", _Plan(), res, 1, peaks, "measured", 8, streams=2)
     assert abs(rm["bytes_per_chain"] / 1e6 - 24.44) < 0.05  # 4 x 4.34 MB of kept columns + 16 planes / 8
     assert abs(rm["achieved"] - rm["bytes_per_chain"] * 1000 / 0.97 / 1e9) < 1e-6
+
+
+def test_golden_errors_only_for_the_full_band_set():
+    # the stored oracle values are for the first 64 bands of the seeded
+    # 512-band set; a run over another band count builds a different set
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Plan:
+        grid = (96, 96, 96)
+
+    for nb in (64, 128, 511):
+        w = dict(bench.workload("gamma_fp64_L27_N96_nb512"), nb=nb)
+        assert bench.golden_errors(Plan(), None, w) is None
