@@ -168,12 +168,16 @@ def time_form(plan, psi, occ, steps, warmup, want_dex=False, rank=0, world=1):
 
 
 # DRAM bytes (read + write) per chain of the dominant kernel, from ncu captures
-# of the 96^3 pair passes at 38 chains per launch and band blocks 8 and 32
-# (profiles/pair_passes_*_96.md); scaled to a launch by its chains, reported
-# only for a captured band block (the orbital re-reads depend on it).
+# of the 96^3 pair passes of the 64-band case at 38 chains per launch, one
+# stream (profiles/pair_passes_*_96.md, profiles/pair_traffic_96.md); scaled
+# to a launch by its chains, reported only for a captured band block (the
+# orbital re-reads depend on it).
 MEASURED_TRAFFIC_PER_CHAIN = {
     ("fp64", 96, "pair_inv", 8): 54.51e6, ("df64", 96, "pair_inv", 8): 57.47e6,
     ("mixed32", 96, "pair_inv", 8): 12.61e6,
+    ("fp64", 96, "pair_inv", 16): 47.05e6, ("fp64", 96, "pair_inv", 32): 52.55e6,
+    ("df64", 96, "pair_inv", 16): 50.71e6, ("df64", 96, "pair_inv", 32): 53.24e6,
+    ("mixed32", 96, "pair_inv", 16): 19.27e6,
 }
 
 
@@ -334,6 +338,8 @@ def loop_roofline(form, plan, res, steps, peaks, peak_src, band_block, streams):
 # its chains
 MEASURED_LOOP_TRAFFIC_PER_CHAIN = {
     ("fp64", 96, 8): 96.47e6, ("df64", 96, 8): 98.72e6, ("mixed32", 96, 8): 29.03e6,
+    ("fp64", 96, 16): 86.74e6, ("fp64", 96, 32): 94.16e6,
+    ("df64", 96, 16): 90.18e6, ("df64", 96, 32): 94.48e6, ("mixed32", 96, 16): 37.53e6,
 }
 
 
@@ -427,12 +433,13 @@ def run_batched(args, peaks, peak_src):
     batch.close()
     for p in plans:
         p.close()
+    mode = int(tuned["options"].get("persistent", 1))
     traffic = None
-    if args.nb is None:  # DRAM bytes per chain of the pair passes (ncu, 64-band systems), scaled by chains
+    if args.nb is None and bb == BATCH_DRAM_BAND_BLOCK and mode == 0:
+        # DRAM bytes per chain of the pair passes (ncu, 64-band systems), scaled by chains
         traffic = sum(((sy["nb"] * (sy["nb"] + 1) // 2 + 1) // 2) * BATCH_DRAM_PER_CHAIN.get(sy["N"], float("nan"))
                       for sy in systems)
         traffic = None if traffic != traffic else traffic
-    mode = int(tuned["options"].get("persistent", 1))
     nbytes_kernel = {0: "pair passes (graph branches)", 1: "k_pair_persistent", 2: "k_pair_dataflow"}[mode]
     persistent = mode != 0
     return {"workload": "batched16_mixed32_sa_N48-96_L13.5-27",
@@ -452,9 +459,11 @@ def run_batched(args, peaks, peak_src):
 
 
 # DRAM bytes (read + write) per chain of the three pair passes of the batch's
-# systems, by grid size (filled from an ncu capture of the pair kernels of the
-# 64-band version of the batch); empty: not captured for these kernels
-BATCH_DRAM_PER_CHAIN = {}
+# systems, by grid size, at band block 16: an ncu capture of every pair launch
+# of the 64-band version of the batch as graph branches (launches serialised
+# by ncu; profiles/pair_traffic_96.md)
+BATCH_DRAM_PER_CHAIN = {48: 3.067e6, 64: 7.338e6, 72: 10.748e6, 96: 42.128e6}
+BATCH_DRAM_BAND_BLOCK = 16
 
 
 def best_by_mode(table):
