@@ -424,10 +424,19 @@ __device__ __forceinline__ void pair_fwd_task(const DevPlan& g, const T* __restr
   const T* qaj = paj + c3;
   const T* qbi = pbi + c3;
   const T* qbj = pbj + c3;
-  const auto product = [&](int, int i2) {
-    return cmake<T>(qai[i2 * N] * qaj[i2 * N], hb ? qbi[i2 * N] * qbj[i2 * N] : T(0));
-  };
-  fft_lines_from<T, N, -1, N, G::TLP, 1, RP, MAXT, EMAX>(P, tw, product);  // along i2
+  if (hb && ch.ai == ch.bi) {
+    // the usual chain, pairs (i, j) and (i, j'): psi_i is read once
+    const auto product = [&](int, int i2) {
+      const T x = qai[i2 * N];
+      return cmake<T>(x * qaj[i2 * N], x * qbj[i2 * N]);
+    };
+    fft_lines_from<T, N, -1, N, G::TLP, 1, RP, MAXT, EMAX>(P, tw, product);  // along i2
+  } else {
+    const auto product = [&](int, int i2) {
+      return cmake<T>(qai[i2 * N] * qaj[i2 * N], hb ? qbi[i2 * N] * qbj[i2 * N] : T(0));
+    };
+    fft_lines_from<T, N, -1, N, G::TLP, 1, RP, MAXT, EMAX>(P, tw, product);  // along i2
+  }
   // along i3: only the rows k2 that hold kept columns, [0, row_lo) and
   // [N - row_hi, N) (the split below reads row k2 and its mirror N - k2, both in)
   const int rlo = g.row_lo, nrows = g.row_lo + g.row_hi;
@@ -698,7 +707,28 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
         const T* vp = vl + k10 * N * KH;
         const T* dvp = dvl + k10 * N * KH;
         C* sp = S + k10 * NC + l;
-        for (int k1 = k10; k1 < N; k1 += kstep, vp += kstep * N * KH, dvp += kstep * N * KH, sp += kstep * NC) {
+        const int vstep = kstep * N * KH, sstep = kstep * NC;
+        // batches of U elements: the U table loads are in flight together
+        constexpr int U = 8;
+        int k1 = k10;
+        for (; k1 + (U - 1) * kstep < N; k1 += U * kstep, vp += U * vstep, dvp += U * vstep, sp += U * sstep) {
+          T v[U], dv[U];
+          C z[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            v[u] = vp[u * vstep];
+            dv[u] = want_d ? dvp[u * vstep] : T(0);
+            z[u] = sp[u * sstep];
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const T a2 = z[u].x * z[u].x + z[u].y * z[u].y;
+            e_sum += v[u] * a2;
+            d_sum += dv[u] * a2;
+            sp[u * sstep] = cmake<T>(z[u].x * v[u], z[u].y * v[u]);
+          }
+        }
+        for (; k1 < N; k1 += kstep, vp += vstep, dvp += vstep, sp += sstep) {
           C z = *sp;
           const T a2 = z.x * z.x + z.y * z.y;
           const T v = *vp;
