@@ -452,8 +452,17 @@ template <int SIGN, class T> struct Dft {
   }
 };
 
+// Position of output element k of a line in shared memory: OMAP 0 natural
+// order; OMAP 1 "quad phases": the line is stored as four runs of N/4, run
+// k mod 4 holding elements k mod 4, k mod 4 + 4, ... (so that element 4c + u
+// sits at u N/4 + c).  Only the last stage of a transform applies a map.
+template <int N, int OMAP> FFT_HD constexpr int out_pos(int k) {
+  if constexpr (OMAP == 1) return (k & 3) * (N / 4) + (k >> 2);
+  else return k;
+}
+
 // One Stockham stage on one line (base, element stride ES) for sub-thread t of TL.
-template <class T, int N, int R, int P, int TL, int ES, int SIGN>
+template <class T, int N, int R, int P, int TL, int ES, int SIGN, int OMAP = 0>
 __device__ __forceinline__ void fft_stage(cplx<T>* base, int t, bool active, const cplx<T>* tw) {
   using C = cplx<T>;
   constexpr int NB = N / R;
@@ -490,7 +499,7 @@ __device__ __forceinline__ void fft_stage(cplx<T>* base, int t, bool active, con
       }
       const int j = (b - kk) * R + kk;
 #pragma unroll
-      for (int q = 0; q < R; ++q) base[(j + q * P) * ES] = x[k][q];
+      for (int q = 0; q < R; ++q) base[out_pos<N, OMAP>(j + q * P) * ES] = x[k][q];
     }
   }
   __syncthreads();
@@ -525,13 +534,13 @@ __device__ __forceinline__ void fft_stage_first(cplx<T>* base, int t, bool activ
   __syncthreads();
 }
 
-template <class T, int N, int SIGN, int TL, int ES, int S, int P, int MAXT, int EMAX = 0>
+template <class T, int N, int SIGN, int TL, int ES, int S, int P, int MAXT, int EMAX = 0, int OMAP = 0>
 __device__ __forceinline__ void fft_stages(cplx<T>* base, int t, bool active, const cplx<T>* tw) {
   constexpr RadixPlan pl = make_radix_plan(N, MAXT, plan_emax<T, EMAX>());
   if constexpr (S < pl.nst) {
     constexpr int R = pl.r[S];
-    fft_stage<T, N, R, P, TL, ES, SIGN>(base, t, active, tw);
-    fft_stages<T, N, SIGN, TL, ES, S + 1, P * R, MAXT, EMAX>(base, t, active, tw);
+    fft_stage<T, N, R, P, TL, ES, SIGN, (S + 1 == pl.nst) ? OMAP : 0>(base, t, active, tw);
+    fft_stages<T, N, SIGN, TL, ES, S + 1, P * R, MAXT, EMAX, OMAP>(base, t, active, tw);
   }
 }
 
@@ -584,13 +593,15 @@ __device__ __forceinline__ void fft_lines_rt(cplx<T>* buf, const cplx<T>* tw, in
 // synchronises); threads with tid >= NLINES*TL idle.
 // MAXT and EMAX name the radix plan (make_radix_plan(N, MAXT, plan_emax<T,
 // EMAX>())) that TL was chosen for.
-template <class T, int N, int SIGN, int NLINES, int TL, int LS, int ES, int MAXT = kMaxThreads, int EMAX = 0>
+// OMAP: the order the last stage leaves the elements of a line in (out_pos).
+template <class T, int N, int SIGN, int NLINES, int TL, int LS, int ES, int MAXT = kMaxThreads, int EMAX = 0,
+          int OMAP = 0>
 __device__ __forceinline__ void fft_lines(cplx<T>* buf, const cplx<T>* tw) {
   const int tid = threadIdx.x;
   const int line = tid % NLINES;
   const int t = tid / NLINES;
   const bool active = t < TL;
-  fft_stages<T, N, SIGN, TL, ES, 0, 1, MAXT, EMAX>(buf + line * LS, t, active, tw);
+  fft_stages<T, N, SIGN, TL, ES, 0, 1, MAXT, EMAX, OMAP>(buf + line * LS, t, active, tw);
 }
 
 }  // namespace fockx

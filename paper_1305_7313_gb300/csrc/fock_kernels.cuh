@@ -918,8 +918,12 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
     }
   }
   __syncthreads();
-  // 4. inverse transform along k3 of the N rows: Q[i2][i3] = phi_a + i phi_b
-  fft_lines<T, N, +1, N, G::TLP, NCP, 1, MAXT, EMAX>(Q, tw);
+  // 4. inverse transform along k3 of the N rows: Q[i2][i3] = phi_a + i phi_b,
+  //    in FP32 with each row left in quad phases (element 4c + u of row i2 at
+  //    i2 NCP + u N/4 + c): the four-point groups of the accumulator update
+  //    are then read with consecutive lanes on consecutive addresses
+  constexpr int OMAP = (RealTraits<T>::prec == 1 && N % 4 == 0) ? 1 : 0;
+  fft_lines<T, N, +1, N, G::TLP, NCP, 1, MAXT, EMAX, OMAP>(Q, tw);
   const int64_t plane0 = (int64_t)i1 * N * N;
   const bool hb = ch.bi >= 0;
   // Up to four updates k, W[tgt_k] -= f[src_k] psi[src_k] phi:
@@ -965,9 +969,9 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
       float* wi = wt[1];
       for (int e4 = threadIdx.x; e4 < N * N / 4; e4 += blockDim.x) {
         const int e = 4 * e4;
-        const int i2 = e / N, i3 = e - i2 * N;
-        const C* q = Q + i2 * NCP + i3;
-        const C z0 = q[0], z1 = q[1], z2 = q[2], z3 = q[3];
+        const int i2 = e4 / (N / 4), c = e4 - i2 * (N / 4);
+        const C* q = Q + i2 * NCP + c;  // quad phases: element 4c + u at u N/4 + c
+        const C z0 = q[0], z1 = q[N / 4], z2 = q[2 * (N / 4)], z3 = q[3 * (N / 4)];
         const float4 vi = ld_f4_hint(pi + e, keep);
         const float4 vj = ld_f4_hint(pj + e, keep);
         const float4 vj2 = ld_f4_hint(pj2 + e, keep);
@@ -989,11 +993,11 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
     }
     for (int e4 = threadIdx.x; e4 < N * N / 4; e4 += blockDim.x) {
       const int e = 4 * e4;
-      const int i2 = e / N, i3 = e - i2 * N;
+      const int i2 = e4 / (N / 4), cq = e4 - i2 * (N / 4);
       float4 phia, phib;
       {
-        const C* q = Q + i2 * NCP + i3;
-        const C z0 = q[0], z1 = q[1], z2 = q[2], z3 = q[3];
+        const C* q = Q + i2 * NCP + cq;  // quad phases
+        const C z0 = q[0], z1 = q[N / 4], z2 = q[2 * (N / 4)], z3 = q[3 * (N / 4)];
         phia = make_float4(z0.x, z1.x, z2.x, z3.x);
         phib = make_float4(z0.y, z1.y, z2.y, z3.y);
       }
