@@ -169,15 +169,13 @@ def time_form(plan, psi, occ, steps, warmup, want_dex=False, rank=0, world=1):
 
 # DRAM bytes (read + write) per chain of the dominant kernel, from ncu captures
 # of the 96^3 pair passes of the 64-band case at 38 chains per launch, one
-# stream (profiles/pair_passes_*_96.md, profiles/pair_traffic_96.md); scaled
+# stream (profiles/pair_traffic_96.md); scaled
 # to a launch by its chains, reported only for a captured band block (the
 # orbital re-reads depend on it).
 MEASURED_TRAFFIC_PER_CHAIN = {
-    ("fp64", 96, "pair_inv", 8): 54.51e6, ("df64", 96, "pair_inv", 8): 57.47e6,
-    ("mixed32", 96, "pair_inv", 8): 12.61e6,
-    ("fp64", 96, "pair_inv", 16): 47.05e6, ("fp64", 96, "pair_inv", 32): 52.55e6,
-    ("df64", 96, "pair_inv", 16): 50.71e6, ("df64", 96, "pair_inv", 32): 53.24e6,
-    ("mixed32", 96, "pair_inv", 16): 19.27e6,
+    ("fp64", 96, "pair_inv", 8): 54.15e6, ("fp64", 96, "pair_inv", 16): 47.07e6, ("fp64", 96, "pair_inv", 32): 52.56e6,
+    ("df64", 96, "pair_inv", 8): 57.45e6, ("df64", 96, "pair_inv", 16): 50.67e6, ("df64", 96, "pair_inv", 32): 53.20e6,
+    ("mixed32", 96, "pair_inv", 8): 12.61e6, ("mixed32", 96, "pair_inv", 16): 19.27e6,
 }
 
 
@@ -334,12 +332,12 @@ def loop_roofline(form, plan, res, steps, peaks, peak_src, band_block, streams):
 
 # DRAM bytes (read + write) per chain of the three pair kernels together, from
 # ncu captures of the 96^3 pair passes on one stream at 38 chains per launch
-# (profiles/pair_passes_*_96.md), by form and band block; scaled to a step by
+# (profiles/pair_traffic_96.md), by form and band block; scaled to a step by
 # its chains
 MEASURED_LOOP_TRAFFIC_PER_CHAIN = {
-    ("fp64", 96, 8): 96.47e6, ("df64", 96, 8): 98.72e6, ("mixed32", 96, 8): 29.03e6,
-    ("fp64", 96, 16): 86.74e6, ("fp64", 96, 32): 94.16e6,
-    ("df64", 96, 16): 90.18e6, ("df64", 96, 32): 94.48e6, ("mixed32", 96, 16): 37.53e6,
+    ("fp64", 96, 8): 96.09e6, ("fp64", 96, 16): 86.96e6, ("fp64", 96, 32): 94.28e6,
+    ("df64", 96, 8): 98.46e6, ("df64", 96, 16): 90.22e6, ("df64", 96, 32): 94.56e6,
+    ("mixed32", 96, 8): 28.91e6, ("mixed32", 96, 16): 37.52e6,
 }
 
 
@@ -462,7 +460,7 @@ def run_batched(args, peaks, peak_src):
 # systems, by grid size, at band block 16: an ncu capture of every pair launch
 # of the 64-band version of the batch as graph branches (launches serialised
 # by ncu; profiles/pair_traffic_96.md)
-BATCH_DRAM_PER_CHAIN = {48: 3.067e6, 64: 7.338e6, 72: 10.748e6, 96: 42.128e6}
+BATCH_DRAM_PER_CHAIN = {48: 3.068e6, 64: 7.342e6, 72: 10.752e6, 96: 42.145e6}
 BATCH_DRAM_BAND_BLOCK = 16
 
 
@@ -516,6 +514,88 @@ def run_kpoints(args, peaks, peak_src):
                          "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
                          "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
                          "peak_src": peak_src + " (hbm copy)"}}
+
+
+def run_fixed(args):
+    """The exchange operator fixed by an occupied set and applied to trial
+    orbitals, as in an SCF inner loop: 96^3, L = 27 bohr, Ecut = 12 Ha, erfc
+    kernel (omega 0.106), mixed form; 256 occupied and 256 trial orbitals,
+    V_x fixed once outside the timed region, each step one apply to the trial
+    set (256 x 256 pairs)."""
+    import torch
+    from paper_1305_7313_gb300 import FockPlan, synth
+    w = workload("gamma_mixed32_erfc_L27_N96_nb512")
+    nocc = ntrial = 256
+    if args.nb:
+        nocc = ntrial = min(nocc, args.nb)
+    from paper_1305_7313_gb300.workloads import cubic_cell
+    cell = cubic_cell(w["L"])
+    plan = FockPlan(w["N"], cell, w["ecut"], w["kernel"], w["omega"], w["prec"])
+    psi = torch.from_numpy(synth.orbitals(plan.miller, cell, nocc, w["seed"])).cuda()
+    phi = torch.from_numpy(synth.orbitals(plan.miller, cell, ntrial, w["seed"] + 1000)).cuda()
+    plan.set_occupied(psi, np.full(nocc, 2.0))
+    out = torch.empty_like(phi)
+    for _ in range(args.warmup):
+        plan.apply_fixed(phi, out)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record()
+    for _ in range(args.steps):
+        plan.apply_fixed(phi, out)
+    end.record()
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    plan.close()
+    pairs = nocc * ntrial
+    return {"workload": "fixed_mixed32_erfc_L27_N96_nocc256_ntrial256", "value": pairs * args.steps / (ms * 1e-3),
+            "unit": UNIT, "ms_per_step": ms / args.steps, "pairs": pairs, "dtype": "f32"}
+
+
+def run_sternheimer(args):
+    """Sternheimer linear response by CG with band regrouping (FP64): 48^3
+    grid, L = 13.5 bohr, Ecut = 12 Ha, H = kinetic + a model local potential
+    (three Gaussian wells), 32 occupied kets and 32 right-hand kets (seeded
+    orthonormal sets, the right-hand ones scaled by 1, 1e-2, 1e-4, 1e-6 in
+    turn), eps_n below the spectrum of H (every system positive definite),
+    alpha = 1, residual threshold 1e-8.  Each step is one solve
+    (the per-iteration readback of the residual norms included)."""
+    import torch
+    from paper_1305_7313_gb300 import FockPlan, PREC_FP64, synth
+    from paper_1305_7313_gb300.workloads import SPENCER_ALAVI, cubic_cell
+    n, L, ecut, nocc, nrhs = 48, 13.5, 12.0, 32, 32
+    if args.nb:
+        nocc, nrhs = min(nocc, args.nb), min(nrhs, args.nb)
+    cell = cubic_cell(L)
+    plan = FockPlan(n, cell, ecut, SPENCER_ALAVI, None, PREC_FP64)
+    v = synth.model_potential((n, n, n), cell, 11)
+    u = torch.from_numpy(synth.orbitals(plan.miller, cell, nocc, 2400)).cuda()
+    # right-hand kets of norms 1, 1e-2, 1e-4, 1e-6 in turn: the bands converge
+    # after different numbers of updates, so the regrouping shrinks the set
+    scale = 10.0 ** (-2 * (np.arange(nrhs) % 4))
+    wk = torch.from_numpy(synth.orbitals(plan.miller, cell, nrhs, 2401) * scale[:, None]).cuda()
+    vd = torch.from_numpy(np.ascontiguousarray(v)).cuda()
+    eps = v.min() - 1.0 - 0.01 * np.arange(nrhs)
+    tol = 1e-8
+    for _ in range(max(1, args.warmup)):
+        plan.sternheimer(vd, u, eps, wk, 1.0, tol)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    updates = 0
+    start.record()
+    for _ in range(args.steps):
+        _, iters, res = plan.sternheimer(vd, u, eps, wk, 1.0, tol)
+        updates += int(np.sum(iters))
+    end.record()
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    plan.close()
+    return {"workload": "sternheimer_fp64_N48_L13.5_nocc32_nrhs32", "value": updates / (ms * 1e-3),
+            "unit": "band CG updates/s", "ms_per_step": ms / args.steps, "npw": int(plan.npw),
+            "iterations_max": int(np.max(iters)), "iterations_min": int(np.min(iters)),
+            "iterations_mean": float(np.mean(iters)),
+            "residual_max": float(np.max(res)), "dtype": "f64"}
 
 
 def run_cufft_comparison(args, w, nbands=128, chunk=32):
@@ -714,6 +794,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-kpoints", action="store_true")
     ap.add_argument("--no-autograd", action="store_true", help="skip the E_x(psi, omega) autograd leg")
+    ap.add_argument("--no-fixed", action="store_true", help="skip the fixed-operator (trial orbitals) leg")
+    ap.add_argument("--no-sternheimer", action="store_true", help="skip the Sternheimer CG leg")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--chain-batch", type=int, default=0,
                     help="with --no-tune: chains per pair-pass launch of the Gamma-point forms")
@@ -859,6 +941,16 @@ def main():
         autograd = run_autograd(args)
         torch.cuda.empty_cache()
 
+    fixed = None
+    if not args.no_fixed and world == 1:
+        fixed = run_fixed(args)
+        torch.cuda.empty_cache()
+
+    stern = None
+    if not args.no_sternheimer and world == 1:
+        stern = run_sternheimer(args)
+        torch.cuda.empty_cache()
+
     cufft = None
     if not args.no_cufft and world == 1:
         cufft = run_cufft_comparison(args, w, args.cufft_bands)
@@ -896,6 +988,8 @@ def main():
         "batched": batched,
         "kpoints": kpoints,
         "autograd": autograd,
+        "fixed_operator": fixed,
+        "sternheimer": stern,
         "cufft_comparison": cufft,
         # the two other forms of the metric last, compact
         "df64_summary": dict(df["summary"], tuned=brief_tuned(df["tuned"])) if df else None,

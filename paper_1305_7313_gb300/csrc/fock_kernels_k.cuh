@@ -148,28 +148,7 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_COLF, Geo<T, N>::MIN_CTAS)
   } else {
     const T* vt = static_cast<const T*>(g.vtabq) + qoff;  // v / Ntot
     float accf[4] = {0.f, 0.f, 0.f, 0.f};
-    // batches of U elements: the table loads of a batch are in flight together
-    constexpr int U = 8;
-    const int step = blockDim.x;
-    int e = threadIdx.x;
-    for (; e + (U - 1) * step < N * N; e += U * step) {
-      T v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int eu = e + u * step;
-        const int k1 = eu / N, k3 = eu - k1 * N;
-        v[u] = vt[((int64_t)k1 * N + k2) * N + k3];
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        C z = S[e + u * step];
-        accf[0] += v[u] * (z.x * z.x + z.y * z.y);
-        z.x *= v[u];
-        z.y *= v[u];
-        S[e + u * step] = z;
-      }
-    }
-    for (; e < N * N; e += step) {
+    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
       const int k1 = e / N, k3 = e - k1 * N;
       const T v = vt[((int64_t)k1 * N + k2) * N + k3];
       C z = S[e];

@@ -86,3 +86,21 @@ def orbitals_k(miller, cell, kfrac, nbands, seed):
     w, u = np.linalg.eigh(s)
     x = (u * (1.0 / np.sqrt(w))[None, :]) @ np.conj(u).T
     return np.ascontiguousarray(x.T @ c)
+
+
+def model_potential(grid, cell, seed=7, depth=1.5, width=0.9, centers=3):
+    """A real local potential V(r) on the FFT grid, float64 [N1, N2, N3]: a few
+    Gaussian wells -depth exp(-|r - R|^2 / (2 width^2)) at seeded fractional
+    positions R (nearest periodic image), with no symmetry that would make the
+    states of H = -1/2 nabla^2 + V degenerate."""
+    rng = np.random.default_rng(seed)
+    a = np.asarray(cell, dtype=np.float64).reshape(3, 3)
+    idx = np.stack(np.meshgrid(*[np.arange(n) / n for n in grid], indexing="ij"), axis=-1)
+    v = np.zeros(tuple(int(n) for n in grid))
+    for _ in range(centers):
+        f = rng.random(3)
+        d = idx - f
+        d -= np.round(d)
+        r = d @ a
+        v -= depth * np.exp(-np.einsum("...x,...x->...", r, r) / (2 * width ** 2))
+    return v

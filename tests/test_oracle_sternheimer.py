@@ -18,20 +18,8 @@ def _cell():
 
 
 def model_potential(grid, cell, seed=7, depth=1.5, width=0.9, centers=3):
-    """A real local potential on the grid: a few Gaussian wells at seeded
-    positions (periodic images summed), no symmetry that would make states
-    degenerate."""
-    rng = np.random.default_rng(seed)
-    a = np.asarray(cell).reshape(3, 3)
-    idx = np.stack(np.meshgrid(*[np.arange(n) / n for n in grid], indexing="ij"), axis=-1)
-    v = np.zeros(grid)
-    for _ in range(centers):
-        f = rng.random(3)
-        d = idx - f
-        d -= np.round(d)
-        r = d @ a
-        v -= depth * np.exp(-np.einsum("...x,...x->...", r, r) / (2 * width ** 2))
-    return v
+    """The seeded model potential of the input generator (Gaussian wells)."""
+    return synth.model_potential(grid, cell, seed, depth, width, centers)
 
 
 def occupied_states(h, mill, nocc):
