@@ -152,6 +152,118 @@ cudaError_t launch_det_pair_sums(const double* part, int npairs, int ncta, doubl
   return cudaGetLastError();
 }
 
+namespace {
+
+// Overlap tiles: 64 x 64 entries of S per CTA (16 x 16 threads, each 4 x 4
+// entries 16 apart), the sum over the real views of the rows (2 npw doubles)
+// split into chunks over gridDim.y and reduced with FP64 atomics.
+constexpr int kOvTile = 64, kOvK = 16, kOvThreads = 256;
+
+__global__ void __launch_bounds__(kOvThreads)
+    k_overlap(const double* __restrict__ A, int na, const double* __restrict__ B, int nbb, int64_t K, int sym,
+              int tiles_j, int64_t kchunk, double* __restrict__ S, int ld) {
+  int ti, tj;
+  if (sym) {  // blockIdx.x enumerates the tiles ti <= tj row by row
+    int rem = blockIdx.x;
+    ti = 0;
+    while (rem >= tiles_j - ti) {
+      rem -= tiles_j - ti;
+      ++ti;
+    }
+    tj = ti + rem;
+  } else {
+    ti = blockIdx.x / tiles_j;
+    tj = blockIdx.x - ti * tiles_j;
+  }
+  const int i0 = ti * kOvTile, j0 = tj * kOvTile;
+  const int64_t k0 = (int64_t)blockIdx.y * kchunk;
+  const int64_t k1 = k0 + kchunk < K ? k0 + kchunk : K;
+  __shared__ double As[kOvK][kOvTile + 1], Bs[kOvK][kOvTile + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+  for (int64_t kb = k0; kb < k1; kb += kOvK) {
+    for (int e = threadIdx.x; e < kOvTile * kOvK; e += kOvThreads) {
+      const int r = e / kOvK, kk = e - r * kOvK;
+      const int64_t k = kb + kk;
+      As[kk][r] = (i0 + r < na && k < k1) ? A[(int64_t)(i0 + r) * K + k] : 0.0;
+      Bs[kk][r] = (j0 + r < nbb && k < k1) ? B[(int64_t)(j0 + r) * K + k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kOvK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[kk][ty + 16 * u];
+        b[u] = Bs[kk][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+      if (i < na && j < nbb && (!sym || j >= i)) atomicAdd(&S[(int64_t)i * ld + j], acc[u][v]);
+    }
+}
+
+__global__ void k_overlap_zero(double* S, int na, int nbb, int sym, int ld) {
+  const int64_t total = (int64_t)na * nbb;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / nbb), j = (int)(e - (int64_t)i * nbb);
+    if (!sym || j >= i) S[(int64_t)i * ld + j] = 0.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_overlap(const double2* a, int na, const double2* b, int nbb, int npw, bool sym, double* S,
+                           int ld, cudaStream_t s) {
+  if (na < 1 || nbb < 1) return cudaSuccess;
+  const int64_t K = 2 * (int64_t)npw;  // the real view of a row
+  const int ti = (na + kOvTile - 1) / kOvTile, tj = (nbb + kOvTile - 1) / kOvTile;
+  const int tiles = sym ? tj * (tj + 1) / 2 : ti * tj;
+  // chunks of the sum: at least two CTAs per SM (152 SMs), each chunk at least
+  // 4 k-blocks, and among up to four times that many the count whose CTAs
+  // fill their last wave over the SMs best (the FP64 pipe is the bound, so
+  // an SM with one CTA more than the others sets the time)
+  constexpr int kSMs = 152;
+  const int64_t max_splits = (K + 4 * kOvK - 1) / (4 * kOvK);
+  int s0 = (2 * kSMs + tiles - 1) / tiles;
+  if (s0 > max_splits) s0 = (int)max_splits;
+  if (s0 < 1) s0 = 1;
+  int splits = s0;
+  double best = -1.0;
+  for (int c = s0; c <= 4 * s0 && c <= max_splits; ++c) {
+    const int64_t ctas = (int64_t)tiles * c;
+    const double fill = (double)ctas / (double)(((ctas + kSMs - 1) / kSMs) * kSMs);
+    if (fill > best + 1e-9) {
+      best = fill;
+      splits = c;
+    }
+  }
+  int64_t kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + kOvK - 1) / kOvK * kOvK;
+  splits = (int)((K + kchunk - 1) / kchunk);
+  const int64_t entries = (int64_t)na * nbb;
+  k_overlap_zero<<<(int)((entries + 255) / 256 < 1216 ? (entries + 255) / 256 : 1216), 256, 0, s>>>(S, na, nbb,
+                                                                                                sym ? 1 : 0, ld);
+  k_overlap<<<dim3(tiles, splits), kOvThreads, 0, s>>>(reinterpret_cast<const double*>(a), na,
+                                                       reinterpret_cast<const double*>(b), nbb, K, sym ? 1 : 0, tj,
+                                                       kchunk, S, ld);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_energy_reduce(const int2* pairs, int npairs, const double* occ,
                                  const double* epair, const double* dpair, double scale,
                                  double* out, cudaStream_t s) {

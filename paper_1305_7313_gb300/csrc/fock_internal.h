@@ -64,6 +64,13 @@ struct DevPlan {
   // Brillouin-zone sampling: full-grid tables [nq][N][N][N] of v(G + q)
   const void* vtabq;      // v / Ntot in the working precision
   const double* vtabq64;  // v in FP64
+  // mixed form: FP64 overlaps S(i, j) = Re sum_G conj(c_i(G)) c_j(G) of the
+  // pairs (i <= j) at ovl[i * ovl_ld + j - ovl_j0]; the column pass takes the
+  // G = 0 value of a pair density as ovl_scale * S(i, j) (= sum over the grid
+  // of psi_i psi_j, ovl_scale = Ntot / Omega).  NULL: the transform's value.
+  const double* ovl;
+  int ovl_ld, ovl_j0;
+  double ovl_scale;
 };
 
 struct KernelOps {
@@ -191,6 +198,12 @@ cudaError_t st_dir(double2* p, const double2* r, const double* rr_new, const dou
                    cudaStream_t s);
 cudaError_t st_gather_rows(const double2* src, double2* dst, const int* perm, int m, int npw, cudaStream_t s);
 cudaError_t st_gather_scalars(const double* src, double* dst, const int* perm, int m, cudaStream_t s);
+
+// S[i * ld + j] = Re sum_G conj(a_i(G)) b_j(G) for i < na, j < nb (sym: a = b
+// and only j >= i), in FP64, a and b complex128 rows of npw; S is overwritten
+// at those entries (others untouched).
+cudaError_t launch_overlap(const double2* a, int na, const double2* b, int nb, int npw, bool sym, double* S,
+                           int ld, cudaStream_t s);
 
 // E = scale * sum_p f_i f_j (1 or 2) e_p over the pairs; out[0] = E, out[1] = dE.
 cudaError_t launch_energy_reduce(const int2* pairs, int npairs, const double* occ,

@@ -266,7 +266,15 @@ __device__ __noinline__ void small_g_term_fp64(const DevPlan& g, cplx<T>* S, int
   const int64_t vi = ((int64_t)k1 * N + k2) * KH + k3;
   const double wgt = (k3 == 0 || 2 * k3 == N) ? 1.0 : 2.0;
   cplx<T> z = S[e];
-  const double zx = z.x, zy = z.y, a2 = zx * zx + zy * zy;
+  double zx = z.x, zy = z.y;
+  if (g.ovl != nullptr && k1 == 0 && k2 == 0 && k3 == 0) {
+    // G = 0: the sum of the pair density over the grid, from the FP64 overlap
+    // of the pair's coefficients instead of the FP32 transform (real)
+    const int i = s ? ch.bi : ch.ai, j = s ? ch.bj : ch.aj;
+    zx = g.ovl_scale * g.ovl[(int64_t)i * g.ovl_ld + (j - g.ovl_j0)];
+    zy = 0.0;
+  }
+  const double a2 = zx * zx + zy * zy;
   const double v = g.vtab64[vi];
   const int slot = s ? ch.pb : ch.pa;
   if (slot >= 0) {

@@ -98,6 +98,12 @@ struct fock_plan {
   double* d_dpart = nullptr;
   int det_nb_cap = 0;
   int det_npair_cap = 0;
+  // mixed form: FP64 pair overlaps for the G = 0 terms (DevPlan::ovl) and the
+  // occupied coefficients of fock_set_occupied (for the fixed operator's)
+  double* d_ovl = nullptr;
+  int64_t ovl_cap = 0;
+  double2* d_cocc = nullptr;
+  int64_t cocc_cap = 0;
   int64_t kept_columns = 0;  // lines of the column map (both pairs)
   double* d_result = nullptr;
   double* h_result = nullptr;  // pinned
@@ -384,6 +390,31 @@ fock_status upload_occ(fock_plan* p, const double* occ, int nb, cudaStream_t s) 
   return FOCK_OK;
 }
 
+// The FP64 overlaps of the mixed form's G = 0 terms: S(i, j) = Re sum_G
+// conj(a_i) b_j for the pairs of an apply, into the plan's buffer, and the
+// DevPlan fields that point the column pass at them (ld columns, column j at
+// j - j0).  Other precisions leave dp.ovl NULL.
+fock_status prepare_overlaps(fock_plan* p, const void* a, int na, const void* b, int nbb, bool sym, int j0,
+                             DevPlan* dp, cudaStream_t s) {
+  dp->ovl = nullptr;
+  if (p->ops->prec != 1 || na < 1 || nbb < 1) return FOCK_OK;
+  const int64_t need = (int64_t)na * nbb;
+  if (need > p->ovl_cap) {
+    cudaFree(p->d_ovl);
+    p->d_ovl = nullptr;
+    p->ovl_cap = 0;
+    FOCK_CUDA(p, dev_alloc(&p->d_ovl, sizeof(double) * (size_t)need));
+    p->ovl_cap = need;
+  }
+  FOCK_CUDA(p, fockx::launch_overlap(static_cast<const double2*>(a), na, static_cast<const double2*>(b), nbb,
+                                     p->npw, sym, p->d_ovl, nbb, s));
+  dp->ovl = p->d_ovl;
+  dp->ovl_ld = nbb;
+  dp->ovl_j0 = j0;
+  dp->ovl_scale = (double)p->dp.ntot / p->vol;
+  return FOCK_OK;
+}
+
 int bands_per_grid_batch(const fock_plan* p) {
   const size_t grid_bytes = (size_t)p->dp.ntot * 2 * (size_t)p->ops->real_bytes;
   const int q = (int)std::max<size_t>(1, p->ws.h_bytes / grid_bytes);
@@ -496,6 +527,11 @@ fock_status apply_impl(fock_plan* p, const void* psiG, int nb, const double* occ
 
   DevPlan dp = p->dp;
   if (!dex) dp.dvtab64 = nullptr;  // skip the dE/domega partials nobody asked for
+  if (p->ops->prec == 1) {  // FP64 overlaps for the G = 0 terms (two launches)
+    PhaseScope ps(p, FOCK_PHASE_TO_REAL, 2, s);
+    st = prepare_overlaps(p, psiG, nb, psiG, nb, true, 0, &dp, s);
+    if (st != FOCK_OK) return st;
+  }
   double* ep = p->ws.epair;
   double* dpp = p->ws.dpair;
   if (p->det) {
@@ -1270,6 +1306,19 @@ fock_status fock_set_occupied(fock_plan_t plan, const void* psi_G, int nb, const
   if (st != FOCK_OK) return st;
   st = orbitals_to_real(plan, psi_G, nb, s);
   if (st != FOCK_OK) return st;
+  if (plan->ops->prec == 1) {
+    // the coefficients of the occupied set, for the FP64 overlaps of the
+    // fixed operator's G = 0 terms
+    const int64_t need = (int64_t)nb * plan->npw;
+    if (need > plan->cocc_cap) {
+      cudaFree(plan->d_cocc);
+      plan->d_cocc = nullptr;
+      plan->cocc_cap = 0;
+      FOCK_CUDA(plan, dev_alloc(&plan->d_cocc, sizeof(double2) * (size_t)need));
+      plan->cocc_cap = need;
+    }
+    FOCK_CUDA(plan, cudaMemcpyAsync(plan->d_cocc, psi_G, sizeof(double2) * (size_t)need, cudaMemcpyDeviceToDevice, s));
+  }
   plan->fixed_nb = nb;
   plan->fixed_sched_nt = -1;
   return FOCK_OK;
@@ -1333,6 +1382,12 @@ fock_status fock_apply_fixed(fock_plan_t plan, const void* phi_G, int nt, void* 
     st = det_buffers(p, nb + nt, 1);
     if (st != FOCK_OK) return st;
     st = det_prepare(p, nb + nt, nb, &dp, s);
+    if (st != FOCK_OK) return st;
+  }
+  if (p->ops->prec == 1 && p->d_cocc != nullptr) {
+    // FP64 overlaps of the pairs (occupied i, trial nb + t) for the G = 0 terms
+    PhaseScope ps(p, FOCK_PHASE_TO_REAL, 2, s);
+    st = prepare_overlaps(p, p->d_cocc, nb, phi_G, nt, false, nb, &dp, s);
     if (st != FOCK_OK) return st;
   }
   const int nch = (int)p->chains.size();
@@ -1447,6 +1502,8 @@ fock_status fock_destroy(fock_plan_t plan) {
   cudaFree(plan->d_scale);
   cudaFree(plan->d_epart);
   cudaFree(plan->d_dpart);
+  cudaFree(plan->d_ovl);
+  cudaFree(plan->d_cocc);
   cudaFree(plan->d_result);
   if (plan->h_result) cudaFreeHost(plan->h_result);
   delete plan;
@@ -1544,6 +1601,11 @@ fock_status batch_enqueue(fock_batch* b, cudaStream_t s) {
                                     std::min(nbat, nb - b0), p->ws.h, p->ws.psi, s));
       b->launches += 3;
     }
+    if (p->ops->prec == 1) {
+      FOCK_BCUDA(b, fockx::launch_overlap(static_cast<const double2*>(b->psi[k]), nb,
+                                          static_cast<const double2*>(b->psi[k]), nb, p->npw, true, p->d_ovl, nb, s));
+      b->launches += 2;
+    }
   }
   const unsigned long long limit_ns = (unsigned long long)(b->opt.wait_limit_s * 1e9);
   // external event nodes when captured, so the elapsed time is readable after a replay
@@ -1569,6 +1631,12 @@ fock_status batch_enqueue(fock_batch* b, cudaStream_t s) {
       FOCK_BCUDA(b, cudaStreamWaitEvent(bs, b->branch_ev[0], 0));
       fockx::DevPlan dp = p->dp;
       if (!b->opt.want_dex) dp.dvtab64 = nullptr;
+      if (p->ops->prec == 1) {
+        dp.ovl = p->d_ovl;
+        dp.ovl_ld = b->nb[k];
+        dp.ovl_j0 = 0;
+        dp.ovl_scale = (double)p->dp.ntot / p->vol;
+      }
       const int nch = (int)p->chains.size();
       for (int c = 0; c < nch; c += p->chain_batch) {
         const int cnt = std::min(p->chain_batch, nch - c);
@@ -1758,6 +1826,22 @@ fock_status fock_batch_create(fock_batch_t* out, int nsys, const fock_plan_t* pl
     fock_plan* p = b->plans[k];
     sd[k].g = p->dp;
     if (!o.want_dex) sd[k].g.dvtab64 = nullptr;
+    if (p->ops->prec == 1) {
+      // the FP64 overlaps of the system's pairs (G = 0 terms), filled by each run
+      const int64_t need = (int64_t)nb[k] * nb[k];
+      if (need > p->ovl_cap) {
+        cudaFree(p->d_ovl);
+        p->d_ovl = nullptr;
+        p->ovl_cap = 0;
+        if ((e = cudaMalloc((void**)&p->d_ovl, sizeof(double) * (size_t)need)) != cudaSuccess)
+          return fail_create(bcuda(b, e, "allocating the overlaps"));
+        p->ovl_cap = need;
+      }
+      sd[k].g.ovl = p->d_ovl;
+      sd[k].g.ovl_ld = nb[k];
+      sd[k].g.ovl_j0 = 0;
+      sd[k].g.ovl_scale = (double)p->dp.ntot / p->vol;
+    }
     sd[k].psi = p->ws.psi;
     sd[k].W = p->ws.w;
     sd[k].occT = p->ws.occT;

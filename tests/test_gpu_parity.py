@@ -250,3 +250,28 @@ def test_pair_launches_on_several_streams_match_the_oracle(prec, tol):
     with pytest.raises(_lib.FockError):
         plan.set_streams(5)
     plan.close()
+
+
+@pytest.mark.parametrize("kind,omega", [(_lib.SPENCER_ALAVI, None), (_lib.ERFC, 0.3)], ids=["sa", "erfc"])
+def test_mixed_form_takes_the_g0_term_from_fp64_overlaps(kind, omega):
+    # one band c(G) = delta_G0, psi(r) = Omega^-1/2: the pair density is a
+    # constant, its transform vanishes away from G = 0 in any arithmetic, and
+    # the one kernel term, at G = 0, comes from the FP64 overlap of the pair's
+    # coefficients: E_x and dE_x/domega to FP64 rounding (the FP32 transform's
+    # own G = 0 value is good to ~1e-7 only)
+    torch = require_gpu()
+    N, L, ecut = 32, 11.0, 6.0
+    cell = cubic(L)
+    plan = FockPlan(N, cell, ecut, kind, omega, _lib.PREC_MIXED32)
+    mill, _ = oracle.gsphere((N,) * 3, cell, ecut)
+    c = np.zeros((1, len(mill)), dtype=np.complex128)
+    c[0, int(np.flatnonzero(np.all(mill == 0, axis=1))[0])] = 1.0
+    occ = np.array([2.0])
+    want_d = kind == _lib.ERFC
+    vpsi, ex, dex = plan.apply(torch.from_numpy(c).cuda(), occ, want_dex=want_d)
+    ok = O_SA if kind == _lib.SPENCER_ALAVI else O_ERFC
+    _, eref, dref = oracle.fock_apply(c, occ, mill, (N,) * 3, cell, ok, omega)
+    assert abs(ex - eref) <= 1e-13 * abs(eref)
+    if want_d:
+        assert abs(dex - dref) <= 1e-13 * abs(dref)
+    plan.close()
