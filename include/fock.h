@@ -73,7 +73,11 @@ typedef enum {
   /* Everything in FP64: transforms, products, accumulators, energies. */
   FOCK_PREC_FP64 = 0,
   /* complex64 transforms and FP32 pair products / V_x psi accumulation; the
-   * kernel terms of the smallest |G| (|m|^2 <= 3) and every energy sum in FP64. */
+   * kernel terms of the smallest |G| (|m|^2 <= 3) and every energy sum in FP64.
+   * The G = 0 value of each pair density is taken from the FP64 overlap
+   * Re sum_G c_i(G)* c_j(G) of the input coefficients (times N^3 / Omega),
+   * computed on the device for every apply (fock_apply, fock_apply_shard,
+   * fock_apply_fixed, batches; an nb x nb FP64 buffer in the plan). */
   FOCK_PREC_MIXED32 = 1,
   /* Double-float: every real of the pair passes and the O(nb) transforms is
    * the unevaluated sum of two floats (about 48 significant bits, float's
@@ -285,7 +289,8 @@ fock_status fock_apply_shard(fock_plan_t plan, const void* psi_G, int nb, const 
  *
  * fock_set_occupied fixes the occupied orbitals (psi_G device complex128
  * [nb][npw], occ host [nb]) that define V_x; they are transformed to real
- * space once and kept in the plan.  fock_apply_fixed then returns, for nt
+ * space once and kept in the plan (in FOCK_PREC_MIXED32 the plan also keeps
+ * a copy of psi_G, for the FP64 overlaps of the G = 0 terms).  fock_apply_fixed then returns, for nt
  * trial orbitals phi_a (phi_G device complex128 [nt][npw]),
  *   (V_x phi_a)(r) = - sum_i f_i psi_i(r) IFFT[v FFT(psi_i* phi_a)](r)
  * on the sphere (vphi_G device complex128 [nt][npw], must not overlap phi_G):
