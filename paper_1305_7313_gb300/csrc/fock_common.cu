@@ -227,6 +227,20 @@ __global__ void k_overlap_zero(double* S, int na, int nbb, int sym, int ld) {
 
 }  // namespace
 
+namespace {
+__global__ void k_scaled_table(const double* __restrict__ v, int64_t n, double factor, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = factor * v[i];
+}
+}  // namespace
+
+cudaError_t launch_scaled_table(const double* v, int64_t n, double factor, double* out, cudaStream_t s) {
+  if (n < 1) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  k_scaled_table<<<(int)(blocks < 1216 ? blocks : 1216), 256, 0, s>>>(v, n, factor, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_overlap(const double2* a, int na, const double2* b, int nbb, int npw, bool sym, double* S,
                            int ld, cudaStream_t s) {
   if (na < 1 || nbb < 1) return cudaSuccess;

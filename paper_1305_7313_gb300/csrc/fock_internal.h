@@ -71,6 +71,13 @@ struct DevPlan {
   const double* ovl;
   int ovl_ld, ovl_j0;
   double ovl_scale;
+  // FP64 form with one occupation f0 for every band: vtab
+  // then holds -f0 v / Ntot (and vtab_f points at it), so that phi arrives at
+  // the inverse pass already scaled by -f0 and its accumulator update saves
+  // the two multiplications by -f per point.  NULL: vtab is v / Ntot, and the
+  // update multiplies by -f itself.  vtab_f_factor = -f0 (nonzero).
+  const void* vtab_f;
+  double vtab_f_factor;
 };
 
 struct KernelOps {
@@ -198,6 +205,9 @@ cudaError_t st_dir(double2* p, const double2* r, const double* rr_new, const dou
                    cudaStream_t s);
 cudaError_t st_gather_rows(const double2* src, double2* dst, const int* perm, int m, int npw, cudaStream_t s);
 cudaError_t st_gather_scalars(const double* src, double* dst, const int* perm, int m, cudaStream_t s);
+
+// out[i] = factor * v[i], i < n (FP64).
+cudaError_t launch_scaled_table(const double* v, int64_t n, double factor, double* out, cudaStream_t s);
 
 // S[i * ld + j] = Re sum_G conj(a_i(G)) b_j(G) for i < na, j < nb (sym: a = b
 // and only j >= i), in FP64, a and b complex128 rows of npw; S is overwritten

@@ -572,7 +572,7 @@ __device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __rest
   int* codes = reinterpret_cast<int*>(red + 32 * 4);
   load_twiddles<df64>(tw, g);
   const bool want_d = g.dvtab64 != nullptr;
-  const df64* vt = static_cast<const df64*>(g.vtab);    // v / Ntot
+  const df64* vt = static_cast<const df64*>(g.vtab);  // v / Ntot
   const df64* dvt = static_cast<const df64*>(g.dvtab);  // dv/domega
   col_codes<NC>(g, cta, codes);
   {
@@ -676,7 +676,8 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
       const double wgt = (k3 == 0 || 2 * k3 == N) ? 1.0 : 2.0;
       const double* v64 = g.vtab64 + k2 * KH + k3;
       const double* dv64 = g.dvtab64 ? g.dvtab64 + k2 * KH + k3 : nullptr;
-      const double* vs64 = static_cast<const double*>(g.vtab) + k2 * KH + k3;  // v / Ntot
+      // v / Ntot, or -f0 v / Ntot when the occupations are uniform (vtab_f set)
+      const double* vs64 = static_cast<const double*>(g.vtab) + k2 * KH + k3;
       double e_sum = 0.0, d_sum = 0.0;
       for (int k1 = threadIdx.x / NC; k1 < N; k1 += kstep) {
         const int e = k1 * NC + l;
@@ -1044,11 +1045,16 @@ __device__ __forceinline__ void pair_inv_task(const DevPlan& g, const T* __restr
     // both sources of each pair equally occupied (the usual case): -f phi is
     // formed once per pair and point, one multiplication fewer per update
     const bool same_f = f[0] == f[1] && f[2] == f[3];
+    // FP64: phi carries -f0 already (uniform occupations)
+    const bool prescaled = RealTraits<T>::prec == 0 && g.vtab_f != nullptr;
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
       const int i2 = e / N, i3 = e - i2 * N;
       const C z = Q[i2 * NCP + i3];
       T c[4];
-      if (same_f) {
+      if (RealTraits<T>::prec == 0 && prescaled) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k] = tgt[k] < 0 ? T(0) : ps[k][e] * (k < 2 ? z.x : z.y);
+      } else if (same_f) {
         const T ga = -f[0] * z.x, gb = -f[2] * z.y;
 #pragma unroll
         for (int k = 0; k < 4; ++k) c[k] = tgt[k] < 0 ? T(0) : ps[k][e] * (k < 2 ? ga : gb);
