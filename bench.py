@@ -173,9 +173,9 @@ def time_form(plan, psi, occ, steps, warmup, want_dex=False, rank=0, world=1):
 # to a launch by its chains, reported only for a captured band block (the
 # orbital re-reads depend on it).
 MEASURED_TRAFFIC_PER_CHAIN = {
-    ("fp64", 96, "pair_inv", 8): 54.15e6, ("fp64", 96, "pair_inv", 16): 47.07e6, ("fp64", 96, "pair_inv", 32): 52.56e6,
+    ("fp64", 96, "pair_inv", 8): 54.04e6, ("fp64", 96, "pair_inv", 16): 47.18e6, ("fp64", 96, "pair_inv", 32): 52.54e6,
     ("df64", 96, "pair_inv", 8): 57.45e6, ("df64", 96, "pair_inv", 16): 50.67e6, ("df64", 96, "pair_inv", 32): 53.20e6,
-    ("mixed32", 96, "pair_inv", 8): 12.61e6, ("mixed32", 96, "pair_inv", 16): 19.27e6,
+    ("mixed32", 96, "pair_inv", 8): 12.61e6, ("mixed32", 96, "pair_inv", 16): 19.28e6,
 }
 
 
@@ -335,9 +335,9 @@ def loop_roofline(form, plan, res, steps, peaks, peak_src, band_block, streams):
 # (profiles/pair_traffic_96.md), by form and band block; scaled to a step by
 # its chains
 MEASURED_LOOP_TRAFFIC_PER_CHAIN = {
-    ("fp64", 96, 8): 96.09e6, ("fp64", 96, 16): 86.96e6, ("fp64", 96, 32): 94.28e6,
+    ("fp64", 96, 8): 95.84e6, ("fp64", 96, 16): 87.02e6, ("fp64", 96, 32): 94.23e6,
     ("df64", 96, 8): 98.46e6, ("df64", 96, 16): 90.22e6, ("df64", 96, 32): 94.56e6,
-    ("mixed32", 96, 8): 28.91e6, ("mixed32", 96, 16): 37.52e6,
+    ("mixed32", 96, 8): 29.07e6, ("mixed32", 96, 16): 37.69e6,
 }
 
 
@@ -460,7 +460,7 @@ def run_batched(args, peaks, peak_src):
 # systems, by grid size, at band block 16: an ncu capture of every pair launch
 # of the 64-band version of the batch as graph branches (launches serialised
 # by ncu; profiles/pair_traffic_96.md)
-BATCH_DRAM_PER_CHAIN = {48: 3.068e6, 64: 7.342e6, 72: 10.752e6, 96: 42.145e6}
+BATCH_DRAM_PER_CHAIN = {48: 3.077e6, 64: 7.361e6, 72: 10.790e6, 96: 42.290e6}
 BATCH_DRAM_BAND_BLOCK = 16
 
 

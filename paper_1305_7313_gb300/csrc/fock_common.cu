@@ -159,9 +159,12 @@ namespace {
 // split into chunks over gridDim.y and reduced with FP64 atomics.
 constexpr int kOvTile = 64, kOvK = 16, kOvThreads = 256;
 
+// K: terms of the sum (real-view entries); with `half`, entry k is component
+// k & 1 of sphere position half[k >> 1] (weight 2, weight 1 for k < 2: the
+// list's first position is G = 0), else entry k of the row; rows are RS doubles.
 __global__ void __launch_bounds__(kOvThreads)
-    k_overlap(const double* __restrict__ A, int na, const double* __restrict__ B, int nbb, int64_t K, int sym,
-              int tiles_j, int64_t kchunk, double* __restrict__ S, int ld) {
+    k_overlap(const double* __restrict__ A, int na, const double* __restrict__ B, int nbb, int64_t K, int64_t RS,
+              const int* __restrict__ half, int sym, int tiles_j, int64_t kchunk, double* __restrict__ S, int ld) {
   int ti, tj;
   if (sym) {  // blockIdx.x enumerates the tiles ti <= tj row by row
     int rem = blockIdx.x;
@@ -189,8 +192,19 @@ __global__ void __launch_bounds__(kOvThreads)
     for (int e = threadIdx.x; e < kOvTile * kOvK; e += kOvThreads) {
       const int r = e / kOvK, kk = e - r * kOvK;
       const int64_t k = kb + kk;
-      As[kk][r] = (i0 + r < na && k < k1) ? A[(int64_t)(i0 + r) * K + k] : 0.0;
-      Bs[kk][r] = (j0 + r < nbb && k < k1) ? B[(int64_t)(j0 + r) * K + k] : 0.0;
+      double a = 0.0, b = 0.0;
+      if (k < k1) {
+        int64_t c = k;
+        double w = 1.0;
+        if (half != nullptr) {
+          c = 2 * (int64_t)half[k >> 1] + (k & 1);
+          w = k < 2 ? 1.0 : 2.0;
+        }
+        if (i0 + r < na) a = w * A[(int64_t)(i0 + r) * RS + c];
+        if (j0 + r < nbb) b = B[(int64_t)(j0 + r) * RS + c];
+      }
+      As[kk][r] = a;
+      Bs[kk][r] = b;
     }
     __syncthreads();
 #pragma unroll
@@ -241,10 +255,11 @@ cudaError_t launch_scaled_table(const double* v, int64_t n, double factor, doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_overlap(const double2* a, int na, const double2* b, int nbb, int npw, bool sym, double* S,
-                           int ld, cudaStream_t s) {
+cudaError_t launch_overlap(const double2* a, int na, const double2* b, int nbb, int npw, const int* half,
+                           int nhalf, bool sym, double* S, int ld, cudaStream_t s) {
   if (na < 1 || nbb < 1) return cudaSuccess;
-  const int64_t K = 2 * (int64_t)npw;  // the real view of a row
+  const int64_t RS = 2 * (int64_t)npw;                        // the real view of a row
+  const int64_t K = half != nullptr ? 2 * (int64_t)nhalf : RS;  // terms of the sum
   const int ti = (na + kOvTile - 1) / kOvTile, tj = (nbb + kOvTile - 1) / kOvTile;
   const int tiles = sym ? tj * (tj + 1) / 2 : ti * tj;
   // chunks of the sum: at least two CTAs per SM (152 SMs), each chunk at least
@@ -273,8 +288,8 @@ cudaError_t launch_overlap(const double2* a, int na, const double2* b, int nbb, 
   k_overlap_zero<<<(int)((entries + 255) / 256 < 1216 ? (entries + 255) / 256 : 1216), 256, 0, s>>>(S, na, nbb,
                                                                                                 sym ? 1 : 0, ld);
   k_overlap<<<dim3(tiles, splits), kOvThreads, 0, s>>>(reinterpret_cast<const double*>(a), na,
-                                                       reinterpret_cast<const double*>(b), nbb, K, sym ? 1 : 0, tj,
-                                                       kchunk, S, ld);
+                                                       reinterpret_cast<const double*>(b), nbb, K, RS, half,
+                                                       sym ? 1 : 0, tj, kchunk, S, ld);
   return cudaGetLastError();
 }
 

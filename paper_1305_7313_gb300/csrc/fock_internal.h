@@ -211,9 +211,12 @@ cudaError_t launch_scaled_table(const double* v, int64_t n, double factor, doubl
 
 // S[i * ld + j] = Re sum_G conj(a_i(G)) b_j(G) for i < na, j < nb (sym: a = b
 // and only j >= i), in FP64, a and b complex128 rows of npw; S is overwritten
-// at those entries (others untouched).
-cudaError_t launch_overlap(const double2* a, int na, const double2* b, int nb, int npw, bool sym, double* S,
-                           int ld, cudaStream_t s);
+// at those entries (others untouched).  half (device, nhalf positions, or
+// NULL): G = 0 first, then one of each pair G, -G; for Gamma-point rows
+// (c(-G) = conj c(G)) the sum is then taken over that half of the sphere,
+// the pairs' terms doubled.
+cudaError_t launch_overlap(const double2* a, int na, const double2* b, int nb, int npw, const int* half, int nhalf,
+                           bool sym, double* S, int ld, cudaStream_t s);
 
 // E = scale * sum_p f_i f_j (1 or 2) e_p over the pairs; out[0] = E, out[1] = dE.
 cudaError_t launch_energy_reduce(const int2* pairs, int npairs, const double* occ,

@@ -102,6 +102,8 @@ struct fock_plan {
   // occupied coefficients of fock_set_occupied (for the fixed operator's)
   double* d_ovl = nullptr;
   int64_t ovl_cap = 0;
+  int* d_half = nullptr;  // G = 0, then one of each pair G, -G of the sphere (positions)
+  int nhalf_g = 0;
   // FP64: the kernel table scaled by -f0 (DevPlan::vtab_f)
   void* d_vtab_f = nullptr;
   double vtab_f_f0 = 0.0;
@@ -410,7 +412,7 @@ fock_status prepare_overlaps(fock_plan* p, const void* a, int na, const void* b,
     p->ovl_cap = need;
   }
   FOCK_CUDA(p, fockx::launch_overlap(static_cast<const double2*>(a), na, static_cast<const double2*>(b), nbb,
-                                     p->npw, sym, p->d_ovl, nbb, s));
+                                     p->npw, p->d_half, p->nhalf_g, sym, p->d_ovl, nbb, s));
   dp->ovl = p->d_ovl;
   dp->ovl_ld = nbb;
   dp->ovl_j0 = j0;
@@ -780,11 +782,20 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
     const int i1 = ((m1 % n) + n) % n, i2 = ((m2 % n) + n) % n, i3 = ((m3 % n) + n) % n;
     return (i1 * n + i2) * n + i3;
   };
+  // half of the sphere for the Gamma-point overlaps: G = 0 first, then the G
+  // whose first nonzero Miller index is positive
+  std::vector<int> half;
+  half.reserve(sph.size() / 2 + 1);
   for (size_t k = 0; k < sph.size(); ++k) {
     for (int a = 0; a < 3; ++a) p->miller[3 * k + a] = sph[k].m[a];
     gidx[k] = off(sph[k].m[0], sph[k].m[1], sph[k].m[2]);
     gneg[k] = off(-sph[k].m[0], -sph[k].m[1], -sph[k].m[2]);
+    const int* m = sph[k].m;
+    const int lead = m[0] != 0 ? m[0] : (m[1] != 0 ? m[1] : m[2]);
+    if (lead == 0) half.insert(half.begin(), (int)k);
+    else if (lead > 0) half.push_back((int)k);
   }
+  p->nhalf_g = (int)half.size();  // (npw + 1) / 2: the sphere is closed under G -> -G
 
   // kernel tables on the stored half of the grid: [k1][k2][k3 <= N/2]
   const int kh = n / 2 + 1;
@@ -871,6 +882,7 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
   }
   bool ok = upload((void**)&p->d_gidx, gidx.data(), sizeof(int) * gidx.size()) &&
             upload((void**)&p->d_gidxneg, gneg.data(), sizeof(int) * gneg.size()) &&
+            upload((void**)&p->d_half, half.data(), sizeof(int) * half.size()) &&
             upload((void**)&p->d_vtab64, v64.data(), sizeof(double) * nhalf);
   if (ok && kind == FOCK_KERNEL_ERFC) ok = upload((void**)&p->d_dvtab64, dv64.data(), sizeof(double) * nhalf);
   if (ok)
@@ -1537,6 +1549,7 @@ fock_status fock_destroy(fock_plan_t plan) {
   cudaFree(plan->d_epart);
   cudaFree(plan->d_dpart);
   cudaFree(plan->d_ovl);
+  cudaFree(plan->d_half);
   cudaFree(plan->d_cocc);
   cudaFree(plan->d_vtab_f);
   cudaFree(plan->d_result);
@@ -1638,7 +1651,8 @@ fock_status batch_enqueue(fock_batch* b, cudaStream_t s) {
     }
     if (p->ops->prec == 1) {
       FOCK_BCUDA(b, fockx::launch_overlap(static_cast<const double2*>(b->psi[k]), nb,
-                                          static_cast<const double2*>(b->psi[k]), nb, p->npw, true, p->d_ovl, nb, s));
+                                          static_cast<const double2*>(b->psi[k]), nb, p->npw, p->d_half, p->nhalf_g,
+                                          true, p->d_ovl, nb, s));
       b->launches += 2;
     }
   }

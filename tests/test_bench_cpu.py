@@ -86,11 +86,11 @@ def test_roofline_arithmetic_matches_the_documented_figures():
     # the measured DFMA-loop rate (1.2557 TFLOP/s at 2070 MHz) is the FP64 denominator
     assert r["kernel"] == "pair_inv" and abs(r["peak"] - 1.2557) < 1e-9
     assert abs(r["achieved"] - 5 * n3 * 2 * lg * 38 / 1e-3 / 1e12) < 1e-9  # 38 chains in 1 ms
-    assert abs(r["traffic"] / 1e6 - 47.07 * 38) < 1e-6  # band block 16: the capture's 47.07 MB per chain
+    assert abs(r["traffic"] / 1e6 - 47.18 * 38) < 1e-6  # band block 16: the capture's 47.18 MB per chain
     r4 = b.roofline("fp64", _Plan(), _res(10.0), 1, peaks, "measured", band_block=4)
     assert r4["traffic"] is None  # band block 4: not captured
     r8 = b.roofline("fp64", _Plan(), _res(10.0), 1, peaks, "measured", band_block=8)
-    assert abs(r8["traffic"] / 1e6 - 54.15 * 38) < 1e-6  # the ncu capture's 2057.7 MB per 38-chain launch
+    assert abs(r8["traffic"] / 1e6 - 54.04 * 38) < 1e-6  # the ncu capture's 2053.5 MB per 38-chain launch
     # double-float peak: the measured FP32 FMA rate (78.52 TFLOP/s = 39.26 T
     # instructions/s) / 9.4 instructions per flop
     rd = b.roofline("df64", _Plan(), _res(10.0), 1, peaks, "measured")
@@ -120,7 +120,7 @@ def test_loop_roofline_counts_all_three_pair_passes():
     rm = b.roofline("mixed32", _Plan(), res, 1, peaks, "measured", 8, streams=2)
     assert abs(rm["bytes_per_chain"] / 1e6 - 24.44) < 0.05  # 4 x 4.34 MB of kept columns + 16 planes / 8
     assert abs(rm["achieved"] - rm["bytes_per_chain"] * 1000 / 0.97 / 1e9) < 1e-6
-    assert abs(rm["traffic"] / 1e6 - 28.91 * 1000) < 1e-6  # all three kernels, 1000 chains
+    assert abs(rm["traffic"] / 1e6 - 29.07 * 1000) < 1e-6  # all three kernels, 1000 chains
     assert b.roofline("mixed32", _Plan(), res, 1, peaks, "measured", 4, streams=2)["traffic"] is None
 
 
