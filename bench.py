@@ -506,14 +506,21 @@ def run_kpoints(args, peaks, peak_src):
     pairs = ns * (ns + 1) // 2
     nbytes = pairs * 4.0 * n**3 * 8.0  # complex64 full spectrum: written, read + written, read
     achieved = nbytes * args.steps / (ms * 1e-3) / 1e9
+    # DRAM bytes (read + write) per pair of the three k-point pair kernels, from
+    # an ncu capture of every pair launch of this leg (profiles/kpair_traffic_48.md)
+    traffic = KPOINT_DRAM_PER_PAIR * pairs if nb == 32 else None
     plan.close()
     return {"workload": "kpoints8_mixed32_erfc_L13.5_N48_nb32", "kpoints": len(kpts), "bands_per_k": nb,
             "value": pairs * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
             "pairs": pairs, "dtype": "f32",
             "roofline": {"bound": "hbm", "kernel": "pair passes (whole step)", "achieved": achieved,
                          "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                         "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                         "frac": achieved / float(peaks["hbm_gbs"]), "traffic": traffic,
+                         "traffic_unit": "DRAM bytes per step (ncu, all three kernels)",
                          "peak_src": peak_src + " (hbm copy)"}}
+
+
+KPOINT_DRAM_PER_PAIR = 3.351e6
 
 
 def run_fixed(args):
