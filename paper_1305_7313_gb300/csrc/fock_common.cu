@@ -152,19 +152,28 @@ cudaError_t launch_det_pair_sums(const double* part, int npairs, int ncta, doubl
   return cudaGetLastError();
 }
 
+#define FOCK_OV_CHECK(call)             \
+  do {                                  \
+    const cudaError_t e_ = (call);      \
+    if (e_ != cudaSuccess) return e_;   \
+  } while (0)
+
 namespace {
 
-// Overlap tiles: 64 x 64 entries of S per CTA (16 x 16 threads, each 4 x 4
-// entries 16 apart), the sum over the real views of the rows (2 npw doubles)
-// split into chunks over gridDim.y and reduced with FP64 atomics.
-constexpr int kOvTile = 64, kOvK = 16, kOvThreads = 256;
+// Overlap tiles: TB x TB entries of S per CTA (16 x 16 threads, each
+// TB/16 x TB/16 entries 16 apart; TB = 64, or 32 for matrices of at most 32
+// rows), the sum over the real views of the rows split into chunks over
+// gridDim.y and reduced with FP64 atomics.
+constexpr int kOvK = 16, kOvThreads = 256;
 
 // K: terms of the sum (real-view entries); with `half`, entry k is component
 // k & 1 of sphere position half[k >> 1] (weight 2, weight 1 for k < 2: the
 // list's first position is G = 0), else entry k of the row; rows are RS doubles.
+template <int TB>
 __global__ void __launch_bounds__(kOvThreads)
     k_overlap(const double* __restrict__ A, int na, const double* __restrict__ B, int nbb, int64_t K, int64_t RS,
               const int* __restrict__ half, int sym, int tiles_j, int64_t kchunk, double* __restrict__ S, int ld) {
+  constexpr int MT = TB / 16;
   int ti, tj;
   if (sym) {  // blockIdx.x enumerates the tiles ti <= tj row by row
     int rem = blockIdx.x;
@@ -178,18 +187,18 @@ __global__ void __launch_bounds__(kOvThreads)
     ti = blockIdx.x / tiles_j;
     tj = blockIdx.x - ti * tiles_j;
   }
-  const int i0 = ti * kOvTile, j0 = tj * kOvTile;
+  const int i0 = ti * TB, j0 = tj * TB;
   const int64_t k0 = (int64_t)blockIdx.y * kchunk;
   const int64_t k1 = k0 + kchunk < K ? k0 + kchunk : K;
-  __shared__ double As[kOvK][kOvTile + 1], Bs[kOvK][kOvTile + 1];
+  __shared__ double As[kOvK][TB + 1], Bs[kOvK][TB + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4];
+  double acc[MT][MT];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < MT; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < MT; ++v) acc[u][v] = 0.0;
   for (int64_t kb = k0; kb < k1; kb += kOvK) {
-    for (int e = threadIdx.x; e < kOvTile * kOvK; e += kOvThreads) {
+    for (int e = threadIdx.x; e < TB * kOvK; e += kOvThreads) {
       const int r = e / kOvK, kk = e - r * kOvK;
       const int64_t k = kb + kk;
       double a = 0.0, b = 0.0;
@@ -209,23 +218,23 @@ __global__ void __launch_bounds__(kOvThreads)
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kOvK; ++kk) {
-      double a[4], b[4];
+      double a[MT], b[MT];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < MT; ++u) {
         a[u] = As[kk][ty + 16 * u];
         b[u] = Bs[kk][tx + 16 * u];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < MT; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < MT; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < MT; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < MT; ++v) {
       const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
       if (i < na && j < nbb && (!sym || j >= i)) atomicAdd(&S[(int64_t)i * ld + j], acc[u][v]);
     }
@@ -255,19 +264,118 @@ cudaError_t launch_scaled_table(const double* v, int64_t n, double factor, doubl
   return cudaGetLastError();
 }
 
+namespace {
+cudaError_t overlap_impl(const double2* a, int na, const double2* b, int nbb, int npw, const int* half, int nhalf,
+                         bool sym, double* S, int ld, cudaStream_t s);
+
+// Complex overlaps of nsets row sets (set z: rows[z], nb rows of npw[z]
+// complex128) with themselves, upper triangles: Sre/Sim[z][i][j] =
+// Re/Im sum_G conj(c_i(G)) c_j(G), j >= i.  32 x 32 tiles (16 x 16 threads,
+// 2 x 2 entries each, real and imaginary parts from the same loads), the
+// sum split into gridDim.y chunks of kchunk complex terms, FP64 atomics.
+__global__ void __launch_bounds__(kOvThreads)
+    k_overlap_sets(const double2* const* __restrict__ rows, const int* __restrict__ npw, int nb, int tiles_j,
+                   int kchunk, double* __restrict__ Sre, double* __restrict__ Sim) {
+  constexpr int TB = 32, KC = 16;
+  const int z = blockIdx.z;
+  int rem = blockIdx.x, ti = 0;
+  while (rem >= tiles_j - ti) {
+    rem -= tiles_j - ti;
+    ++ti;
+  }
+  const int tj = ti + rem;
+  const int i0 = ti * TB, j0 = tj * TB;
+  const double2* R = rows[z];
+  const int K = npw[z];
+  const int k0 = blockIdx.y * kchunk;
+  const int k1 = k0 + kchunk < K ? k0 + kchunk : K;
+  __shared__ double2 As[KC][TB + 1], Bs[KC][TB + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double re[2][2] = {{0.0, 0.0}, {0.0, 0.0}}, im[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int kb = k0; kb < k1; kb += KC) {
+    for (int e = threadIdx.x; e < TB * KC; e += kOvThreads) {
+      const int r = e / KC, kk = e - r * KC;
+      const int k = kb + kk;
+      const double2 zero = make_double2(0.0, 0.0);
+      As[kk][r] = (k < k1 && i0 + r < nb) ? R[(int64_t)(i0 + r) * K + k] : zero;
+      Bs[kk][r] = (k < k1 && j0 + r < nb) ? R[(int64_t)(j0 + r) * K + k] : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      double2 a[2], b[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        a[u] = As[kk][ty + 16 * u];
+        b[u] = Bs[kk][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          re[u][v] = fma(a[u].x, b[v].x, fma(a[u].y, b[v].y, re[u][v]));
+          im[u][v] = fma(a[u].x, b[v].y, fma(-a[u].y, b[v].x, im[u][v]));
+        }
+    }
+    __syncthreads();
+  }
+  const int64_t off = (int64_t)z * nb * nb;
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+      if (i < nb && j < nb && j >= i) {
+        atomicAdd(&Sre[off + (int64_t)i * nb + j], re[u][v]);
+        atomicAdd(&Sim[off + (int64_t)i * nb + j], im[u][v]);
+      }
+    }
+}
+}  // namespace
+
+cudaError_t launch_overlap_sets(const double2* const* rows, const int* npw, int npw_max, int nsets, int nb,
+                                double* Sre, double* Sim, cudaStream_t s) {
+  if (nsets < 1 || nb < 1) return cudaSuccess;
+  FOCK_OV_CHECK(cudaMemsetAsync(Sre, 0, sizeof(double) * (size_t)nsets * nb * nb, s));
+  FOCK_OV_CHECK(cudaMemsetAsync(Sim, 0, sizeof(double) * (size_t)nsets * nb * nb, s));
+  const int tj = (nb + 31) / 32, tiles = tj * (tj + 1) / 2;
+  // chunks: two CTAs per SM over all sets, each chunk at least 4 k-blocks,
+  // at most 64 chunks adding into one entry
+  int splits = (2 * 152 + tiles * nsets - 1) / (tiles * nsets);
+  const int max_splits = (npw_max + 63) / 64;
+  if (splits > max_splits) splits = max_splits;
+  if (splits > 64) splits = 64;
+  if (splits < 1) splits = 1;
+  int kchunk = (npw_max + splits - 1) / splits;
+  kchunk = (kchunk + 15) / 16 * 16;
+  splits = (npw_max + kchunk - 1) / kchunk;
+  k_overlap_sets<<<dim3(tiles, splits, nsets), kOvThreads, 0, s>>>(rows, npw, nb, tj, kchunk, Sre, Sim);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_overlap(const double2* a, int na, const double2* b, int nbb, int npw, const int* half,
                            int nhalf, bool sym, double* S, int ld, cudaStream_t s) {
+  return overlap_impl(a, na, b, nbb, npw, half, nhalf, sym, S, ld, s);
+}
+
+
+namespace {
+cudaError_t overlap_impl(const double2* a, int na, const double2* b, int nbb, int npw, const int* half, int nhalf,
+                         bool sym, double* S, int ld, cudaStream_t s) {
   if (na < 1 || nbb < 1) return cudaSuccess;
   const int64_t RS = 2 * (int64_t)npw;                        // the real view of a row
   const int64_t K = half != nullptr ? 2 * (int64_t)nhalf : RS;  // terms of the sum
-  const int ti = (na + kOvTile - 1) / kOvTile, tj = (nbb + kOvTile - 1) / kOvTile;
+  const int TB = (na <= 32 && nbb <= 32) ? 32 : 64;
+  const int ti = (na + TB - 1) / TB, tj = (nbb + TB - 1) / TB;
   const int tiles = sym ? tj * (tj + 1) / 2 : ti * tj;
-  // chunks of the sum: at least two CTAs per SM (152 SMs), each chunk at least
-  // 4 k-blocks, and among up to four times that many the count whose CTAs
-  // fill their last wave over the SMs best (the FP64 pipe is the bound, so
-  // an SM with one CTA more than the others sets the time)
+  // chunks of the sum: at least two CTAs per SM (152 SMs) and among up to
+  // four times that many the count whose CTAs fill their last wave over the
+  // SMs best (the FP64 pipe is the bound, so an SM with one CTA more than the
+  // others sets the time); each chunk at least 4 k-blocks, and at most 64
+  // chunks add into one entry (atomics on a small matrix contend)
   constexpr int kSMs = 152;
-  const int64_t max_splits = (K + 4 * kOvK - 1) / (4 * kOvK);
+  int64_t max_splits = (K + 4 * kOvK - 1) / (4 * kOvK);
+  if (max_splits > 64) max_splits = 64;
   int s0 = (2 * kSMs + tiles - 1) / tiles;
   if (s0 > max_splits) s0 = (int)max_splits;
   if (s0 < 1) s0 = 1;
@@ -287,11 +395,17 @@ cudaError_t launch_overlap(const double2* a, int na, const double2* b, int nbb, 
   const int64_t entries = (int64_t)na * nbb;
   k_overlap_zero<<<(int)((entries + 255) / 256 < 1216 ? (entries + 255) / 256 : 1216), 256, 0, s>>>(S, na, nbb,
                                                                                                 sym ? 1 : 0, ld);
-  k_overlap<<<dim3(tiles, splits), kOvThreads, 0, s>>>(reinterpret_cast<const double*>(a), na,
-                                                       reinterpret_cast<const double*>(b), nbb, K, RS, half,
-                                                       sym ? 1 : 0, tj, kchunk, S, ld);
+  const double* A = reinterpret_cast<const double*>(a);
+  const double* B = reinterpret_cast<const double*>(b);
+  if (TB == 32)
+    k_overlap<32><<<dim3(tiles, splits), kOvThreads, 0, s>>>(A, na, B, nbb, K, RS, half, sym ? 1 : 0, tj, kchunk,
+                                                            S, ld);
+  else
+    k_overlap<64><<<dim3(tiles, splits), kOvThreads, 0, s>>>(A, na, B, nbb, K, RS, half, sym ? 1 : 0, tj, kchunk,
+                                                            S, ld);
   return cudaGetLastError();
 }
+}  // namespace
 
 cudaError_t launch_energy_reduce(const int2* pairs, int npairs, const double* occ,
                                  const double* epair, const double* dpair, double scale,

@@ -64,6 +64,16 @@ struct DevPlan {
   // Brillouin-zone sampling: full-grid tables [nq][N][N][N] of v(G + q)
   const void* vtabq;      // v / Ntot in the working precision
   const double* vtabq64;  // v in FP64
+  // mixed form with k points: q of each table in reduced coordinates
+  // ([nq][3]; terms with |m + q|^2 <= msmall2 are done in FP64), the index of
+  // q = 0 (-1: none), and the FP64 overlaps of the states of each k point
+  // (kovl_re/im [nk][nb][nb], entries n <= n'), whose q = 0 pairs take their
+  // G = 0 value from them (times ovl_scale).  NULL: transform values.
+  const float* qfrac;
+  int q0;
+  const double* kovl_re;
+  const double* kovl_im;
+  int kovl_nb;
   // mixed form: FP64 overlaps S(i, j) = Re sum_G conj(c_i(G)) c_j(G) of the
   // pairs (i <= j) at ovl[i * ovl_ld + j - ovl_j0]; the column pass takes the
   // G = 0 value of a pair density as ovl_scale * S(i, j) (= sum over the grid
@@ -217,6 +227,13 @@ cudaError_t launch_scaled_table(const double* v, int64_t n, double factor, doubl
 // the pairs' terms doubled.
 cudaError_t launch_overlap(const double2* a, int na, const double2* b, int nb, int npw, const int* half, int nhalf,
                            bool sym, double* S, int ld, cudaStream_t s);
+// Complex overlaps of nsets sets of nb rows with themselves (set z: the
+// device pointer rows[z] to nb rows of npw[z] complex128; rows and npw are
+// device arrays, npw_max their largest npw): Sre/Sim[z][i][j] = Re/Im
+// sum_G conj(c_i(G)) c_j(G) for j >= i, in FP64 (Sre, Sim [nsets][nb][nb],
+// overwritten).
+cudaError_t launch_overlap_sets(const double2* const* rows, const int* npw, int npw_max, int nsets, int nb,
+                                double* Sre, double* Sim, cudaStream_t s);
 
 // E = scale * sum_p f_i f_j (1 or 2) e_p over the pairs; out[0] = E, out[1] = dE.
 cudaError_t launch_energy_reduce(const int2* pairs, int npairs, const double* occ,

@@ -148,14 +148,74 @@ __global__ void __launch_bounds__(Geo<T, N>::THR_COLF, Geo<T, N>::MIN_CTAS)
   } else {
     const T* vt = static_cast<const T*>(g.vtabq) + qoff;  // v / Ntot
     float accf[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-      const int k1 = e / N, k3 = e - k1 * N;
-      const T v = vt[((int64_t)k1 * N + k2) * N + k3];
-      C z = S[e];
-      accf[0] += v * (z.x * z.x + z.y * z.y);
-      z.x *= v;
-      z.y *= v;
-      S[e] = z;
+    // the terms with |m + q|^2 <= msmall2 (reduced coordinates) in FP64 from
+    // the FP64 table; the one with m + q = 0 (q = 0 pairs) from the FP64
+    // overlap of the pair's coefficients when the plan provides it
+    bool row_small = false;
+    float q1 = 0.f, q3 = 0.f, r2 = 0.f;
+    if (g.qfrac != nullptr && g.msmall2 >= 0) {
+      q1 = g.qfrac[3 * ch.pad1];
+      q3 = g.qfrac[3 * ch.pad1 + 2];
+      const float m2 = float(freq_of(k2, N)) + g.qfrac[3 * ch.pad1 + 1];
+      r2 = m2 * m2;
+      row_small = r2 <= float(g.msmall2);
+    }
+    if (!row_small) {
+      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int k1 = e / N, k3 = e - k1 * N;
+        const T v = vt[((int64_t)k1 * N + k2) * N + k3];
+        C z = S[e];
+        accf[0] += v * (z.x * z.x + z.y * z.y);
+        z.x *= v;
+        z.y *= v;
+        S[e] = z;
+      }
+    } else {
+      const double* v64 = g.vtabq64 + qoff;
+      double e64 = 0.0;
+      // |m1 + q1|^2 <= msmall2 - m2q^2 bounds |m1| by b1 (and m3 by b3): an
+      // integer box test first, the exact one inside it; k3 is the same for
+      // all of a thread's elements when the CTA's threads are a multiple of N
+      const float lim = sqrtf(float(g.msmall2) - r2);
+      const int b1 = min(N / 2 - 1, (int)floorf(lim + fabsf(q1))), b3 = min(N / 2 - 1, (int)floorf(lim + fabsf(q3)));
+      const bool k3_fixed = blockDim.x % N == 0;
+      const int k3t = threadIdx.x % N;
+      const bool box3_t = (k3t + b3 < N ? k3t + b3 : k3t + b3 - N) <= 2 * b3;
+      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int k1 = e / N, k3 = e - k1 * N;
+        const int64_t vi = ((int64_t)k1 * N + k2) * N + k3;
+        C z = S[e];
+        const int w1 = k1 + b1 < N ? k1 + b1 : k1 + b1 - N;
+        const bool box3 = k3_fixed ? box3_t : (k3 + b3 < N ? k3 + b3 : k3 + b3 - N) <= 2 * b3;
+        bool small = false;
+        if (box3 && w1 <= 2 * b1) {
+          const float m1 = float(freq_of(k1, N)) + q1, m3 = float(freq_of(k3, N)) + q3;
+          small = m1 * m1 + r2 + m3 * m3 <= float(g.msmall2);
+        }
+        if (small) {
+          double zx = z.x, zy = z.y;
+          if (g.kovl_re != nullptr && ch.pad1 == g.q0 && k1 == 0 && k2 == 0 && k3 == 0 &&
+              ch.ai / g.kovl_nb == ch.aj / g.kovl_nb) {
+            // q = 0 pair (a, b) of one k point: sum over the grid of conj(u_a) u_b
+            const int nb = g.kovl_nb, kk = ch.ai / nb;
+            const int64_t oi = ((int64_t)kk * nb + ch.ai % nb) * nb + ch.aj % nb;
+            zx = g.ovl_scale * g.kovl_re[oi];
+            zy = g.ovl_scale * g.kovl_im[oi];
+          }
+          const double v = v64[vi];
+          e64 += v * (zx * zx + zy * zy);
+          const double vs = v * g.inv_ntot;
+          z.x = T(zx * vs);
+          z.y = T(zy * vs);
+        } else {
+          const T v = vt[vi];
+          accf[0] += v * (z.x * z.x + z.y * z.y);
+          z.x *= v;
+          z.y *= v;
+        }
+        S[e] = z;
+      }
+      if (e64 != 0.0 && ch.pa >= 0) atomicAdd(&epair[ch.pa], e64);
     }
     float hi[4], lo[4];
     block_sum4_ff(accf, hi, lo, reinterpret_cast<float*>(red));

@@ -45,6 +45,13 @@ struct fock_kplan {
   std::vector<int> qidx;  // [ka * nk + kb] -> distinct q = k_b - k_a
   void* d_vq = nullptr;
   double* d_vq64 = nullptr;
+  float* d_qfrac = nullptr;  // [nq][3] q in reduced coordinates (mixed form)
+  // mixed form: FP64 overlaps of the states of each k point (q = 0 pairs' G = 0)
+  double* d_kovl = nullptr;  // [2][nk][nb][nb]: real parts, then imaginary parts
+  int64_t kovl_cap = 0;
+  const double2** d_krows = nullptr;  // [nk] the orbital arrays of an apply
+  int* d_knpw = nullptr;              // [nk] sphere sizes
+  int npw_max = 0;
   void* d_tw = nullptr;
   const fockx::KernelOps* ops = nullptr;
   const fockx::KOps* kops = nullptr;
@@ -327,6 +334,24 @@ fock_status fock_kplan_create(fock_kplan_t* out, const int grid[3], const double
   d.msmall2 = -1;
   d.vtabq = p->d_vq;
   d.vtabq64 = p->d_vq64;
+  d.q0 = -1;
+  for (int j = 0; j < p->nq; ++j)
+    if (qs[3 * j] == 0.0 && qs[3 * j + 1] == 0.0 && qs[3 * j + 2] == 0.0) d.q0 = j;
+  if (!fp64) {
+    // the mixed form's FP64 terms: |m + q|^2 <= 3 (reduced coordinates)
+    std::vector<float> qf(qs.begin(), qs.end());
+    if ((e = cudaMalloc((void**)&p->d_qfrac, sizeof(float) * qf.size())) != cudaSuccess ||
+        (e = cudaMemcpy(p->d_qfrac, qf.data(), sizeof(float) * qf.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(kcuda(p, e, "uploading q"));
+    d.qfrac = p->d_qfrac;
+    d.msmall2 = 3;
+    p->npw_max = *std::max_element(p->npw.begin(), p->npw.end());
+    if ((e = cudaMalloc((void**)&p->d_krows, sizeof(double2*) * nk)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&p->d_knpw, sizeof(int) * nk)) != cudaSuccess ||
+        (e = cudaMemcpy(p->d_knpw, p->npw.data(), sizeof(int) * nk, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(kcuda(p, e, "uploading the sphere sizes"));
+    d.ovl_scale = (double)ntot / p->vol;
+  }
   p->chain_batch = (int)std::max<size_t>(1, kBufferBytes / ((size_t)ntot * csz(p)));
 
   int optin = 0;
@@ -462,12 +487,35 @@ fock_status fock_kplan_apply(fock_kplan_t p, const void* const* psi_G, int nb, c
       const double2* src = static_cast<const double2*>(psi_G[k]) + (size_t)b0 * p->npw[k];
       FOCK_KCUDA(p, p->kops->to_real(p->dp, src, p->npw[k], p->d_gidx[k], k * nb + b0, cnt, p->d_h, p->d_u, s));
     }
+  DevPlan dp = p->dp;
+  if (p->ops->real_bytes == 4 && dp.q0 >= 0) {
+    // FP64 overlaps of each k point's states for the G = 0 terms of its q = 0 pairs
+    const int64_t per = (int64_t)nb * nb;
+    if (2 * nk * per > p->kovl_cap) {
+      cudaFree(p->d_kovl);
+      p->d_kovl = nullptr;
+      p->kovl_cap = 0;
+      FOCK_KCUDA(p, cudaMalloc((void**)&p->d_kovl, sizeof(double) * (size_t)(2 * nk * per)));
+      p->kovl_cap = 2 * nk * per;
+    }
+    double* re = p->d_kovl;
+    double* im = p->d_kovl + nk * per;
+    std::vector<const double2*> rows(nk);
+    for (int k = 0; k < nk; ++k) rows[k] = static_cast<const double2*>(psi_G[k]);
+    FOCK_KCUDA(p, cudaMemcpyAsync(p->d_krows, rows.data(), sizeof(double2*) * nk, cudaMemcpyHostToDevice, s));
+    // (a copy from pageable memory returns once the source has been staged,
+    // so the local vector may go)
+    FOCK_KCUDA(p, fockx::launch_overlap_sets(p->d_krows, p->d_knpw, p->npw_max, nk, nb, re, im, s));
+    dp.kovl_re = re;
+    dp.kovl_im = im;
+    dp.kovl_nb = nb;
+  }
   for (int c = 0; c < npairs; c += p->chain_batch) {
     const int cnt = std::min(p->chain_batch, npairs - c);
     const Chain* ch = p->d_chains + c;
-    FOCK_KCUDA(p, p->kops->pair_fwd(p->dp, p->d_u, ch, cnt, p->d_h, s));
-    FOCK_KCUDA(p, p->kops->pair_col(p->dp, p->d_h, ch, cnt, p->d_epair, s));
-    FOCK_KCUDA(p, p->kops->pair_inv(p->dp, p->d_u, p->d_w, p->d_occwT, ch, cnt, p->d_h, s));
+    FOCK_KCUDA(p, p->kops->pair_fwd(dp, p->d_u, ch, cnt, p->d_h, s));
+    FOCK_KCUDA(p, p->kops->pair_col(dp, p->d_h, ch, cnt, p->d_epair, s));
+    FOCK_KCUDA(p, p->kops->pair_inv(dp, p->d_u, p->d_w, p->d_occwT, ch, cnt, p->d_h, s));
   }
   for (int k = 0; k < nk; ++k)
     for (int b0 = 0; b0 < nb; b0 += nbat) {
@@ -494,6 +542,10 @@ fock_status fock_kplan_destroy(fock_kplan_t p) {
   for (int* d : p->d_gidx) cudaFree(d);
   cudaFree(p->d_vq);
   cudaFree(p->d_vq64);
+  cudaFree(p->d_qfrac);
+  cudaFree(p->d_kovl);
+  cudaFree(p->d_krows);
+  cudaFree(p->d_knpw);
   cudaFree(p->d_tw);
   cudaFree(p->d_result);
   if (p->h_result) cudaFreeHost(p->h_result);

@@ -112,3 +112,25 @@ def test_aliasing_grid_is_refused_and_the_device_stays_usable():
     vmax = max(np.max(np.abs(v)) for v in vref)
     for k in range(2):
         assert np.max(np.abs(vk[k].cpu().numpy() - vref[k])) <= 1e-10 * vmax
+
+
+@pytest.mark.parametrize("kind,omega", [(_lib.SPENCER_ALAVI, None), (_lib.ERFC, 0.5)], ids=["sa", "erfc"])
+def test_mixed_kpoints_take_the_g0_term_from_fp64_overlaps(kind, omega):
+    # one k point (q = 0 for its pairs), one state whose periodic part is a
+    # constant (c = 1 at G = 0): the pair density is constant, its transform
+    # vanishes away from G = 0 in any arithmetic, and the one kernel term
+    # comes from the FP64 overlap and the FP64 table: E_x to FP64 rounding
+    # (the FP32 transform's own value is good to ~1e-7 only)
+    torch = require_gpu()
+    N, L, ecut = 16, 7.0, 4.0
+    kp = np.array([[0.5, 0.0, 0.0]])
+    cell = cubic(L)
+    plan = FockKPlan(N, cell, ecut, kp, [1.0], kind, omega, _lib.PREC_MIXED32)
+    m = plan.miller(0)
+    c = np.zeros((1, len(m)), dtype=np.complex128)
+    c[0, int(np.flatnonzero(np.all(m == 0, axis=1))[0])] = 1.0
+    occ = np.array([[2.0]])
+    _, ex = plan.apply([torch.from_numpy(c).cuda()], occ)
+    ok = "spencer_alavi" if kind == _lib.SPENCER_ALAVI else "erfc"
+    _, eref = oracle.fock_apply_kpoints([c], occ, [m], kp, [1.0], (N, N, N), cell, ok, omega)
+    assert abs(ex - eref) <= 1e-13 * abs(eref)
