@@ -487,7 +487,10 @@ typedef struct fock_kplan* fock_kplan_t;
  * and the FFT plan.
  *   kpts   host double [nk][3]: k in reduced coordinates (k = sum_a kpts_a b_a).
  *   wk     host double [nk]: k-point weights (usually summing to 1).
- *   Other arguments as fock_plan_create.
+ *   Other arguments as fock_plan_create.  FOCK_PREC_MIXED32: the kernel terms
+ *   with |m + q|^2 <= 3 (m + q in reduced coordinates) in FP64, and for the
+ *   pairs of one k point the G = 0 value of the pair density from the FP64
+ *   overlap sum_G c_a(G)* c_b(G) of the input coefficients.
  * The grid is checked on the host before any CUDA call: GRID_TOO_SMALL when
  * an S_k does not fit (2 |m_a| >= N) or a pair density reaches the Nyquist
  * frequency (the condition above).
