@@ -371,11 +371,12 @@ cudaError_t overlap_impl(const double2* a, int na, const double2* b, int nbb, in
   // chunks of the sum: at least two CTAs per SM (152 SMs) and among up to
   // four times that many the count whose CTAs fill their last wave over the
   // SMs best (the FP64 pipe is the bound, so an SM with one CTA more than the
-  // others sets the time); each chunk at least 4 k-blocks, and at most 64
-  // chunks add into one entry (atomics on a small matrix contend)
+  // others sets the time); each chunk at least 4 k-blocks, and at most two
+  // CTAs per SM add into one entry (a few hundred FP64 atomics an entry, at
+  // the end of each CTA's chunk, cost microseconds against its sum)
   constexpr int kSMs = 152;
   int64_t max_splits = (K + 4 * kOvK - 1) / (4 * kOvK);
-  if (max_splits > 64) max_splits = 64;
+  if (max_splits > 2 * kSMs) max_splits = 2 * kSMs;
   int s0 = (2 * kSMs + tiles - 1) / tiles;
   if (s0 > max_splits) s0 = (int)max_splits;
   if (s0 < 1) s0 = 1;

@@ -152,6 +152,32 @@ def test_invalid_calls_fail_cleanly():
     assert abs(ex - eref) <= TOL64 * abs(eref)
 
 
+@pytest.mark.parametrize("prec", [_lib.PREC_FP64, _lib.PREC_DF64, _lib.PREC_MIXED32],
+                         ids=["fp64", "df64", "mixed32"])
+def test_empty_occupations_give_zero_and_no_bands_is_refused(prec):
+    # every f_i = 0: each term of V_x psi and of E_x carries an occupation, so
+    # both are exactly zero (the uniform-occupation scaling and the mixed
+    # form's FP64 overlaps included); a call with no bands is an error
+    torch = require_gpu()
+    case = setup_case(24, 10.0, 10.0, 7, 17, kind=_lib.ERFC, omega=0.3, prec=prec, occ=np.zeros(7))
+    plan = case["plan"]
+    vpsi = torch.full_like(case["psi"], complex(np.nan, np.nan))
+    ex, dex = _lib.fock_apply(plan.handle, case["psi"], case["occ"], vpsi, want_dex=True)
+    assert ex == 0.0 and dex == 0.0
+    assert bool(torch.all(vpsi == 0).item())  # written (no NaN left) and zero
+    vref, eref, dref = oracle_of(case)
+    assert not np.any(vref) and eref == 0.0 and dref == 0.0
+    with pytest.raises(_lib.FockError):
+        _lib.fock_apply(plan.handle, case["psi"][:0], [], torch.empty_like(case["psi"][:0]))
+    # the plan still works afterwards, with occupations again
+    case["occ"] = np.full(7, 2.0)
+    v2, e2, _ = plan.apply(case["psi"], case["occ"])
+    vref, eref, _ = oracle_of(case)
+    tol_v, tol_e = (TOL32_V, TOL32_E) if prec == _lib.PREC_MIXED32 else (TOL64, TOL64)
+    assert rel_inf(v2.cpu().numpy(), vref) <= tol_v
+    assert abs(e2 - eref) <= tol_e * abs(eref)
+
+
 @pytest.mark.parametrize("prec,tol_v,tol_e", [(_lib.PREC_FP64, TOL64, TOL64), (_lib.PREC_DF64, TOL64, TOL64),
                                               (_lib.PREC_MIXED32, TOL32_V, TOL32_E)],
                          ids=["fp64", "df64", "mixed32"])
