@@ -94,6 +94,7 @@ struct KernelOps {
   int real_bytes;  // sizeof of the working real type
   int prec;        // 0 FP64, 1 mixed FP32, 2 double-float (fock_precision)
   int n;           // grid size these kernels are compiled for
+  int col_lines;   // lines of the column map a column-pass CTA takes
   size_t smem;     // largest dynamic shared memory of its kernels
   cudaError_t (*configure)(const DevPlan&);
   // c(G) of bands [band0, band0 + nbat) to psi(r); X is scratch of >= ceil(nbat/2) grids.

@@ -159,6 +159,9 @@ __device__ inline void block_sum4_df(df64 v[4], float* red) {
   }
 }
 
+// Shared memory of one SM on sm_103 (228 KB; each resident CTA also reserves 1 KB).
+constexpr size_t kSmemPerSM = 233472;
+
 // Compile-time geometry of the passes for grid size N and radix-plan variant
 // EMAX (elements a thread holds across a stage; 0: the type's own).
 template <class T, int N, int MAXT = kMaxThreads, int EMAX = 0>
@@ -176,11 +179,28 @@ struct Geo {
   static constexpr int THR_PLANE = (N * TLP + 31) / 32 * 32;
   static constexpr int THR_COLH = (NC * TLC + 31) / 32 * 32;
   static constexpr int THR_COLF = (N * TLP + 31) / 32 * 32;
+  // lines per CTA of the column pass: the NC columns of a row's width, or,
+  // where two CTAs of that width do not fit the SM's shared memory (FP64 and
+  // double-float at N = 96: 153 KB each), about half as many, rounded up to 8
+  // lines (whole warps at 4 and 8 threads a line), so that two CTAs share an
+  // SM and the barriers of one overlap the arithmetic of the other
+  static constexpr int NLC_HALF = (KH + 7) / 8 * 8;
+  static constexpr bool COL_SPLIT =
+      2 * (sizeof(C) * (size_t)(N * NC + kTwiddleTable * N) + 32 * 4 * sizeof(double) + NC * sizeof(int) + 1024) >
+          kSmemPerSM &&
+      NLC_HALF < NC;
+  static constexpr int NLC = COL_SPLIT ? NLC_HALF : NC;
+  static constexpr int THR_COL = (NLC * TLC + 31) / 32 * 32;
   static_assert(THR_PLANE <= 1024 && THR_COLH <= 1024, "CTA too large");
   // CTAs per SM the column and inverse passes are register-budgeted for
   // (shared memory allows two in FP32 up to N = 96, one in FP64): two when two
   // CTAs of 72 registers a thread fit the register file
   static constexpr int MIN_CTAS = (sizeof(T) == 4 && 2 * 72 * THR_COLH <= 65536) ? 2 : 1;
+  // CTAs per SM the column pass is register-budgeted for: two where its CTAs
+  // take half a row's width of lines with more than 256 threads (72 registers a
+  // thread); smaller ones fit two at the registers they take unbounded (142 at
+  // 224 threads in FP64)
+  static constexpr int MIN_CTAS_COL = (NLC < NC && THR_COL > 256) ? 2 : MIN_CTAS;
   // CTAs per SM the k-point inverse plane pass is register-budgeted for: in
   // FP32, eight where eight CTAs of 40 registers a thread fit the register file
   // (its shared memory allows that many up to N = 48); 0 leaves the choice to
@@ -191,7 +211,7 @@ struct Geo {
   static constexpr int TWN = kTwiddleTable * N;
   static constexpr size_t SMEM_PLANE = sizeof(C) * (size_t)(N * RP + TWN);
   static constexpr size_t SMEM_COLH =
-      sizeof(C) * (size_t)(N * NC + TWN) + 32 * 4 * sizeof(double) + NC * sizeof(int);
+      sizeof(C) * (size_t)(N * NLC + TWN) + 32 * 4 * sizeof(double) + NLC * sizeof(int);
   static constexpr size_t SMEM_COLF = sizeof(C) * (size_t)(N * N + TWN);
   // inverse plane pass: the stored half plane with an odd row stride NC + 1,
   // the twiddles and the column map's row lengths
@@ -527,32 +547,33 @@ template <class T> __host__ __device__ constexpr bool inv_first_stage_direct() {
   return kFirstStageDirect && RealTraits<T>::prec != 2;
 }
 
-// Stage the column pass's line codes in shared memory.
-template <int NC>
+// Stage the column pass's line codes (NL a CTA) in shared memory.
+template <int NL>
 __device__ __forceinline__ void col_codes(const DevPlan& g, int cta, int* codes) {
-  for (int l = threadIdx.x; l < NC; l += blockDim.x) codes[l] = __ldg(g.colmap + cta * NC + l);
+  for (int l = threadIdx.x; l < NL; l += blockDim.x) codes[l] = __ldg(g.colmap + cta * NL + l);
   __syncthreads();
 }
 
-// The column of Hc that this thread's line of the column pass reads and
-// writes (the line-fast thread mapping of the transforms: line tid mod NC),
-// or NULL for a line without a code.  codes must be staged.
-template <class C, int N, int NC>
+// The column of Hc (NC stored columns a row) that this thread's line of the
+// column pass reads and writes (the line-fast thread mapping of the
+// transforms: line tid mod NL), or NULL for a line without a code.  codes
+// must be staged.
+template <class C, int N, int NC, int NL>
 __device__ __forceinline__ C* col_line_ptr(C* Hc, const int* codes) {
   constexpr int KH = NC / 2;
-  const int code = codes[threadIdx.x % NC];
+  const int code = codes[threadIdx.x % NL];
   return code >= 0 ? Hc + line_k2(code) * NC + line_s(code) * KH + line_k3(code) : nullptr;
 }
 
 // Store the transformed lines: thread (line l, sub-thread t) writes elements
 // i1 = t, t + TL, ... of its own line (consecutive lanes hold consecutive
 // lines, so both the shared reads and the global writes are contiguous).
-template <class C, int N, int NC, int TL>
+template <class C, int N, int NC, int NL, int TL>
 __device__ __forceinline__ void col_store_lines(C* lp, const C* S) {
-  const int l = threadIdx.x % NC, t = threadIdx.x / NC;
+  const int l = threadIdx.x % NL, t = threadIdx.x / NL;
   if (lp != nullptr && t < TL) {
 #pragma unroll 4
-    for (int i1 = t; i1 < N; i1 += TL) lp[(int64_t)i1 * N * NC] = S[i1 * NC + l];
+    for (int i1 = t; i1 < N; i1 += TL) lp[(int64_t)i1 * N * NC] = S[i1 * NL + l];
   }
 }
 
@@ -565,18 +586,18 @@ __device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __rest
                                                  unsigned char* smem_raw) {
   using C = cdf64;
   using G = Geo<df64, N, MAXT, EMAX>;
-  constexpr int KH = G::KH, NC = G::NC;
+  constexpr int KH = G::KH, NC = G::NC, NL = G::NLC;
   C* S = reinterpret_cast<C*>(smem_raw);
-  C* tw = S + N * NC;
+  C* tw = S + N * NL;
   double* red = reinterpret_cast<double*>(tw + G::TWN);
   int* codes = reinterpret_cast<int*>(red + 32 * 4);
   load_twiddles<df64>(tw, g);
   const bool want_d = g.dvtab64 != nullptr;
   const df64* vt = static_cast<const df64*>(g.vtab);  // v / Ntot
   const df64* dvt = static_cast<const df64*>(g.dvtab);  // dv/domega
-  col_codes<NC>(g, cta, codes);
+  col_codes<NL>(g, cta, codes);
   {
-    const C* lp = col_line_ptr<C, N, NC>(Hc, codes);
+    const C* lp = col_line_ptr<C, N, NC, NL>(Hc, codes);
     const auto val = [&](int, int i1) {
       C v;
       if (lp != nullptr) {
@@ -587,19 +608,19 @@ __device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __rest
       }
       return v;
     };
-    fft_lines_from<df64, N, -1, NC, G::TLC, 1, NC, MAXT, EMAX>(S, tw, val);  // along i1
+    fft_lines_from<df64, N, -1, NL, G::TLC, 1, NL, MAXT, EMAX>(S, tw, val);  // along i1
   }
   {
     df64 accd[4] = {df64(0.f), df64(0.f), df64(0.f), df64(0.f)};
     // one line per thread (decoded once), walking k1
-    const int l = threadIdx.x % NC, kstep = blockDim.x / NC;
-    const int code = threadIdx.x < kstep * NC ? codes[l] : -1;
+    const int l = threadIdx.x % NL, kstep = blockDim.x / NL;
+    const int code = threadIdx.x < kstep * NL ? codes[l] : -1;
     if (code >= 0) {
       const int k2 = line_k2(code), s = line_s(code), k3 = line_k3(code);
       const float wgt = (k3 == 0 || 2 * k3 == N) ? 1.0f : 2.0f;
       df64 e_sum(0.f), d_sum(0.f);
-      for (int k1 = threadIdx.x / NC; k1 < N; k1 += kstep) {
-        const int e = k1 * NC + l;
+      for (int k1 = threadIdx.x / NL; k1 < N; k1 += kstep) {
+        const int e = k1 * NL + l;
         const int vi = (k1 * N + k2) * KH + k3;
         C z = S[e];
         const df64 a2 = z.x * z.x + z.y * z.y;
@@ -628,8 +649,8 @@ __device__ __forceinline__ void pair_col_task_df(const DevPlan& g, cdf64* __rest
       put_energies(g, ch, cta, acc, want_d, epair, dpair);
     }
   }
-  fft_lines<df64, N, +1, NC, G::TLC, 1, NC, MAXT, EMAX>(S, tw);  // inverse along k1
-  col_store_lines<C, N, NC, G::TLC>(col_line_ptr<C, N, NC>(Hc, codes), S);
+  fft_lines<df64, N, +1, NL, G::TLC, 1, NL, MAXT, EMAX>(S, tw);  // inverse along k1
+  col_store_lines<C, N, NC, NL, G::TLC>(col_line_ptr<C, N, NC, NL>(Hc, codes), S);
 }
 
 // The column pass in FP64 or in the mixed form.
@@ -639,17 +660,17 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
                                                   double* __restrict__ dpair, unsigned char* smem_raw) {
   using C = cplx<T>;
   using G = Geo<T, N, MAXT, EMAX>;
-  constexpr int KH = G::KH, NC = G::NC;
+  constexpr int KH = G::KH, NC = G::NC, NL = G::NLC;
   C* S = reinterpret_cast<C*>(smem_raw);
-  C* tw = S + N * NC;
+  C* tw = S + N * NL;
   double* red = reinterpret_cast<double*>(tw + G::TWN);
   int* codes = reinterpret_cast<int*>(red + 32 * 4);
   load_twiddles<T>(tw, g);
-  col_codes<NC>(g, cta, codes);
+  col_codes<NL>(g, cta, codes);
   {
     // the first stage reads this thread's line straight from the transform
     // buffer: one base pointer per thread, compile-time offsets per element
-    const C* lp = col_line_ptr<C, N, NC>(Hc, codes);
+    const C* lp = col_line_ptr<C, N, NC, NL>(Hc, codes);
     const auto val = [&](int, int i1) {
       C v;
       if (lp != nullptr) {
@@ -660,7 +681,7 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
       }
       return v;
     };
-    fft_lines_from<T, N, -1, NC, G::TLC, 1, NC, MAXT, EMAX>(S, tw, val);  // along i1
+    fft_lines_from<T, N, -1, NL, G::TLC, 1, NL, MAXT, EMAX>(S, tw, val);  // along i1
   }
 
   // kernel multiply and energy partials
@@ -668,8 +689,8 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
   double acc[4] = {0.0, 0.0, 0.0, 0.0};  // e_a, e_b, d_a, d_b (FP64 terms)
   float acc_f32[4] = {0.f, 0.f, 0.f, 0.f};  // the same from the FP32 terms (mixed form)
   // one line per thread (decoded once), walking k1
-  const int l = threadIdx.x % NC, kstep = blockDim.x / NC;
-  const int code = threadIdx.x < kstep * NC ? codes[l] : -1;
+  const int l = threadIdx.x % NL, kstep = blockDim.x / NL;
+  const int code = threadIdx.x < kstep * NL ? codes[l] : -1;
   if constexpr (RealTraits<T>::prec == 0) {
     if (code >= 0) {
       const int k2 = line_k2(code), s = line_s(code), k3 = line_k3(code);
@@ -679,8 +700,8 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
       // v / Ntot, or -f0 v / Ntot when the occupations are uniform (vtab_f set)
       const double* vs64 = static_cast<const double*>(g.vtab) + k2 * KH + k3;
       double e_sum = 0.0, d_sum = 0.0;
-      for (int k1 = threadIdx.x / NC; k1 < N; k1 += kstep) {
-        const int e = k1 * NC + l;
+      for (int k1 = threadIdx.x / NL; k1 < N; k1 += kstep) {
+        const int e = k1 * NL + l;
         const int vo = k1 * N * KH;
         C z = S[e];
         const double a2 = z.x * z.x + z.y * z.y;
@@ -712,11 +733,11 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
       const T* dvl = dvt + k2 * KH + k3;
       T e_sum = T(0), d_sum = T(0);
       if (r23 > g.msmall2) {  // no term of this line is a small-|G| one
-        const int k10 = threadIdx.x / NC;
+        const int k10 = threadIdx.x / NL;
         const T* vp = vl + k10 * N * KH;
         const T* dvp = dvl + k10 * N * KH;
-        C* sp = S + k10 * NC + l;
-        const int vstep = kstep * N * KH, sstep = kstep * NC;
+        C* sp = S + k10 * NL + l;
+        const int vstep = kstep * N * KH, sstep = kstep * NL;
         // batches of U elements: the U table loads are in flight together
         constexpr int U = 8;
         int k1 = k10;
@@ -748,8 +769,8 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
           *sp = z;
         }
       } else {
-        for (int k1 = threadIdx.x / NC; k1 < N; k1 += kstep) {
-          const int e = k1 * NC + l;
+        for (int k1 = threadIdx.x / NL; k1 < N; k1 += kstep) {
+          const int e = k1 * NL + l;
           const int m1 = freq_of(k1, N);
           if (m1 * m1 + r23 <= g.msmall2) {
             if (s == 0 || ch.bi >= 0) small_g_term_fp64<T, N>(g, S, e, k1, k2, k3, s, ch, epair, dpair);
@@ -782,8 +803,8 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
     acc_f32[3] = accf[3];
   }
   __syncthreads();
-  fft_lines<T, N, +1, NC, G::TLC, 1, NC, MAXT, EMAX>(S, tw);  // inverse along k1
-  col_store_lines<C, N, NC, G::TLC>(col_line_ptr<C, N, NC>(Hc, codes), S);
+  fft_lines<T, N, +1, NL, G::TLC, 1, NL, MAXT, EMAX>(S, tw);  // inverse along k1
+  col_store_lines<C, N, NC, NL, G::TLC>(col_line_ptr<C, N, NC, NL>(Hc, codes), S);
   if constexpr (RealTraits<T>::prec != 1) {
     block_sum4(acc, red);
   } else {
@@ -797,7 +818,7 @@ __device__ __forceinline__ void pair_col_task_std(const DevPlan& g, cplx<T>* __r
   if (threadIdx.x == 0) put_energies(g, ch, cta, acc, want_d, epair, dpair);
 }
 
-// One task of the column pass: the NC lines `cta` of the column map for chain
+// One task of the column pass: the NLC lines `cta` of the column map for chain
 // `ch` (transform buffer Hc).  Shared memory: Geo::SMEM_COLH bytes at smem_raw.
 template <class T, int N, int MAXT, int EMAX = 0>
 __device__ __forceinline__ void pair_col_task(const DevPlan& g, cplx<T>* __restrict__ Hc,
@@ -811,7 +832,7 @@ __device__ __forceinline__ void pair_col_task(const DevPlan& g, cplx<T>* __restr
 }
 
 template <class T, int N, int EMAX = 0>
-__global__ void __launch_bounds__(Geo<T, N, kMaxThreads, EMAX>::THR_COLH, Geo<T, N, kMaxThreads, EMAX>::MIN_CTAS)
+__global__ void __launch_bounds__(Geo<T, N, kMaxThreads, EMAX>::THR_COL, Geo<T, N, kMaxThreads, EMAX>::MIN_CTAS_COL)
     k_pair_col(DevPlan g, cplx<T>* __restrict__ H, const Chain* __restrict__ chains,
                double* __restrict__ epair, double* __restrict__ dpair) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1150,7 +1171,8 @@ struct Launch {
     for (int k = 0; k < pl.nst; ++k) radices[k] = pl.r[k];
     const bool plane = pass == 0;
     *threads_per_line = plane ? pl.tl_plane : pl.tl_colh;
-    *threads = tile == 1 ? (plane ? G1::THR_PLANE : G1::THR_COLH) : (plane ? G::THR_PLANE : G::THR_COLH);
+    const int thr_col = pass == 1 ? G::THR_COL : G::THR_COLH, thr_col1 = pass == 1 ? G1::THR_COL : G1::THR_COLH;
+    *threads = tile == 1 ? (plane ? G1::THR_PLANE : thr_col1) : (plane ? G::THR_PLANE : thr_col);
     return E1 != 0 ? 2 : 1;
   }
 
@@ -1181,10 +1203,10 @@ struct Launch {
   static cudaError_t pair_col(const DevPlan& g, void* H, const Chain* ch, int nch, double* ep,
                               double* dp, cudaStream_t s) {
     if (E1 != 0 && g.tile[1] == 1)
-      k_pair_col<T, N, E1><<<dim3(g.ncta_col, nch), G1::THR_COLH, G::SMEM_COLH, s>>>(
+      k_pair_col<T, N, E1><<<dim3(g.ncta_col, nch), G1::THR_COL, G::SMEM_COLH, s>>>(
           g, static_cast<C*>(H), ch, ep, dp);
     else
-      k_pair_col<T, N><<<dim3(g.ncta_col, nch), G::THR_COLH, G::SMEM_COLH, s>>>(
+      k_pair_col<T, N><<<dim3(g.ncta_col, nch), G::THR_COL, G::SMEM_COLH, s>>>(
           g, static_cast<C*>(H), ch, ep, dp);
     return cudaGetLastError();
   }
@@ -1214,7 +1236,7 @@ struct Launch {
   }
 
   static constexpr KernelOps ops() {
-    return KernelOps{(int)sizeof(T), RealTraits<T>::prec, N,
+    return KernelOps{(int)sizeof(T), RealTraits<T>::prec, N, G::NLC,
                      smem_max(smem_max(G::SMEM_COLH, G::SMEM_PLANE), G::SMEM_INV),
                      configure, to_real, pair_fwd, pair_col, pair_inv, to_sphere, tile_plan};
   }

@@ -850,7 +850,7 @@ fock_status fock_plan_create(fock_plan_t* out, const int grid[3], const double c
       for (int k3 = 0; k3 < ncol[k2]; ++k3) colmap.push_back((k2 << 16) | (s << 15) | k3);
   for (int k2 = 0; k2 < n; ++k2)
     for (int k3 = 0; k3 < ncol[k2]; ++k3) kept.push_back((k2 << 16) | k3);
-  const int nlines = 2 * kh;
+  const int nlines = ops->col_lines;
   p->kept_columns = (int64_t)colmap.size();
   const int ncta_col = std::max(1, (int)((colmap.size() + nlines - 1) / nlines));
   colmap.resize((size_t)ncta_col * nlines, -1);
