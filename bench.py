@@ -335,8 +335,8 @@ def loop_roofline(form, plan, res, steps, peaks, peak_src, band_block, streams):
 # (profiles/pair_traffic_96.md), by form and band block; scaled to a step by
 # its chains
 MEASURED_LOOP_TRAFFIC_PER_CHAIN = {
-    ("fp64", 96, 8): 95.84e6, ("fp64", 96, 16): 87.02e6, ("fp64", 96, 32): 94.23e6,
-    ("df64", 96, 8): 98.46e6, ("df64", 96, 16): 90.22e6, ("df64", 96, 32): 94.56e6,
+    ("fp64", 96, 8): 95.61e6, ("fp64", 96, 16): 86.80e6, ("fp64", 96, 32): 94.01e6,
+    ("df64", 96, 8): 98.40e6, ("df64", 96, 16): 90.15e6, ("df64", 96, 32): 94.48e6,
     ("mixed32", 96, 8): 29.07e6, ("mixed32", 96, 16): 37.69e6,
 }
 
