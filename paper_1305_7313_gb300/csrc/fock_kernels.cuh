@@ -179,15 +179,18 @@ struct Geo {
   static constexpr int THR_PLANE = (N * TLP + 31) / 32 * 32;
   static constexpr int THR_COLH = (NC * TLC + 31) / 32 * 32;
   static constexpr int THR_COLF = (N * TLP + 31) / 32 * 32;
-  // lines per CTA of the column pass: the NC columns of a row's width, or,
-  // where two CTAs of that width do not fit the SM's shared memory (FP64 and
-  // double-float at N = 96: 153 KB each), about half as many, rounded up to 8
-  // lines (whole warps at 4 and 8 threads a line), so that two CTAs share an
-  // SM and the barriers of one overlap the arithmetic of the other
+  // lines per CTA of the column pass: the NC columns of a row's width, or
+  // about half as many, rounded up to 8 lines (whole warps at 4 and 8 threads
+  // a line), where two CTAs of that width do not fit the SM's shared memory
+  // (FP64 and double-float at N = 96: 153 KB each; halved, two share an SM)
+  // and in FP32 from N = 96 (four CTAs of 46 KB an SM instead of two of 78
+  // KB): more CTAs an SM, so that the barriers of one overlap the arithmetic
+  // of the others
   static constexpr int NLC_HALF = (KH + 7) / 8 * 8;
   static constexpr bool COL_SPLIT =
-      2 * (sizeof(C) * (size_t)(N * NC + kTwiddleTable * N) + 32 * 4 * sizeof(double) + NC * sizeof(int) + 1024) >
-          kSmemPerSM &&
+      (2 * (sizeof(C) * (size_t)(N * NC + kTwiddleTable * N) + 32 * 4 * sizeof(double) + NC * sizeof(int) + 1024) >
+           kSmemPerSM ||
+       (sizeof(C) == 8 && N >= 96)) &&
       NLC_HALF < NC;
   static constexpr int NLC = COL_SPLIT ? NLC_HALF : NC;
   static constexpr int THR_COL = (NLC * TLC + 31) / 32 * 32;
@@ -196,11 +199,12 @@ struct Geo {
   // (shared memory allows two in FP32 up to N = 96, one in FP64): two when two
   // CTAs of 72 registers a thread fit the register file
   static constexpr int MIN_CTAS = (sizeof(T) == 4 && 2 * 72 * THR_COLH <= 65536) ? 2 : 1;
-  // CTAs per SM the column pass is register-budgeted for: two where its CTAs
-  // take half a row's width of lines with more than 256 threads (72 registers a
-  // thread); smaller ones fit two at the registers they take unbounded (142 at
-  // 224 threads in FP64)
-  static constexpr int MIN_CTAS_COL = (NLC < NC && THR_COL > 256) ? 2 : MIN_CTAS;
+  // CTAs per SM the column pass is register-budgeted for where its CTAs take
+  // half a row's width of lines: in FP32 as many as fit at 72 registers a
+  // thread; in FP64 and double-float two above 256 threads (72 registers), and
+  // no bound below (two 224-thread CTAs fit the 142 registers FP64 takes)
+  static constexpr int MIN_CTAS_COL =
+      NLC < NC ? (sizeof(C) == 8 ? 65536 / (72 * THR_COL) : (THR_COL > 256 ? 2 : MIN_CTAS)) : MIN_CTAS;
   // CTAs per SM the k-point inverse plane pass is register-budgeted for: in
   // FP32, eight where eight CTAs of 40 registers a thread fit the register file
   // (its shared memory allows that many up to N = 48); 0 leaves the choice to
