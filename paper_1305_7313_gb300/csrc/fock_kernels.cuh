@@ -177,6 +177,8 @@ struct Geo {
   // CTA sizes rounded up to whole warps (the extra threads idle in the FFT
   // stages), so warp shuffles always see 32 live lanes
   static constexpr int THR_PLANE = (N * TLP + 31) / 32 * 32;
+  // NC lines at the column tiling: the inverse plane pass's CTA (its k2
+  // transform of up to NC stored columns); the column pass sizes its own below
   static constexpr int THR_COLH = (NC * TLC + 31) / 32 * 32;
   static constexpr int THR_COLF = (N * TLP + 31) / 32 * 32;
   // lines per CTA of the column pass: the NC columns of a row's width, or
