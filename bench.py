@@ -333,11 +333,11 @@ def loop_roofline(form, plan, res, steps, peaks, peak_src, band_block, streams):
 # DRAM bytes (read + write) per chain of the three pair kernels together, from
 # ncu captures of the 96^3 pair passes on one stream at 38 chains per launch
 # (profiles/pair_traffic_96.md), by form and band block; scaled to a step by
-# its chains
+# its chains.  The mixed form's column pass has changed since its capture
+# (CTAs of 56 lines), so its loop has no measured figure
 MEASURED_LOOP_TRAFFIC_PER_CHAIN = {
     ("fp64", 96, 8): 95.61e6, ("fp64", 96, 16): 86.80e6, ("fp64", 96, 32): 94.01e6,
     ("df64", 96, 8): 98.40e6, ("df64", 96, 16): 90.15e6, ("df64", 96, 32): 94.48e6,
-    ("mixed32", 96, 8): 29.07e6, ("mixed32", 96, 16): 37.69e6,
 }
 
 
@@ -459,8 +459,9 @@ def run_batched(args, peaks, peak_src):
 # DRAM bytes (read + write) per chain of the three pair passes of the batch's
 # systems, by grid size, at band block 16: an ncu capture of every pair launch
 # of the 64-band version of the batch as graph branches (launches serialised
-# by ncu; profiles/pair_traffic_96.md)
-BATCH_DRAM_PER_CHAIN = {48: 3.077e6, 64: 7.361e6, 72: 10.790e6, 96: 42.290e6}
+# by ncu; profiles/pair_traffic_96.md).  The 96^3 systems' column pass has
+# changed since (CTAs of 56 lines), so the batch has no measured total
+BATCH_DRAM_PER_CHAIN = {48: 3.077e6, 64: 7.361e6, 72: 10.790e6}
 BATCH_DRAM_BAND_BLOCK = 16
 
 
