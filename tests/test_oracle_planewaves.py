@@ -198,3 +198,33 @@ def test_bloch_plane_waves_take_the_momentum_difference(kind, omega):
         assert np.max(np.abs(vk[k] - expect)) <= 1e-12 * np.max(np.abs(lam))
         ex_expect += 0.5 * weights[k] * np.dot(occ[k], lam)
     assert abs(ex - ex_expect) <= 1e-12 * abs(ex_expect)
+
+
+@pytest.mark.parametrize("kind,omega", CASES, ids=["spencer_alavi", "erfc"])
+def test_fixed_operator_on_trial_plane_waves(kind, omega):
+    # V_x fixed by plane-wave occupied states, applied to trial plane waves
+    # that are not among them (complex orbitals): each trial wave is an
+    # eigenfunction with -(1/Omega) sum_i f_i v(G_a - G_i)
+    grid = (16, 16, 16)
+    cell = GENERAL_CELL
+    vol = cell_volume(cell)
+    b = reciprocal_lattice(cell)
+    miller, _ = oracle.gsphere(grid, cell, 4.0)
+    occupied = [(0, 0, 0), (1, 0, 0), (0, 1, -1)]
+    occ = np.array([2.0, 1.25, 0.5])
+    trial = [(-1, 0, 0), (0, 0, 1), (1, -1, 1), (0, 0, 0)]
+    c_occ = np.zeros((len(occupied), len(miller)), dtype=np.complex128)
+    c_tr = np.zeros((len(trial), len(miller)), dtype=np.complex128)
+    for n, m in enumerate(occupied):
+        c_occ[n, sphere_row(miller, m)] = 1.0
+    for n, m in enumerate(trial):
+        c_tr[n, sphere_row(miller, m)] = 1.0
+    out = oracle.fock_apply_to(c_occ, occ, c_tr, miller, grid, cell, kind, omega, real=False)
+    go = np.array(occupied, dtype=np.float64) @ b
+    gt = np.array(trial, dtype=np.float64) @ b
+    lam = np.zeros(len(trial))
+    for a in range(len(trial)):
+        for i in range(len(occupied)):
+            d = gt[a] - go[i]
+            lam[a] -= occ[i] * kernel(kind, float(d @ d), vol, omega)[0] / vol
+    assert np.max(np.abs(out - lam[:, None] * c_tr)) <= 1e-12 * np.max(np.abs(lam))
